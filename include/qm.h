@@ -1,0 +1,137 @@
+/*
+ * qm.h -- C ABI of the GB300 quantile library (libqm.so).
+ *
+ * Element-wise quantile evaluation over device arrays, after Shaw, Luu &
+ * Brickman, "Quantile Mechanics II" (arXiv 0901.0638):
+ *   - the normal quantile w(u) = Phi^{-1}(u) (Sec. 1, Eq. 1) through a change
+ *     of variables to the exponential coordinate v = -log(2 min(u, 1-u))
+ *     (Sec. 6, Sec. 7.2) or the scaled Student-t_2 coordinate
+ *     v = |u - 1/2| / sqrt(u - u^2) (Sec. 7.3), each followed by one rational
+ *     approximation;
+ *   - the recycling maps Q(x) = F^{-1}(G(x)) of Sec. 2.1: normal -> Student t
+ *     (Sec. 3) and exponential -> normal (Sec. 2.3, Sec. 6);
+ *   - fused counter-based generation (Philox4x32-10) + transform.
+ *
+ * Conventions (all entry points):
+ *   - Data pointers are DEVICE pointers owned by the caller unless stated.
+ *     The library owns only workspaces it allocates in *_create calls (and a
+ *     small per-device scratch for reductions, allocated on first use).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous on it; argument errors are returned
+ *     synchronously before any launch; launch failures return QM_ERR_CUDA.
+ *   - n == 0 returns QM_OK with no launch.  In-place (in == out) is allowed;
+ *     any other overlap of in and out is QM_ERR_INVALID.  Pointers of any
+ *     alignment are accepted (16-byte aligned ones take the vector path).
+ *   - Out-of-domain inputs give IEEE results, not errors: Phi^{-1}(0) = -inf,
+ *     Phi^{-1}(1) = +inf, NaN for u outside [0, 1] or NaN.
+ *   - qm_last_error() returns a thread-local message for the last failure.
+ */
+#ifndef QM_H
+#define QM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QM_OK = 0,
+    QM_ERR_INVALID = 1,      /* bad argument: null pointer, overlap, bad enum */
+    QM_ERR_UNSUPPORTED = 2,  /* valid request this library does not provide  */
+    QM_ERR_CUDA = 3,         /* a CUDA runtime call or launch failed          */
+    QM_ERR_NOMEM = 4,        /* device or host allocation failed              */
+    QM_ERR_TIMEOUT = 5       /* a bounded device wait gave up                 */
+} qm_status;
+
+typedef enum {
+    QM_DIST_UNIFORM = 0,
+    QM_DIST_NORMAL = 1,
+    QM_DIST_STUDENT_T = 2,
+    QM_DIST_EXPONENTIAL = 3
+} qm_dist;
+
+/* Algorithm variants of the normal quantile. */
+typedef enum {
+    QM_VAR_DEFAULT = 0,      /* FP32: SQRT_FORM.  FP64: COMPACT.                 */
+    QM_VAR_BRANCHFREE = 1,   /* exponential coordinate, one rational for the
+                                whole range (FP32: Sec. 6.1 form z = v P/Q on
+                                v <= 25; FP64: Sec. 7.2 form on v <= 42 plus a
+                                deep-tail rational on 42 < v <= 745)            */
+    QM_VAR_HYBRID_VOTE = 2,  /* FP64: t_2 coordinate when the whole warp has
+                                v < 15.5, else the exponential form (Sec. 7.3,
+                                the warp vote)                                  */
+    QM_VAR_MIXED_HALLEY = 3, /* FP64: FP32 rational + one FP64 Halley step     */
+    QM_VAR_COMPACT = 4,      /* FP64: t_2 coordinate for every element it
+                                covers; the others are compacted per block and
+                                evaluated densely in the exponential form       */
+    QM_VAR_SQRT_FORM = 5,    /* FP32: exponential coordinate with a two-float
+                                logarithm, z = v sqrt(R(v)), R = (Q(v)/v)^2     */
+    QM_VAR_CUDA_LIBM = 6     /* comparator: CUDA's normcdfinvf / normcdfinv     */
+} qm_variant;
+
+typedef struct {
+    double nu; /* Student-t degrees of freedom, nu > 0; ignored otherwise */
+} qm_params;
+
+/* ---- normal quantile ------------------------------------------------------
+ * z[i] = Phi^{-1}(u[i]) for i < n (Sec. 1, Eq. 1).  FP32 variants: DEFAULT,
+ * BRANCHFREE, SQRT_FORM, CUDA_LIBM; FP64 variants: DEFAULT, BRANCHFREE,
+ * HYBRID_VOTE, MIXED_HALLEY, COMPACT, CUDA_LIBM (others: QM_ERR_INVALID).
+ * u, z: contiguous arrays of n elements (device).                           */
+qm_status qm_normal_quantile_f32(const float* u, float* z, size_t n,
+                                 int variant, void* stream);
+qm_status qm_normal_quantile_f64(const double* u, double* z, size_t n,
+                                 int variant, void* stream);
+
+/* z[i] = Phi^{-1}((k + 1/2) 2^-24) with k = words[i] >> 8 (the top 24 bits),
+ * evaluated in the exact reflected form d = (min(k, 2^24-1-k) + 1/2) 2^-24
+ * (Sec. 6.1, the "better" reflection).  words: uint32[n], z: float[n].      */
+qm_status qm_normal_quantile_bits24_f32(const uint32_t* words, float* z,
+                                        size_t n, void* stream);
+
+/* ---- Philox4x32-10 (Salmon et al., SC'11) ---------------------------------
+ * out[i] = word (ctr0 + i) of the stream with 64-bit key `key`: output word
+ * (j mod 4) of block floor(j/4), block b = counter (b lo32, b hi32, 0, 0),
+ * key (key lo32, key hi32).  out: uint32[n] (device).                      */
+qm_status qm_philox_fill_u32(uint64_t key, uint64_t ctr0, uint32_t* out,
+                             size_t n, void* stream);
+
+/* ---- fused generate + transform -------------------------------------------
+ * Sample i (0 <= i < n) of `target` drawn from the key's stream starting at
+ * word ctr0 (ctr0 must be a multiple of 4), uniforms kept in registers:
+ *   QM_DIST_NORMAL, out_is_f64 = 0: word ctr0+i -> k = top 24 bits ->
+ *       z = Phi^{-1}((k + 1/2) 2^-24), identical to
+ *       qm_philox_fill_u32 + qm_normal_quantile_bits24_f32;
+ *   QM_DIST_NORMAL, out_is_f64 = 1: words (ctr0+2i, ctr0+2i+1) -> 53-bit k
+ *       -> z = Phi^{-1}((k + 1/2) 2^-53) (FP64 exponential form);
+ *   QM_DIST_STUDENT_T (p->nu required): t = F_nu^{-1}(Phi(z)) of the FP64
+ *       normal above (Sec. 3 map), FP64 only;
+ *   QM_DIST_EXPONENTIAL: x = -log((k + 1/2) 2^-53) mapped to the normal by
+ *       the Sec. 6 recycling map, FP64 only.
+ * out: float[n] / double[n] (device) or NULL.  moments4: double[4] (device)
+ * or NULL; if given it receives sum z, sum z^2, sum z^3, sum z^4 over the n
+ * samples (overwritten, not accumulated).  At least one of out / moments4. */
+qm_status qm_sample_fused(int target, const qm_params* p, uint64_t key,
+                          uint64_t ctr0, void* out, int out_is_f64, size_t n,
+                          double* moments4, void* stream);
+
+/* ---- recycling maps Q = F^{-1}(G(x)) (Sec. 2.1) -----------------------------
+ * Supported (src, dst): (NORMAL, STUDENT_T): out = F_nu^{-1}(Phi(in))
+ * (Sec. 3; nu in {1,2,3,4,5,8,10,30}, p->nu required);
+ * (EXPONENTIAL, NORMAL): out = Phi^{-1}(1 - e^{-in}) (Sec. 2.3, Sec. 6);
+ * (UNIFORM, NORMAL): out = Phi^{-1}(in) (FP64 default variant).
+ * Anything else: QM_ERR_UNSUPPORTED.  in, out: double[n] (device).        */
+qm_status qm_recycle(int src, int dst, const qm_params* p, const double* in,
+                     double* out, size_t n, void* stream);
+
+/* ---- diagnostics ----------------------------------------------------------- */
+const char* qm_last_error(void);
+const char* qm_version(void);
+int qm_sm_count(void); /* SMs of the current device, or -1 */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QM_H */

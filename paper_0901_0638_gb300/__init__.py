@@ -1,0 +1,156 @@
+"""GB300 quantile library: Python binding of the C ABI in include/qm.h.
+
+Argument marshalling only.  Every computation runs in the CUDA kernels of
+``libqm.so`` (built in-tree from ``csrc/`` by ``_build.build()``); there is no
+CPU or PyTorch fallback, and a missing library raises at import of a binding.
+Tensors are torch CUDA tensors used for device memory; the stream defaults to
+torch's current stream on the tensor's device.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _build
+
+QM_OK, QM_ERR_INVALID, QM_ERR_UNSUPPORTED, QM_ERR_CUDA, QM_ERR_NOMEM, QM_ERR_TIMEOUT = range(6)
+QM_DIST_UNIFORM, QM_DIST_NORMAL, QM_DIST_STUDENT_T, QM_DIST_EXPONENTIAL = range(4)
+(QM_VAR_DEFAULT, QM_VAR_BRANCHFREE, QM_VAR_HYBRID_VOTE, QM_VAR_MIXED_HALLEY,
+ QM_VAR_COMPACT, QM_VAR_SQRT_FORM, QM_VAR_CUDA_LIBM) = range(7)
+
+LIB_PATH = _build.LIB
+
+_lib = None
+
+
+class QMError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"qm status {status}: {msg}")
+        self.status = status
+
+
+class qm_params(ctypes.Structure):
+    _fields_ = [("nu", ctypes.c_double)]
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libqm.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library {LIB_PATH} is missing; run __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, sz, i, u64, d = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint64, ctypes.c_double
+    sig = {
+        "qm_normal_quantile_f32": [vp, vp, sz, i, vp],
+        "qm_normal_quantile_f64": [vp, vp, sz, i, vp],
+        "qm_normal_quantile_bits24_f32": [vp, vp, sz, vp],
+        "qm_philox_fill_u32": [u64, u64, vp, sz, vp],
+        "qm_sample_fused": [i, vp, u64, u64, vp, i, sz, vp, vp],
+        "qm_recycle": [i, i, vp, vp, vp, sz, vp],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    L.qm_last_error.restype = ctypes.c_char_p
+    L.qm_last_error.argtypes = []
+    L.qm_version.restype = ctypes.c_char_p
+    L.qm_sm_count.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def declared_symbols():
+    """The entry points include/qm.h declares (parsed from the header)."""
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    names = []
+    for h in sorted(os.listdir(os.path.join(root, "include"))):
+        if not h.endswith(".h"):
+            continue
+        txt = open(os.path.join(root, "include", h)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names += re.findall(r"\b(qm_[a-z0-9_]+)\s*\(", txt)
+    return sorted(set(names))
+
+
+def _check(status: int):
+    if status != QM_OK:
+        raise QMError(status, load().qm_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream, t=None):
+    if stream is None:
+        import torch
+        dev = t.device if (t is not None and hasattr(t, "device")) else None
+        return torch.cuda.current_stream(dev).cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _numel(t, n):
+    return t.numel() if n is None else n
+
+
+def _params(nu):
+    return None if nu is None else ctypes.byref(qm_params(float(nu)))
+
+
+# ---- bindings (same names as the C entry points) ---------------------------
+
+def qm_normal_quantile_f32(u, z, variant: int = QM_VAR_DEFAULT, n=None, stream=None):
+    _check(load().qm_normal_quantile_f32(_ptr(u), _ptr(z), _numel(u, n), variant, _stream(stream, u)))
+    return z
+
+
+def qm_normal_quantile_f64(u, z, variant: int = QM_VAR_DEFAULT, n=None, stream=None):
+    _check(load().qm_normal_quantile_f64(_ptr(u), _ptr(z), _numel(u, n), variant, _stream(stream, u)))
+    return z
+
+
+def qm_normal_quantile_bits24_f32(words, z, n=None, stream=None):
+    _check(load().qm_normal_quantile_bits24_f32(_ptr(words), _ptr(z), _numel(words, n),
+                                                _stream(stream, words)))
+    return z
+
+
+def qm_philox_fill_u32(key: int, ctr0: int, out, n=None, stream=None):
+    _check(load().qm_philox_fill_u32(key, ctr0, _ptr(out), _numel(out, n), _stream(stream, out)))
+    return out
+
+
+def qm_sample_fused(target: int, key: int, ctr0: int, out=None, out_is_f64: bool = False,
+                    n=None, moments4=None, nu=None, stream=None):
+    ref = out if out is not None else moments4
+    if n is None:
+        n = out.numel()
+    _check(load().qm_sample_fused(target, _params(nu), key, ctr0, _ptr(out), int(out_is_f64), n,
+                                  _ptr(moments4), _stream(stream, ref)))
+    return out
+
+
+def qm_recycle(src: int, dst: int, inp, out, nu=None, n=None, stream=None):
+    _check(load().qm_recycle(src, dst, _params(nu), _ptr(inp), _ptr(out), _numel(inp, n),
+                             _stream(stream, inp)))
+    return out
+
+
+def qm_last_error() -> str:
+    return load().qm_last_error().decode()
+
+
+def qm_version() -> str:
+    return load().qm_version().decode()

@@ -1,0 +1,15 @@
+// qm_host.h -- host-side helpers shared by the library's translation units.
+#pragma once
+
+#include <cstddef>
+
+#include "qm.h"
+
+namespace qm {
+
+qm_status fail(qm_status s, const char* fmt, ...);
+qm_status check_launch(const char* what);
+int sm_count();
+bool bad_overlap(const void* a, size_t abytes, const void* b, size_t bbytes);
+
+}  // namespace qm

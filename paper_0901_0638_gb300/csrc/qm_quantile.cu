@@ -1,0 +1,695 @@
+// qm_quantile.cu -- streaming normal-quantile kernels, Philox fill, fused
+// generate+transform, the exponential->normal recycling map, and their C ABI.
+//
+// Kernel shapes (sm_103a, 152 SMs):
+//   * map kernels: persistent grid-stride over 128-bit vectors (float4 /
+//     double2), U independent vectors in flight per thread, streaming cache
+//     hints (ld.global.cs / st.global.cs); scalar tail.  Grid = SMs x resident
+//     blocks per SM.
+//   * COMPACT (FP64): per 1024-element tile, every element whose t_2
+//     coordinate is below 15.5 is finished in place; the rest are appended to
+//     two shared-memory queues (exponential main piece, deep tail) with
+//     warp-aggregated atomics and evaluated densely by the whole block.
+//   * HYBRID_VOTE (FP64): the Sec. 7.3 warp vote with __all_sync.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "qm.h"
+#include "qm_device.cuh"
+#include "qm_host.h"
+
+namespace qm {
+
+// ===========================================================================
+// Error reporting
+// ===========================================================================
+static thread_local std::string g_last_error;
+
+qm_status fail(qm_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+qm_status check_launch(const char* what)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return fail(QM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    return QM_OK;
+}
+
+int sm_count()
+{
+    static int cached[64];
+    static std::once_flag once[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -1;
+    std::call_once(once[dev], [dev] {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) v = -1;
+        cached[dev] = v;
+    });
+    return cached[dev];
+}
+
+bool bad_overlap(const void* a, size_t abytes, const void* b, size_t bbytes)
+{
+    const char* pa = (const char*)a;
+    const char* pb = (const char*)b;
+    if (pa == pb) return false;  // exact in-place is allowed
+    return pa < pb + bbytes && pb < pa + abytes;
+}
+
+// ===========================================================================
+// Element functors
+// ===========================================================================
+struct F32Sqrt   { __device__ float operator()(float u) const { return probit_f32<FORM_SQRT>(u); } };
+struct F32Paper  { __device__ float operator()(float u) const { return probit_f32<FORM_PAPER>(u); } };
+struct F32Libm   { __device__ float operator()(float u) const { return normcdfinvf(u); } };
+
+struct F64BranchFree {
+    __device__ double operator()(double u) const
+    {
+        const double d = reflect_f64(u);
+        const double v = -log(2.0 * d);
+        const double m = is_deep(d) ? probit_mag_exp_deep(v) : probit_mag_exp_main(v);
+        return fix_edges_f64(u, d, m);
+    }
+};
+struct F64Mixed {
+    __device__ double operator()(double u) const
+    {
+        const double d = reflect_f64(u);
+        const double m = (d > 0.0 && d <= 0.5) ? probit_mag_mixed(d) : 0.0;
+        return fix_edges_f64(u, d, m);
+    }
+};
+struct F64Libm { __device__ double operator()(double u) const { return normcdfinv(u); } };
+
+// Sec. 6 exponential -> normal map, z = Phi^{-1}(1 - e^{-x}).  With
+// y = ln2 - x (ln 2 split hi + lo): x >= ln 2 gives z = +Q(v), v = -y, with no
+// logarithm at all; x < ln 2 gives z = -Q(v), v = -log(2 - e^y), taken as
+// -log1p(-expm1(y)) for x >= 0.35 and -log(-2 expm1(-x)) below.
+struct ExpToNormal {
+    __device__ double operator()(double x) const
+    {
+        const double kLn2Hi = 0.69314718055994528623, kLn2Lo = 2.3190468138462996154e-17;
+        const double y = __dadd_rn(__dadd_rn(kLn2Hi, -x), kLn2Lo);
+        double v;
+        bool neg;
+        if (y <= 0.0) {
+            v = -y;
+            neg = false;
+        } else {
+            v = (x >= 0.35) ? -log1p(-expm1(y)) : -log(-2.0 * expm1(-x));
+            neg = true;
+        }
+        double m = (v <= coef::F64_EXP_HI) ? probit_mag_exp_main(v) : probit_mag_exp_deep(v);
+        m = (x == 0.0) ? __longlong_as_double(0x7ff0000000000000ll) : m;
+        m = (x >= 0.0) ? m : __longlong_as_double(0x7ff8000000000000ll);
+        m = (x == __longlong_as_double(0x7ff0000000000000ll)) ? x : m;
+        return neg ? -m : m;
+    }
+};
+
+// ===========================================================================
+// Generic streaming map
+// ===========================================================================
+template <typename T> struct Vec;
+template <> struct Vec<float>  { using type = float4;  static constexpr int W = 4; };
+template <> struct Vec<double> { using type = double2; static constexpr int W = 2; };
+
+template <typename V, class F>
+__device__ __forceinline__ V apply_vec(V a, const F& f);
+template <class F>
+__device__ __forceinline__ float4 apply_vec(float4 a, const F& f)
+{
+    return make_float4(f(a.x), f(a.y), f(a.z), f(a.w));
+}
+template <class F>
+__device__ __forceinline__ double2 apply_vec(double2 a, const F& f)
+{
+    return make_double2(f(a.x), f(a.y));
+}
+
+template <typename T, int U, class F>
+__global__ void __launch_bounds__(256)
+k_map_vec(const T* __restrict__ in, T* out, size_t n, F f)
+{
+    using V = typename Vec<T>::type;
+    constexpr int W = Vec<T>::W;
+    const size_t nv = n / W;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const V* vin = reinterpret_cast<const V*>(in);
+    V* vout = reinterpret_cast<V*>(out);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride * U) {
+        V a[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k)
+            if (i + k * stride < nv) a[k] = __ldcs(vin + i + k * stride);
+#pragma unroll
+        for (int k = 0; k < U; ++k)
+            if (i + k * stride < nv) __stcs(vout + i + k * stride, apply_vec(a[k], f));
+    }
+    const size_t tail = nv * W;
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n - tail) out[tail + t] = f(in[tail + t]);
+}
+
+template <typename T, class F>
+__global__ void __launch_bounds__(256)
+k_map_scalar(const T* in, T* out, size_t n, F f)
+{
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        out[i] = f(in[i]);
+}
+
+template <typename K>
+static int grid_for(K kernel, int block, size_t work_items)
+{
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, block, 0) != cudaSuccess || bps < 1)
+        bps = 1;
+    const int sms = sm_count() > 0 ? sm_count() : 1;
+    size_t g = (work_items + block - 1) / block;
+    size_t cap = (size_t)sms * bps;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+template <typename T, class F>
+static qm_status launch_map(const T* in, T* out, size_t n, F f, cudaStream_t s, const char* what)
+{
+    constexpr int U = 2, B = 256;
+    const bool aligned = ((uintptr_t)in % 16 == 0) && ((uintptr_t)out % 16 == 0);
+    if (aligned) {
+        const size_t nv = n / Vec<T>::W;
+        const int g = grid_for(k_map_vec<T, U, F>, B, (nv + U - 1) / U > 0 ? (nv + U - 1) / U : 1);
+        k_map_vec<T, U, F><<<g, B, 0, s>>>(in, out, n, f);
+    } else {
+        const int g = grid_for(k_map_scalar<T, F>, B, n);
+        k_map_scalar<T, F><<<g, B, 0, s>>>(in, out, n, f);
+    }
+    return check_launch(what);
+}
+
+// ===========================================================================
+// FP64 hybrid with the warp vote (Sec. 7.3): every lane holds one element;
+// if all 32 t_2 coordinates are below 15.5 the warp takes the t_2 rational,
+// otherwise the whole warp takes the exponential form.
+// ===========================================================================
+__device__ __forceinline__ double hybrid_vote_elem(double u, bool valid)
+{
+    const double d = reflect_f64(u);
+    const bool t2 = in_t2_domain(d) || !valid;
+    double m;
+    if (__all_sync(0xffffffffu, t2)) {
+        m = probit_mag_t2(t2_coord(d));
+    } else {
+        const double v = -log(2.0 * d);
+        m = is_deep(d) ? probit_mag_exp_deep(v) : probit_mag_exp_main(v);
+    }
+    return fix_edges_f64(u, d, m);
+}
+
+template <int U>
+__global__ void __launch_bounds__(256)
+k_f64_hybrid_vote(const double* __restrict__ in, double* out, size_t n)
+{
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t warp_base0 = ((size_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u));
+    const unsigned lane = threadIdx.x & 31u;
+    for (size_t wb = warp_base0; wb < n; wb += stride * U) {
+        double a[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const size_t i = wb + k * stride + lane;
+            a[k] = (i < n) ? __ldcs(in + i) : 0.5;
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const size_t i = wb + k * stride + lane;
+            const double z = hybrid_vote_elem(a[k], i < n);
+            if (i < n) __stcs(out + i, z);
+        }
+    }
+}
+
+// ===========================================================================
+// FP64 COMPACT: t_2 in place, compacted exponential / deep-tail queues.
+// ===========================================================================
+constexpr int kCompactBlock = 256;
+constexpr int kCompactEPT = 4;
+constexpr int kCompactTile = kCompactBlock * kCompactEPT;
+
+__device__ __forceinline__ void queue_push(bool pred, int* counter, unsigned short* q,
+                                           unsigned short idx)
+{
+    const unsigned mask = __ballot_sync(0xffffffffu, pred);
+    if (mask == 0) return;
+    const unsigned lane = threadIdx.x & 31u;
+    const int leader = __ffs(mask) - 1;
+    int base = 0;
+    if ((int)lane == leader) base = atomicAdd(counter, __popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (pred) q[base + __popc(mask & ((1u << lane) - 1u))] = idx;
+}
+
+__global__ void __launch_bounds__(kCompactBlock)
+k_f64_compact(const double* __restrict__ in, double* out, size_t n)
+{
+    __shared__ unsigned short q_exp[kCompactTile];
+    __shared__ unsigned short q_deep[kCompactTile];
+    __shared__ int cnt[2];
+    const size_t ntiles = (n + kCompactTile - 1) / kCompactTile;
+    for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const size_t base = tile * kCompactTile;
+        if (threadIdx.x < 2) cnt[threadIdx.x] = 0;
+        __syncthreads();
+        double a[kCompactEPT];
+#pragma unroll
+        for (int k = 0; k < kCompactEPT; ++k) {
+            const size_t i = base + k * kCompactBlock + threadIdx.x;
+            a[k] = (i < n) ? __ldcs(in + i) : 0.5;
+        }
+#pragma unroll
+        for (int k = 0; k < kCompactEPT; ++k) {
+            const unsigned short li = (unsigned short)(k * kCompactBlock + threadIdx.x);
+            const size_t i = base + li;
+            const double u = a[k];
+            const double d = reflect_f64(u);
+            const bool edge = !(d > 0.0 && d <= 0.5);       // 0, NaN, out of range
+            const bool t2 = !edge && in_t2_domain(d);
+            const bool deep = !edge && !t2 && is_deep(d);
+            const bool ex = !edge && !t2 && !deep;
+            if (i < n && (t2 || edge)) {
+                const double m = t2 ? probit_mag_t2(t2_coord(d)) : 0.0;
+                __stcs(out + i, fix_edges_f64(u, d, m));
+            }
+            queue_push(i < n && ex, &cnt[0], q_exp, li);
+            queue_push(i < n && deep, &cnt[1], q_deep, li);
+        }
+        __syncthreads();
+        const int ne = cnt[0], nd = cnt[1];
+        for (int j = threadIdx.x; j < ne; j += kCompactBlock) {
+            const size_t i = base + q_exp[j];
+            const double u = in[i];
+            const double d = reflect_f64(u);
+            const double m = probit_mag_exp_main(-log(2.0 * d));
+            out[i] = fix_edges_f64(u, d, m);
+        }
+        for (int j = threadIdx.x; j < nd; j += kCompactBlock) {
+            const size_t i = base + q_deep[j];
+            const double u = in[i];
+            const double d = reflect_f64(u);
+            const double m = probit_mag_exp_deep(-log(2.0 * d));
+            out[i] = fix_edges_f64(u, d, m);
+        }
+        __syncthreads();
+    }
+}
+
+// ===========================================================================
+// Philox fill, 24-bit grid transform, fused generate + transform
+// ===========================================================================
+__device__ __forceinline__ uint32_t word_of(uint4 b, unsigned j)
+{
+    return j == 0 ? b.x : j == 1 ? b.y : j == 2 ? b.z : b.w;
+}
+
+__global__ void __launch_bounds__(256)
+k_philox_fill(uint64_t key, uint64_t ctr0, uint32_t* out, size_t n)
+{
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const uint64_t first_blk = ctr0 >> 2;
+    const unsigned off = (unsigned)(ctr0 & 3);
+    // thread t produces words of blocks first_blk + t, + stride, ...
+    const size_t nblk = (off + n + 3) / 4;
+    for (size_t b = (size_t)blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += stride) {
+        const uint4 w = philox_block(key, first_blk + b);
+#pragma unroll
+        for (unsigned j = 0; j < 4; ++j) {
+            const long long i = (long long)(b * 4 + j) - (long long)off;
+            if (i >= 0 && (size_t)i < n) out[i] = word_of(w, j);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_bits24_f32(const uint32_t* __restrict__ words, float* z, size_t n)
+{
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        z[i] = probit_grid24<FORM_SQRT>(words[i] >> 8);
+}
+
+// Per-block partial moments -> partials[blockIdx.x * 4 + k].
+__device__ __forceinline__ void block_reduce4(double s[4], double* partials)
+{
+    __shared__ double red[32][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int k = 0; k < 4; ++k) red[warp][k] = s[k];
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        for (int k = 0; k < 4; ++k) {
+            double v = lane < nw ? red[lane][k] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) partials[blockIdx.x * 4 + k] = v;
+        }
+    }
+}
+
+__global__ void k_sum_partials(const double* partials, int nblocks, double* moments)
+{
+    // one warp per moment, fixed summation order
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (k >= 4) return;
+    double v = 0.0;
+    for (int b = lane; b < nblocks; b += 32) v += partials[b * 4 + k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) moments[k] = v;
+}
+
+// Moments are accumulated per thread in FP32 over 16 samples (4 Philox
+// blocks), then folded into FP64 accumulators.
+template <bool OUT, bool MOM>
+__global__ void __launch_bounds__(256)
+k_fused_normal_f32(uint64_t key, uint64_t blk0, size_t n, float* out, double* partials)
+{
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t nblk = (n + 3) / 4;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    float f1 = 0.f, f2 = 0.f, f3 = 0.f, f4 = 0.f;
+    int cnt = 0;
+    const bool vec_ok = OUT && ((uintptr_t)out % 16 == 0);
+    for (size_t b = (size_t)blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += stride) {
+        const uint4 w = philox_block(key, blk0 + b);
+        float z[4];
+        z[0] = probit_grid24<FORM_SQRT>(w.x >> 8);
+        z[1] = probit_grid24<FORM_SQRT>(w.y >> 8);
+        z[2] = probit_grid24<FORM_SQRT>(w.z >> 8);
+        z[3] = probit_grid24<FORM_SQRT>(w.w >> 8);
+        const size_t i0 = b * 4;
+        const bool full = i0 + 4 <= n;
+        if (OUT) {
+            if (full && vec_ok) {
+                __stcs(reinterpret_cast<float4*>(out + i0), make_float4(z[0], z[1], z[2], z[3]));
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (i0 + j < n) out[i0 + j] = z[j];
+            }
+        }
+        if (MOM) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float x = (i0 + j < n) ? z[j] : 0.0f;
+                const float x2 = x * x;
+                f1 += x;
+                f2 += x2;
+                f3 = __fmaf_rn(x2, x, f3);
+                f4 = __fmaf_rn(x2, x2, f4);
+            }
+            if (++cnt == 4) {
+                acc[0] += f1; acc[1] += f2; acc[2] += f3; acc[3] += f4;
+                f1 = f2 = f3 = f4 = 0.f;
+                cnt = 0;
+            }
+        }
+    }
+    if (MOM) {
+        acc[0] += f1; acc[1] += f2; acc[2] += f3; acc[3] += f4;
+        block_reduce4(acc, partials);
+    }
+}
+
+// FP64 normal samples: block b gives two samples from 53-bit integers
+// k = (w0 >> 11) 2^32 + w1 and (w2 >> 11) 2^32 + w3, evaluated at the exact
+// reflected point d = (min(k, 2^53-1-k) + 1/2) 2^-53 with the t_2 / warp-vote
+// hybrid (Sec. 7.3).  KIND 0: normal; KIND 2: exponential -> normal with
+// x = -log((k + 1/2) 2^-53).
+__device__ __forceinline__ double half_open53(uint32_t hi, uint32_t lo, bool& upper)
+{
+    const uint64_t k = ((uint64_t)(hi >> 11) << 32) | lo;
+    upper = k >= (1ull << 52);
+    const uint64_t j = upper ? ((1ull << 53) - 1 - k) : k;
+    return ((double)j + 0.5) * 1.1102230246251565404e-16;   // 2^-53, exact
+}
+
+__device__ __forceinline__ double normal_from_d_vote(double d, bool upper, bool valid)
+{
+    const bool t2 = in_t2_domain(d) || !valid;
+    double m;
+    if (__all_sync(0xffffffffu, t2)) {
+        m = probit_mag_t2(t2_coord(d));
+    } else {
+        const double v = -log(2.0 * d);
+        m = probit_mag_exp_main(v);   // d >= 2^-54 here: v <= 36.7 < 42
+    }
+    return upper ? m : -m;
+}
+
+template <int KIND, bool OUT, bool MOM>
+__global__ void __launch_bounds__(256)
+k_fused_f64(uint64_t key, uint64_t blk0, size_t n, double* out, double* partials)
+{
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t nblk = (n + 1) / 2;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const size_t warp0 = (size_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+    const unsigned lane = threadIdx.x & 31u;
+    for (size_t wb = warp0; wb < nblk; wb += stride) {
+        const size_t b = wb + lane;
+        const bool valid = b < nblk;
+        const uint4 w = philox_block(key, blk0 + b);
+        double z[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            bool upper;
+            const double d = half_open53(h ? w.z : w.x, h ? w.w : w.y, upper);
+            if (KIND == 0) {
+                z[h] = normal_from_d_vote(d, upper, valid);
+            } else {
+                // x = -log(u), u = upper ? 1 - d : d, then the Sec. 6 map
+                const double x = upper ? -log1p(-d) : -log(d);
+                z[h] = ExpToNormal()(x);
+            }
+        }
+        const size_t i0 = b * 2;
+        if (OUT && valid) {
+            if (i0 + 2 <= n && ((uintptr_t)out % 16 == 0)) {
+                __stcs(reinterpret_cast<double2*>(out + i0), make_double2(z[0], z[1]));
+            } else {
+                for (int h = 0; h < 2; ++h)
+                    if (i0 + h < n) out[i0 + h] = z[h];
+            }
+        }
+        if (MOM && valid) {
+            for (int h = 0; h < 2; ++h) {
+                const double x = (i0 + h < n) ? z[h] : 0.0;
+                const double x2 = x * x;
+                acc[0] += x;
+                acc[1] += x2;
+                acc[2] += x2 * x;
+                acc[3] += x2 * x2;
+            }
+        }
+    }
+    if (MOM) block_reduce4(acc, partials);
+}
+
+// Per-device scratch for moment partials (allocated on first use).
+static double* partials_scratch(int nblocks)
+{
+    static std::mutex mu;
+    static double* ptr[64] = {nullptr};
+    static int cap[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (cap[dev] < nblocks) {
+        if (ptr[dev]) cudaFree(ptr[dev]);
+        ptr[dev] = nullptr;
+        cap[dev] = 0;
+        if (cudaMalloc(&ptr[dev], sizeof(double) * 4 * (size_t)nblocks) != cudaSuccess) return nullptr;
+        cap[dev] = nblocks;
+    }
+    return ptr[dev];
+}
+
+}  // namespace qm
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+using namespace qm;
+
+extern "C" const char* qm_last_error(void) { return g_last_error.c_str(); }
+extern "C" const char* qm_version(void) { return "qm 0.1 (sm_103a)"; }
+extern "C" int qm_sm_count(void) { return sm_count(); }
+
+extern "C" qm_status qm_normal_quantile_f32(const float* u, float* z, size_t n, int variant,
+                                           void* stream)
+{
+    if (n == 0) return QM_OK;
+    if (!u || !z) return fail(QM_ERR_INVALID, "qm_normal_quantile_f32: null pointer");
+    if (bad_overlap(u, n * 4, z, n * 4))
+        return fail(QM_ERR_INVALID, "qm_normal_quantile_f32: partially overlapping in/out");
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (variant) {
+    case QM_VAR_DEFAULT:
+    case QM_VAR_SQRT_FORM: return launch_map(u, z, n, F32Sqrt(), s, "f32 sqrt form");
+    case QM_VAR_BRANCHFREE: return launch_map(u, z, n, F32Paper(), s, "f32 branch-free");
+    case QM_VAR_CUDA_LIBM: return launch_map(u, z, n, F32Libm(), s, "f32 normcdfinvf");
+    default: return fail(QM_ERR_INVALID, "qm_normal_quantile_f32: variant %d not available in FP32", variant);
+    }
+}
+
+extern "C" qm_status qm_normal_quantile_f64(const double* u, double* z, size_t n, int variant,
+                                           void* stream)
+{
+    if (n == 0) return QM_OK;
+    if (!u || !z) return fail(QM_ERR_INVALID, "qm_normal_quantile_f64: null pointer");
+    if (bad_overlap(u, n * 8, z, n * 8))
+        return fail(QM_ERR_INVALID, "qm_normal_quantile_f64: partially overlapping in/out");
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (variant) {
+    case QM_VAR_BRANCHFREE: return launch_map(u, z, n, F64BranchFree(), s, "f64 branch-free");
+    case QM_VAR_MIXED_HALLEY: return launch_map(u, z, n, F64Mixed(), s, "f64 mixed");
+    case QM_VAR_CUDA_LIBM: return launch_map(u, z, n, F64Libm(), s, "f64 normcdfinv");
+    case QM_VAR_HYBRID_VOTE: {
+        const int g = grid_for(k_f64_hybrid_vote<2>, 256, (n + 1) / 2);
+        k_f64_hybrid_vote<2><<<g, 256, 0, s>>>(u, z, n);
+        return check_launch("f64 hybrid vote");
+    }
+    case QM_VAR_DEFAULT:
+    case QM_VAR_COMPACT: {
+        if (u == z) {
+            // the queues re-read the input after the in-place t_2 stores
+            const int g = grid_for(k_f64_hybrid_vote<2>, 256, (n + 1) / 2);
+            k_f64_hybrid_vote<2><<<g, 256, 0, s>>>(u, z, n);
+            return check_launch("f64 hybrid vote (in place)");
+        }
+        const size_t tiles = (n + kCompactTile - 1) / kCompactTile;
+        const int g = grid_for(k_f64_compact, kCompactBlock, tiles * kCompactBlock);
+        k_f64_compact<<<g, kCompactBlock, 0, s>>>(u, z, n);
+        return check_launch("f64 compact");
+    }
+    default: return fail(QM_ERR_INVALID, "qm_normal_quantile_f64: variant %d not available in FP64", variant);
+    }
+}
+
+extern "C" qm_status qm_normal_quantile_bits24_f32(const uint32_t* words, float* z, size_t n,
+                                                  void* stream)
+{
+    if (n == 0) return QM_OK;
+    if (!words || !z) return fail(QM_ERR_INVALID, "qm_normal_quantile_bits24_f32: null pointer");
+    if (bad_overlap(words, n * 4, z, n * 4))
+        return fail(QM_ERR_INVALID, "qm_normal_quantile_bits24_f32: partially overlapping in/out");
+    const int g = grid_for(k_bits24_f32, 256, n);
+    k_bits24_f32<<<g, 256, 0, (cudaStream_t)stream>>>(words, z, n);
+    return check_launch("bits24 f32");
+}
+
+extern "C" qm_status qm_philox_fill_u32(uint64_t key, uint64_t ctr0, uint32_t* out, size_t n,
+                                       void* stream)
+{
+    if (n == 0) return QM_OK;
+    if (!out) return fail(QM_ERR_INVALID, "qm_philox_fill_u32: null pointer");
+    const int g = grid_for(k_philox_fill, 256, (n + 3) / 4 + 1);
+    k_philox_fill<<<g, 256, 0, (cudaStream_t)stream>>>(key, ctr0, out, n);
+    return check_launch("philox fill");
+}
+
+extern "C" qm_status qm_sample_fused(int target, const qm_params* p, uint64_t key, uint64_t ctr0,
+                                    void* out, int out_is_f64, size_t n, double* moments4,
+                                    void* stream)
+{
+    (void)p;
+    if (n == 0) {
+        if (moments4) {
+            if (cudaMemsetAsync(moments4, 0, 4 * sizeof(double), (cudaStream_t)stream) != cudaSuccess)
+                return fail(QM_ERR_CUDA, "qm_sample_fused: memset failed");
+        }
+        return QM_OK;
+    }
+    if (!out && !moments4) return fail(QM_ERR_INVALID, "qm_sample_fused: no output requested");
+    if (ctr0 % 4 != 0) return fail(QM_ERR_INVALID, "qm_sample_fused: ctr0 must be a multiple of 4");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int B = 256;
+    if (target == QM_DIST_NORMAL && !out_is_f64) {
+        const size_t nblk = (n + 3) / 4;
+        int g;
+        double* part = nullptr;
+        if (moments4) {
+            g = grid_for(k_fused_normal_f32<true, true>, B, nblk);
+            part = partials_scratch(g);
+            if (!part) return fail(QM_ERR_NOMEM, "qm_sample_fused: scratch allocation failed");
+            if (out) k_fused_normal_f32<true, true><<<g, B, 0, s>>>(key, ctr0 / 4, n, (float*)out, part);
+            else k_fused_normal_f32<false, true><<<g, B, 0, s>>>(key, ctr0 / 4, n, nullptr, part);
+            k_sum_partials<<<1, 128, 0, s>>>(part, g, moments4);
+        } else {
+            g = grid_for(k_fused_normal_f32<true, false>, B, nblk);
+            k_fused_normal_f32<true, false><<<g, B, 0, s>>>(key, ctr0 / 4, n, (float*)out, nullptr);
+        }
+        return check_launch("fused normal f32");
+    }
+    if ((target == QM_DIST_NORMAL || target == QM_DIST_EXPONENTIAL) && out_is_f64) {
+        const size_t nblk = (n + 1) / 2;
+        const int g = grid_for(k_fused_f64<0, true, true>, B, nblk);
+        double* part = nullptr;
+        if (moments4) {
+            part = partials_scratch(g);
+            if (!part) return fail(QM_ERR_NOMEM, "qm_sample_fused: scratch allocation failed");
+        }
+        double* o = (double*)out;
+        const uint64_t b0 = ctr0 / 4;
+#define QM_LAUNCH_F64(KIND)                                                              \
+    if (o && part) k_fused_f64<KIND, true, true><<<g, B, 0, s>>>(key, b0, n, o, part);   \
+    else if (o) k_fused_f64<KIND, true, false><<<g, B, 0, s>>>(key, b0, n, o, nullptr);  \
+    else k_fused_f64<KIND, false, true><<<g, B, 0, s>>>(key, b0, n, nullptr, part);
+        if (target == QM_DIST_NORMAL) { QM_LAUNCH_F64(0) } else { QM_LAUNCH_F64(2) }
+#undef QM_LAUNCH_F64
+        if (part) k_sum_partials<<<1, 128, 0, s>>>(part, g, moments4);
+        return check_launch("fused f64");
+    }
+    if (target == QM_DIST_STUDENT_T)
+        return fail(QM_ERR_UNSUPPORTED, "qm_sample_fused: Student t target not built yet");
+    return fail(QM_ERR_INVALID, "qm_sample_fused: unsupported target/precision (%d, %d)", target, out_is_f64);
+}
+
+extern "C" qm_status qm_recycle(int src, int dst, const qm_params* p, const double* in, double* out,
+                               size_t n, void* stream)
+{
+    (void)p;
+    if (src == QM_DIST_EXPONENTIAL && dst == QM_DIST_NORMAL) {
+        if (n == 0) return QM_OK;
+        if (!in || !out) return fail(QM_ERR_INVALID, "qm_recycle: null pointer");
+        if (bad_overlap(in, n * 8, out, n * 8))
+            return fail(QM_ERR_INVALID, "qm_recycle: partially overlapping in/out");
+        return launch_map(in, out, n, ExpToNormal(), (cudaStream_t)stream, "recycle exp->normal");
+    }
+    if (src == QM_DIST_UNIFORM && dst == QM_DIST_NORMAL)
+        return qm_normal_quantile_f64(in, out, n, QM_VAR_DEFAULT, stream);
+    if (src == QM_DIST_NORMAL && dst == QM_DIST_STUDENT_T)
+        return fail(QM_ERR_UNSUPPORTED, "qm_recycle: normal->Student t not built yet");
+    return fail(QM_ERR_UNSUPPORTED, "qm_recycle: pair (%d -> %d) not supported", src, dst);
+}

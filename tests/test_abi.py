@@ -1,0 +1,43 @@
+"""CPU-side checks of the C-ABI boundary: the library builds for sm_103a,
+loads, exports every entry point include/*.h declares, and rejects bad
+arguments synchronously (no kernel is launched on these paths)."""
+import ctypes
+import subprocess
+
+import pytest
+
+import paper_0901_0638_gb300 as qm
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return qm.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = qm.declared_symbols()
+    assert "qm_normal_quantile_f32" in names and "qm_recycle" in names
+    out = subprocess.run(["nm", "-D", "--defined-only", qm.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        getattr(lib, n)
+
+
+def test_argument_errors_are_synchronous(lib):
+    vp = ctypes.c_void_p
+    assert lib.qm_normal_quantile_f32(None, None, 0, 0, None) == qm.QM_OK
+    assert lib.qm_normal_quantile_f32(None, vp(4096), 8, 0, None) == qm.QM_ERR_INVALID
+    assert "null" in qm.qm_last_error()
+    # partial overlap of in and out
+    assert lib.qm_normal_quantile_f64(vp(4096), vp(4096 + 8), 8, 0, None) == qm.QM_ERR_INVALID
+    assert "overlap" in qm.qm_last_error()
+    # a variant that does not exist in FP32
+    assert lib.qm_normal_quantile_f32(vp(4096), vp(8192), 4, qm.QM_VAR_HYBRID_VOTE, None) == qm.QM_ERR_INVALID
+    assert lib.qm_sample_fused(qm.QM_DIST_NORMAL, None, 1, 3, vp(4096), 0, 8, None, None) == qm.QM_ERR_INVALID
+    assert lib.qm_sample_fused(qm.QM_DIST_NORMAL, None, 1, 0, None, 0, 8, None, None) == qm.QM_ERR_INVALID
+    assert lib.qm_recycle(qm.QM_DIST_UNIFORM, qm.QM_DIST_EXPONENTIAL, None, vp(4096), vp(8192), 8,
+                          None) == qm.QM_ERR_UNSUPPORTED
+    assert lib.qm_philox_fill_u32(1, 0, None, 8, None) == qm.QM_ERR_INVALID

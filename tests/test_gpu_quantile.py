@@ -1,0 +1,254 @@
+"""GPU parity of the normal-quantile kernels against the CPU FP64 oracle.
+
+Tolerances (stated in the specification of this library):
+  FP32: |z - w| <= 4 ulp32(w), or <= 2e-7 absolute where |w| < 1e-2;
+  FP64: |z/w - 1| <= 4e-15 for u in [1e-300, 1 - 2^-53], w != 0;
+  results defined to be identical (symmetry pairs, fused vs unfused) must be
+  bit-identical.  Infinities, NaN and zero must be reproduced exactly.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_0901_0638_gb300 as qm
+from paper_0901_0638_gb300 import workloads as W
+from tests.gpu_util import f32_violations, f64_violations, max_ulp, rel_err
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+F32_VARIANTS = {"default": qm.QM_VAR_DEFAULT, "sqrt_form": qm.QM_VAR_SQRT_FORM}
+F64_VARIANTS = {"default": qm.QM_VAR_DEFAULT, "branchfree": qm.QM_VAR_BRANCHFREE,
+                "hybrid_vote": qm.QM_VAR_HYBRID_VOTE, "mixed_halley": qm.QM_VAR_MIXED_HALLEY,
+                "compact": qm.QM_VAR_COMPACT}
+
+
+def run_f32(u_host: np.ndarray, variant) -> np.ndarray:
+    u = torch.from_numpy(np.ascontiguousarray(u_host, dtype=np.float32)).to(DEV)
+    z = torch.empty_like(u)
+    qm.qm_normal_quantile_f32(u, z, variant)
+    torch.cuda.synchronize()
+    return z.cpu().numpy()
+
+
+def run_f64(u_host: np.ndarray, variant) -> np.ndarray:
+    u = torch.from_numpy(np.ascontiguousarray(u_host, dtype=np.float64)).to(DEV)
+    z = torch.empty_like(u)
+    qm.qm_normal_quantile_f64(u, z, variant)
+    torch.cuda.synchronize()
+    return z.cpu().numpy()
+
+
+# ------------------------------------------------------------------ FP32
+
+@pytest.fixture(scope="module")
+def cfg1():
+    """2^20 uniforms u = fl32((k + 1/2) 2^-24), k = top 24 bits of Philox
+    word i (seed 1)."""
+    k, u = W.uniform24(1, 1 << 20)
+    w = oracle.probit(u.double().numpy())
+    return k.numpy(), u.numpy(), w
+
+
+@pytest.mark.parametrize("name", list(F32_VARIANTS))
+def test_f32_float_array_cfg1(cfg1, name):
+    _, u, w = cfg1
+    z = run_f32(u, F32_VARIANTS[name])
+    bad = f32_violations(z, w)
+    print(f"{name}: max ulp {max_ulp(z, w):.3f}")
+    assert not bad.any(), (int(bad.sum()), u[bad][:5], z[bad][:5], w[bad][:5])
+
+
+def test_f32_paper_form_accuracy_reported(cfg1):
+    """The Sec. 6.1 single-precision form (degree (5,6) on v <= 25): its
+    rounding errors are reported; the bound asserted is the paper's realized
+    precision claim (relative error about 3.1e-7, Sec. 6.3)."""
+    _, u, w = cfg1
+    z = run_f32(u, qm.QM_VAR_BRANCHFREE)
+    r = rel_err(z, w)
+    fin = np.isfinite(w) & (np.abs(w) > 1e-2)
+    print(f"paper form: max ulp {max_ulp(z, w):.3f}, max rel {r[fin].max():.3g}")
+    assert r[fin].max() < 3.1e-7
+
+
+def test_f32_cuda_libm_comparator(cfg1):
+    _, u, w = cfg1
+    z = run_f32(u, qm.QM_VAR_CUDA_LIBM)
+    print(f"normcdfinvf: max ulp {max_ulp(z, w):.3f}")
+    assert np.all(np.isfinite(z[np.isfinite(w)]))
+
+
+def test_f32_full_24bit_grid_exact_reflection():
+    """Every point of the 24-bit grid through the exact reflected form
+    (words carry k in their top 24 bits)."""
+    j = np.arange(1 << 23, dtype=np.float64)
+    w_half = -oracle.probit((j + 0.5) * 2.0**-24)          # |w| for k < 2^23
+    k = torch.arange(1 << 24, dtype=torch.int64, device=DEV)
+    words = (k << 8).to(torch.int32)
+    z = torch.empty(1 << 24, dtype=torch.float32, device=DEV)
+    qm.qm_normal_quantile_bits24_f32(words, z)
+    z = z.cpu().numpy()
+    w = np.concatenate([-w_half, w_half[::-1]])
+    bad = f32_violations(z, w)
+    print(f"grid: max ulp {max_ulp(z, w):.3f}")
+    assert not bad.any(), int(bad.sum())
+    # exact oddness of the grid: k <-> 2^24 - 1 - k
+    assert np.array_equal(z[: 1 << 23], -z[::-1][: 1 << 23])
+
+
+def test_f32_random_float_bit_patterns():
+    """Uniformly random bit patterns of floats in (0, 1): every binade from
+    the subnormals up, so the tail pieces are exercised."""
+    rng = np.random.default_rng(11)
+    bits = rng.integers(1, 0x3F800000, size=1 << 20, dtype=np.uint32)
+    u = bits.view(np.float32)
+    u = np.concatenate([u, (1.0 - u[u > 2**-24]).astype(np.float32)])
+    w = oracle.probit(u.astype(np.float64))
+    z = run_f32(u, qm.QM_VAR_DEFAULT)
+    bad = f32_violations(z, w)
+    print(f"bit patterns: max ulp {max_ulp(z, w):.3f}")
+    assert not bad.any(), (int(bad.sum()), u[bad][:5], z[bad][:5], w[bad][:5])
+
+
+def test_f32_edges():
+    u = np.array([0.0, 1.0, 0.5, np.nan, -0.0, -1e-30, 1.0000001, np.inf, -np.inf,
+                  1.4e-45, 1.17549435e-38, 1 - 2**-24, 0.5 - 2**-25, 0.5 + 2**-24,
+                  0.25, 0.75, 7e-12, 6.9e-12], dtype=np.float32)
+    for v in (qm.QM_VAR_DEFAULT, qm.QM_VAR_BRANCHFREE):
+        z = run_f32(u, v)
+        assert z[0] == -np.inf and z[1] == np.inf
+        assert z[2] == 0.0 and np.signbit(z[2]) == False  # noqa: E712
+        assert np.isnan(z[3])
+        assert z[4] == -np.inf                           # -0.0 is 0
+        assert np.all(np.isnan(z[5:9]))
+    z = run_f32(u, qm.QM_VAR_DEFAULT)
+    w = oracle.probit(u[9:].astype(np.float64))
+    assert not f32_violations(z[9:], w).any(), (z[9:], w)
+
+
+def test_f32_symmetry_bit_exact():
+    rng = np.random.default_rng(3)
+    u = rng.uniform(0.25, 0.5, 1 << 18).astype(np.float32)
+    v = (1.0 - u).astype(np.float32)
+    assert np.array_equal((1.0 - v).astype(np.float32), u)   # exact pairs
+    a, b = run_f32(u, qm.QM_VAR_DEFAULT), run_f32(v, qm.QM_VAR_DEFAULT)
+    assert np.array_equal(a, -b)
+
+
+@pytest.mark.parametrize("n", [1, 3, 5, 31, 33, 1000003])
+def test_f32_ragged_and_misaligned(n):
+    rng = np.random.default_rng(n)
+    host = rng.random(n + 1).astype(np.float32)
+    buf = torch.from_numpy(host).to(DEV)
+    out = torch.zeros(n + 1, dtype=torch.float32, device=DEV)
+    qm.qm_normal_quantile_f32(buf[1:], out[1:], qm.QM_VAR_DEFAULT)   # 4-byte offset
+    ref = torch.empty(n, dtype=torch.float32, device=DEV)
+    qm.qm_normal_quantile_f32(buf[1:].clone(), ref, qm.QM_VAR_DEFAULT)
+    torch.cuda.synchronize()
+    assert out[0].item() == 0.0                                        # no overrun
+    assert torch.equal(out[1:], ref)
+    w = oracle.probit(host[1:].astype(np.float64))
+    assert not f32_violations(out[1:].cpu().numpy(), w).any()
+
+
+def test_f32_in_place():
+    k, u = W.uniform24(9, 4099)
+    t = u.clone().to(DEV)
+    ref = torch.empty_like(t)
+    qm.qm_normal_quantile_f32(t, ref, qm.QM_VAR_DEFAULT)
+    qm.qm_normal_quantile_f32(t, t, qm.QM_VAR_DEFAULT)
+    torch.cuda.synchronize()
+    assert torch.equal(t, ref)
+
+
+# ------------------------------------------------------------------ FP64
+
+@pytest.fixture(scope="module")
+def cfg2_small():
+    """2^21 doubles of the seed-2 mixture: 90% k 2^-53, 10% tail stress
+    2^-e m (e up to 990), mirrored with probability 1/2."""
+    u = W.mixture_f64(2, 1 << 21).numpy()
+    return u, oracle.probit(u)
+
+
+@pytest.mark.parametrize("name", list(F64_VARIANTS))
+def test_f64_mixture(cfg2_small, name):
+    u, w = cfg2_small
+    z = run_f64(u, F64_VARIANTS[name])
+    bad = f64_violations(z, w, 4e-15, u=u)
+    r = rel_err(z, w)
+    dom = (u >= 1e-300) & (u <= 1 - 2.0**-53)
+    print(f"{name}: max rel {r[dom].max():.3g}")
+    assert not bad.any(), (int(bad.sum()), u[bad][:5], z[bad][:5], w[bad][:5])
+
+
+def test_f64_cuda_libm_comparator(cfg2_small):
+    u, w = cfg2_small
+    z = run_f64(u, qm.QM_VAR_CUDA_LIBM)
+    r = rel_err(z, w)
+    dom = (u >= 1e-300) & (u <= 1 - 2.0**-53)
+    print(f"normcdfinv: max rel {r[dom].max():.3g}")
+
+
+def test_f64_deep_tail_and_edges():
+    e = np.arange(1, 1075)
+    u = np.concatenate([np.ldexp(0.75, -e), np.ldexp(0.5000001, -e)[:1070],
+                        [0.0, 1.0, 0.5, np.nan, -1e-300, 1.0 + 2**-52, np.inf, 1 - 2**-53,
+                         0.5 - 2**-54, 0.5 + 2**-53, 2.8748221264034482e-19,
+                         1.0373472162855378e-3, 1e-300]])
+    w = oracle.probit(u)
+    for name, v in F64_VARIANTS.items():
+        z = run_f64(u, v)
+        bad = f64_violations(z, w, 4e-15, u=u)
+        assert not bad.any(), (name, u[bad][:5], z[bad][:5], w[bad][:5])
+        # below 1e-300 (outside the stated domain): still close
+        sub = (u > 0) & (u < 1e-300)
+        assert np.all(rel_err(z[sub], w[sub]) < 1e-12), name
+
+
+def test_f64_symmetry_bit_exact():
+    rng = np.random.default_rng(5)
+    k = rng.integers(1, 2**52, size=1 << 18, dtype=np.int64)
+    u = k.astype(np.float64) * 2.0**-53
+    v = (2**53 - k).astype(np.float64) * 2.0**-53
+    for name in ("branchfree", "compact", "hybrid_vote", "mixed_halley"):
+        a = run_f64(u, F64_VARIANTS[name])
+        b = run_f64(v, F64_VARIANTS[name])
+        assert np.array_equal(a, -b), name
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 1023, 1025, 65537])
+def test_f64_ragged_misaligned_inplace(n):
+    u = W.mixture_f64(7, n + 1).numpy()
+    w = oracle.probit(u[1:])
+    for name, v in F64_VARIANTS.items():
+        buf = torch.from_numpy(u).to(DEV)
+        out = torch.zeros(n + 1, dtype=torch.float64, device=DEV)
+        qm.qm_normal_quantile_f64(buf[1:], out[1:], v)            # 8-byte offset
+        inplace = buf[1:].clone()
+        qm.qm_normal_quantile_f64(inplace, inplace, v)
+        torch.cuda.synchronize()
+        assert out[0].item() == 0.0
+        z = out[1:].cpu().numpy()
+        assert not f64_violations(z, w, 4e-15, u=u[1:]).any(), name
+        if name != "hybrid_vote":
+            zi = inplace.cpu().numpy()
+            assert not f64_violations(zi, w, 4e-15, u=u[1:]).any(), name
+
+
+def test_f64_full_size_sampled():
+    """The bench workload (2^28 doubles of the mixture, default variant) on the
+    device, checked against the oracle on 2^16 sampled outputs."""
+    n = 1 << 28
+    u = W.mixture_f64(2, n, device=DEV)
+    z = torch.empty_like(u)
+    qm.qm_normal_quantile_f64(u, z, qm.QM_VAR_DEFAULT)
+    torch.cuda.synchronize()
+    idx = torch.from_numpy(np.random.default_rng(2).integers(0, n, 1 << 16)).to(DEV)
+    us = u[idx].cpu().numpy()
+    zs = z[idx].cpu().numpy()
+    w = oracle.probit(us)
+    assert not f64_violations(zs, w, 4e-15, u=us).any()
+    del u, z
+    torch.cuda.empty_cache()
