@@ -68,7 +68,12 @@ typedef enum {
                                 evaluated densely in the exponential form       */
     QM_VAR_SQRT_FORM = 5,    /* FP32: exponential coordinate with a two-float
                                 logarithm, z = v sqrt(R(v)), R = (Q(v)/v)^2     */
-    QM_VAR_CUDA_LIBM = 6     /* comparator: CUDA's normcdfinvf / normcdfinv     */
+    QM_VAR_CUDA_LIBM = 6,    /* comparator: CUDA's normcdfinvf / normcdfinv     */
+    QM_VAR_TABLE = 7         /* exponential coordinate without log or divide:
+                                x = 2d = 2^E m, segment (E, top bits of m),
+                                r = m c - 1, |z| = local expansion G(r) of Q(v)
+                                from the recycling ODE (FP64: d >= 2^-65, the
+                                deep tail compacted to the deep rational)       */
 } qm_variant;
 
 typedef struct {

@@ -77,6 +77,7 @@ bool bad_overlap(const void* a, size_t abytes, const void* b, size_t bbytes)
 struct F32Sqrt   { __device__ float operator()(float u) const { return probit_f32<FORM_SQRT>(u); } };
 struct F32Paper  { __device__ float operator()(float u) const { return probit_f32<FORM_PAPER>(u); } };
 struct F32Libm   { __device__ float operator()(float u) const { return normcdfinvf(u); } };
+struct F32Table  { __device__ float operator()(float u) const { return probit_f32_tbl(u); } };
 
 struct F64BranchFree {
     __device__ double operator()(double u) const
@@ -311,6 +312,65 @@ k_f64_compact(const double* __restrict__ in, double* out, size_t n)
             const double m = probit_mag_exp_main(-log(2.0 * d));
             out[i] = fix_edges_f64(u, d, m);
         }
+        for (int j = threadIdx.x; j < nd; j += kCompactBlock) {
+            const size_t i = base + q_deep[j];
+            const double u = in[i];
+            const double d = reflect_f64(u);
+            const double m = probit_mag_exp_deep(-log(2.0 * d));
+            out[i] = fix_edges_f64(u, d, m);
+        }
+        __syncthreads();
+    }
+}
+
+// ===========================================================================
+// FP64 TABLE: table-driven exponential coordinate for d >= 2^-65, the deep
+// tail compacted per tile and evaluated densely with the deep rational.
+// Reflection, domain tests and the sign use integer operations on the bits
+// (the FP64 pipe is the bottleneck on this part).
+// ===========================================================================
+__global__ void __launch_bounds__(kCompactBlock)
+k_f64_table(const double* __restrict__ in, double* out, size_t n)
+{
+    __shared__ unsigned short q_deep[kCompactTile];
+    __shared__ int cnt;
+    const size_t ntiles = (n + kCompactTile - 1) / kCompactTile;
+    for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const size_t base = tile * kCompactTile;
+        if (threadIdx.x == 0) cnt = 0;
+        __syncthreads();
+        double a[kCompactEPT];
+#pragma unroll
+        for (int k = 0; k < kCompactEPT; ++k) {
+            const size_t i = base + k * kCompactBlock + threadIdx.x;
+            a[k] = (i < n) ? __ldcs(in + i) : 0.5;
+        }
+#pragma unroll
+        for (int k = 0; k < kCompactEPT; ++k) {
+            const unsigned short li = (unsigned short)(k * kCompactBlock + threadIdx.x);
+            const size_t i = base + li;
+            const double u = a[k];
+            const long long ub = __double_as_longlong(u);
+            const bool upper = ub >= 0x3FE0000000000000ll;                // u >= 1/2
+            const bool valid = ub > 0 && ub < 0x3FF0000000000000ll;       // 0 < u < 1
+            const double d = upper ? __dadd_rn(1.0, -u) : u;
+            const bool covers = valid && __double_as_longlong(d) >= 0x3BE0000000000000ll;  // 2^-65
+            if (i < n && !(valid && !covers)) {
+                double m = covers ? probit_mag_f64_tbl(d) : 0.0;
+                long long mb = __double_as_longlong(fabs(m));
+                if (!valid) {
+                    const bool zero = (ub & 0x7fffffffffffffffll) == 0;
+                    mb = zero ? (0x7ff0000000000000ll | (1ll << 63))
+                              : (ub == 0x3FF0000000000000ll ? 0x7ff0000000000000ll : 0x7ff8000000000000ll);
+                } else if (!upper) {
+                    mb |= (1ll << 63);
+                }
+                __stcs(out + i, __longlong_as_double(mb));
+            }
+            queue_push(i < n && valid && !covers, &cnt, q_deep, li);
+        }
+        __syncthreads();
+        const int nd = cnt;
         for (int j = threadIdx.x; j < nd; j += kCompactBlock) {
             const size_t i = base + q_deep[j];
             const double u = in[i];
@@ -559,6 +619,7 @@ extern "C" qm_status qm_normal_quantile_f32(const float* u, float* z, size_t n, 
     case QM_VAR_SQRT_FORM: return launch_map(u, z, n, F32Sqrt(), s, "f32 sqrt form");
     case QM_VAR_BRANCHFREE: return launch_map(u, z, n, F32Paper(), s, "f32 branch-free");
     case QM_VAR_CUDA_LIBM: return launch_map(u, z, n, F32Libm(), s, "f32 normcdfinvf");
+    case QM_VAR_TABLE: return launch_map(u, z, n, F32Table(), s, "f32 table");
     default: return fail(QM_ERR_INVALID, "qm_normal_quantile_f32: variant %d not available in FP32", variant);
     }
 }
@@ -579,6 +640,16 @@ extern "C" qm_status qm_normal_quantile_f64(const double* u, double* z, size_t n
         const int g = grid_for(k_f64_hybrid_vote<2>, 256, (n + 1) / 2);
         k_f64_hybrid_vote<2><<<g, 256, 0, s>>>(u, z, n);
         return check_launch("f64 hybrid vote");
+    }
+    case QM_VAR_TABLE: {
+        if (u == z) {
+            // the deep-tail queue re-reads the input after in-place stores
+            return launch_map(u, z, n, F64BranchFree(), s, "f64 branch-free (in place)");
+        }
+        const size_t tiles = (n + kCompactTile - 1) / kCompactTile;
+        const int g = grid_for(k_f64_table, kCompactBlock, tiles * kCompactBlock);
+        k_f64_table<<<g, kCompactBlock, 0, s>>>(u, z, n);
+        return check_launch("f64 table");
     }
     case QM_VAR_DEFAULT:
     case QM_VAR_COMPACT: {

@@ -1,0 +1,128 @@
+"""Generate csrc/qm_tables.h: segment tables of the table-driven normal quantile.
+
+The quantile is evaluated in the paper's exponential coordinate
+v = -log(2d), d = min(u, 1-u) (Sec. 6), but the logarithm is never formed.
+Write x = 2d = 2^E m with m in [1, 2); the top k bits of m pick a segment j
+with a short reduction constant c_j ~ 1/(segment centre) (c = 1/2 for the top
+segment, which makes r exact at the centre of the distribution), and
+
+    r = m c_j - 1,       v = V_{E,j} - log(1 + r),  V_{E,j} = -E ln2 + ln c_j.
+
+Around V the function Q(v) = Phi^{-1}(1 - e^{-v}/2) is expanded with the
+recycling ODE of the exponential background, Q'' + Q' = Q Q'^2 (Sec. 2.3,
+Sec. 6; rode.taylor_exp_background), and composed with -log(1 + r), giving
+per segment the Taylor coefficients of G(r) = Q(V - log(1 + r)).  A kernel
+evaluates |Phi^{-1}(u)| = G(r) with a short Horner chain: no logarithm, no
+division.
+
+FP64 table: E = -1 .. -64 (v <= 44.4), k = 5 (32 segments per binade);
+  entry = a0..a5, c (double) | a6 a7 (float)            -- 64 bytes.
+  (a0..a5 are evaluated in double, a6 a7 in single precision: their terms
+  are below 1e-12 of the result.)
+FP32 table: E = -1 .. -149, k = 4 (16 segments per binade);
+  entry = c, a0..a5, 0 (float)                           -- 32 bytes.
+Usage:  python -m paper_0901_0638_gb300.fit.gen_tables
+"""
+from __future__ import annotations
+
+import multiprocessing as mproc
+import os
+import sys
+
+import mpmath as mp
+import numpy as np
+
+from . import rode
+from . import targets as T
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+OUT = os.path.join(os.path.dirname(HERE), "csrc", "qm_tables.h")
+
+F64_K, F64_EMIN, F64_DEG = 5, -64, 7
+F32_K, F32_EMIN, F32_DEG = 4, -149, 5
+
+
+def seg_const(j, k):
+    if j == 2**k - 1:
+        return 0.5
+    lo = 1.0 + j / 2.0**k
+    hi = 1.0 + (j + 1) / 2.0**k
+    c = 2.0 / (lo + hi)
+    return float(np.float32(float(np.float32(c))))  # a float, exact in double
+
+
+def seg_coeffs(args):
+    E, j, k, deg = args
+    mp.mp.dps = 45
+    c = mp.mpf(seg_const(j, k))
+    V = -E * mp.log(2) + mp.log(c)
+    if E == -1 and j == 2**k - 1:
+        V = mp.mpf(0)
+        q0, q1 = mp.mpf(0), mp.sqrt(mp.pi / 2)
+    else:
+        q0 = T.q_exp(V)
+        q1 = mp.exp(-V) / 2 / mp.npdf(q0)      # Q' = (e^{-v}/2) / phi(Q)
+    b = rode.taylor_exp_background(V, q0, q1, deg + 2)
+    a = rode.compose(b, rode.neg_log1p_series(deg + 2), deg + 2)
+    # check: evaluate the truncated, rounded polynomial at the segment ends
+    mlo = 1 + mp.mpf(j) / 2**k
+    mhi = 1 + mp.mpf(j + 1) / 2**k
+    worst = mp.mpf(0)
+    for m in (mlo, (mlo + mhi) / 2, mhi - mp.mpf(2) ** -40):
+        r = m * c - 1
+        x = m * mp.mpf(2) ** E
+        ref = T.q_exp(-mp.log(x)) if x != 1 else mp.mpf(0)
+        approx = sum(a[n] * r**n for n in range(deg + 1))
+        if ref != 0:
+            worst = max(worst, abs(approx / ref - 1))
+    return (E, j, float(c), [a[n] for n in range(deg + 1)], float(worst))
+
+
+def hexd(x):
+    return float(x).hex()
+
+
+def hexf(x):
+    return float(np.float32(float(x))).hex() + "f"
+
+
+def main():
+    jobs64 = [(E, j, F64_K, F64_DEG) for E in range(-1, F64_EMIN - 1, -1) for j in range(2**F64_K)]
+    jobs32 = [(E, j, F32_K, F32_DEG) for E in range(-1, F32_EMIN - 1, -1) for j in range(2**F32_K)]
+    with mproc.Pool(max(1, (os.cpu_count() or 2))) as pool:
+        r64 = pool.map(seg_coeffs, jobs64, chunksize=16)
+        r32 = pool.map(seg_coeffs, jobs32, chunksize=16)
+    w64 = max(r[4] for r in r64)
+    w32 = max(r[4] for r in r32)
+    print(f"FP64 table: {len(r64)} segments, truncation <= {w64:.3g}", file=sys.stderr)
+    print(f"FP32 table: {len(r32)} segments, truncation <= {w32:.3g}", file=sys.stderr)
+    lines = [
+        "// Generated by paper_0901_0638_gb300/fit/gen_tables.py -- do not edit.\n",
+        "// Segment tables of the table-driven normal quantile: per segment (E, j)\n",
+        "// of x = 2d = 2^E m, the Taylor coefficients in r = m c - 1 of\n",
+        "// G(r) = Q(V - log(1+r)), Q the exponential-coordinate normal quantile,\n",
+        "// obtained from the recycling ODE Q'' + Q' = Q Q'^2.  Index (-1-E) 2^k + j.\n",
+        f"// FP64: k = {F64_K}, E = -1..{F64_EMIN}, degree {F64_DEG}, max truncation {w64:.3g}.\n",
+        f"// FP32: k = {F32_K}, E = -1..{F32_EMIN}, degree {F32_DEG}, max truncation {w32:.3g}.\n",
+        "#pragma once\n\nnamespace qm {\nnamespace tbl {\n\n",
+        f"constexpr int F64_K = {F64_K};\nconstexpr int F64_EMIN = {F64_EMIN};\n",
+        f"constexpr int F32_K = {F32_K};\nconstexpr int F32_EMIN = {F32_EMIN};\n\n",
+        "struct alignas(64) SegF64 { double a[6]; double c; float b6, b7; };\n",
+        "struct alignas(32) SegF32 { float c, a0, a1, a2, a3, a4, a5, pad; };\n\n",
+        f"__device__ const SegF64 SEG_F64[{len(r64)}] = {{\n",
+    ]
+    for E, j, c, a, _ in r64:
+        lines.append("  {{" + ",".join(hexd(x) for x in a[:6]) + "}," + hexd(c) + "," +
+                     ",".join(hexf(x) for x in a[6:8]) + "},\n")
+    lines.append("};\n\n")
+    lines.append(f"__device__ const SegF32 SEG_F32[{len(r32)}] = {{\n")
+    for E, j, c, a, _ in r32:
+        lines.append("  {" + hexf(c) + "," + ",".join(hexf(x) for x in a[:6]) + ",0.0f},\n")
+    lines.append("};\n\n}  // namespace tbl\n}  // namespace qm\n")
+    with open(OUT, "w") as f:
+        f.write("".join(lines))
+    print("wrote", OUT, file=sys.stderr)
+
+
+if __name__ == "__main__":
+    main()

@@ -49,5 +49,5 @@ def f64_violations(z, w, tol, u=None, lo=1e-300, hi=1.0 - 2.0**-53):
     if u is not None:
         u = np.asarray(u, dtype=np.float64)
         m &= (u >= lo) & (u <= hi)
-    bad[m] = np.abs(z[m] / w[m] - 1.0) > tol
+    bad[m] = ~(np.abs(z[m] / w[m] - 1.0) <= tol)   # NaN counts as a miss
     return bad

@@ -84,7 +84,13 @@ def test_fused_f64_normal_and_exponential():
     torch.cuda.synchronize()
     x = np.where(upper, -np.log1p(-d), -np.log(d))
     w = oracle.recycle_exp(x)
-    assert not f64_violations(out.cpu().numpy(), w, 1e-12).any()
+    z = out.cpu().numpy()
+    # x is formed on the device with its own log/log1p (within an ulp or so of
+    # numpy's); the map's slope dz/dx = e^{-x}/phi(z) turns that into an
+    # absolute difference, which dominates where z is near 0 (x near ln 2).
+    slope = np.exp(-x) / (np.exp(-0.5 * w * w) / np.sqrt(2 * np.pi))
+    tol = 1e-12 * np.abs(w) + 4 * 2.2e-16 * x * slope
+    assert np.all(np.abs(z - w) <= tol)
 
 
 def test_recycle_exp_to_normal():
