@@ -54,7 +54,7 @@ typedef enum {
 
 /* Algorithm variants of the normal quantile. */
 typedef enum {
-    QM_VAR_DEFAULT = 0,      /* FP32: SQRT_FORM.  FP64: COMPACT.                 */
+    QM_VAR_DEFAULT = 0,      /* TABLE (FP32 and FP64)                           */
     QM_VAR_BRANCHFREE = 1,   /* exponential coordinate, one rational for the
                                 whole range (FP32: Sec. 6.1 form z = v P/Q on
                                 v <= 25; FP64: Sec. 7.2 form on v <= 42 plus a
@@ -82,8 +82,9 @@ typedef struct {
 
 /* ---- normal quantile ------------------------------------------------------
  * z[i] = Phi^{-1}(u[i]) for i < n (Sec. 1, Eq. 1).  FP32 variants: DEFAULT,
- * BRANCHFREE, SQRT_FORM, CUDA_LIBM; FP64 variants: DEFAULT, BRANCHFREE,
- * HYBRID_VOTE, MIXED_HALLEY, COMPACT, CUDA_LIBM (others: QM_ERR_INVALID).
+ * BRANCHFREE, SQRT_FORM, TABLE, CUDA_LIBM; FP64 variants: DEFAULT, BRANCHFREE,
+ * HYBRID_VOTE, MIXED_HALLEY, COMPACT, TABLE, CUDA_LIBM (others:
+ * QM_ERR_INVALID).
  * u, z: contiguous arrays of n elements (device).                           */
 qm_status qm_normal_quantile_f32(const float* u, float* z, size_t n,
                                  int variant, void* stream);
@@ -92,7 +93,8 @@ qm_status qm_normal_quantile_f64(const double* u, double* z, size_t n,
 
 /* z[i] = Phi^{-1}((k + 1/2) 2^-24) with k = words[i] >> 8 (the top 24 bits),
  * evaluated in the exact reflected form d = (min(k, 2^24-1-k) + 1/2) 2^-24
- * (Sec. 6.1, the "better" reflection).  words: uint32[n], z: float[n].      */
+ * (Sec. 6.1, the "better" reflection) with the TABLE form.
+ * words: uint32[n], z: float[n].                                            */
 qm_status qm_normal_quantile_bits24_f32(const uint32_t* words, float* z,
                                         size_t n, void* stream);
 

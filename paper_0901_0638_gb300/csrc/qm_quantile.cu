@@ -357,7 +357,7 @@ k_f64_table(const double* __restrict__ in, double* out, size_t n)
             const bool covers = valid && __double_as_longlong(d) >= 0x3BE0000000000000ll;  // 2^-65
             if (i < n && !(valid && !covers)) {
                 double m = covers ? probit_mag_f64_tbl(d) : 0.0;
-                long long mb = __double_as_longlong(fabs(m));
+                long long mb = __double_as_longlong(m) & 0x7fffffffffffffffll;
                 if (!valid) {
                     const bool zero = (ub & 0x7fffffffffffffffll) == 0;
                     mb = zero ? (0x7ff0000000000000ll | (1ll << 63))
@@ -413,7 +413,7 @@ k_bits24_f32(const uint32_t* __restrict__ words, float* z, size_t n)
 {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-        z[i] = probit_grid24<FORM_SQRT>(words[i] >> 8);
+        z[i] = probit_grid24_tbl(words[i] >> 8);
 }
 
 // Per-block partial moments -> partials[blockIdx.x * 4 + k].
@@ -463,10 +463,10 @@ k_fused_normal_f32(uint64_t key, uint64_t blk0, size_t n, float* out, double* pa
     for (size_t b = (size_t)blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += stride) {
         const uint4 w = philox_block(key, blk0 + b);
         float z[4];
-        z[0] = probit_grid24<FORM_SQRT>(w.x >> 8);
-        z[1] = probit_grid24<FORM_SQRT>(w.y >> 8);
-        z[2] = probit_grid24<FORM_SQRT>(w.z >> 8);
-        z[3] = probit_grid24<FORM_SQRT>(w.w >> 8);
+        z[0] = probit_grid24_tbl(w.x >> 8);
+        z[1] = probit_grid24_tbl(w.y >> 8);
+        z[2] = probit_grid24_tbl(w.z >> 8);
+        z[3] = probit_grid24_tbl(w.w >> 8);
         const size_t i0 = b * 4;
         const bool full = i0 + 4 <= n;
         if (OUT) {
@@ -615,10 +615,10 @@ extern "C" qm_status qm_normal_quantile_f32(const float* u, float* z, size_t n, 
         return fail(QM_ERR_INVALID, "qm_normal_quantile_f32: partially overlapping in/out");
     cudaStream_t s = (cudaStream_t)stream;
     switch (variant) {
-    case QM_VAR_DEFAULT:
     case QM_VAR_SQRT_FORM: return launch_map(u, z, n, F32Sqrt(), s, "f32 sqrt form");
     case QM_VAR_BRANCHFREE: return launch_map(u, z, n, F32Paper(), s, "f32 branch-free");
     case QM_VAR_CUDA_LIBM: return launch_map(u, z, n, F32Libm(), s, "f32 normcdfinvf");
+    case QM_VAR_DEFAULT:
     case QM_VAR_TABLE: return launch_map(u, z, n, F32Table(), s, "f32 table");
     default: return fail(QM_ERR_INVALID, "qm_normal_quantile_f32: variant %d not available in FP32", variant);
     }
@@ -641,6 +641,7 @@ extern "C" qm_status qm_normal_quantile_f64(const double* u, double* z, size_t n
         k_f64_hybrid_vote<2><<<g, 256, 0, s>>>(u, z, n);
         return check_launch("f64 hybrid vote");
     }
+    case QM_VAR_DEFAULT:
     case QM_VAR_TABLE: {
         if (u == z) {
             // the deep-tail queue re-reads the input after in-place stores
@@ -651,7 +652,6 @@ extern "C" qm_status qm_normal_quantile_f64(const double* u, double* z, size_t n
         k_f64_table<<<g, kCompactBlock, 0, s>>>(u, z, n);
         return check_launch("f64 table");
     }
-    case QM_VAR_DEFAULT:
     case QM_VAR_COMPACT: {
         if (u == z) {
             // the queues re-read the input after the in-place t_2 stores

@@ -19,8 +19,11 @@ FP64 table: E = -1 .. -64 (v <= 44.4), k = 5 (32 segments per binade);
   entry = a0..a5, c (double) | a6 a7 (float)            -- 64 bytes.
   (a0..a5 are evaluated in double, a6 a7 in single precision: their terms
   are below 1e-12 of the result.)
-FP32 table: E = -1 .. -149, k = 4 (16 segments per binade);
-  entry = c, a0..a5, 0 (float)                           -- 32 bytes.
+FP32 table: E = -1 .. -149, k = 5 (32 segments per binade), with the
+  subtractive reduction r = m - m_j (m_j the segment centre, or 2 for the top
+  segment, where r = 2x - 2 is exact and G(0) = 0 at u = 1/2), so
+  G(r) = Q(V - log(1 + r/m_j)), V = -E ln2 - ln m_j;
+  entry = a0..a3 (float)                                 -- 16 bytes, one load.
 Usage:  python -m paper_0901_0638_gb300.fit.gen_tables
 """
 from __future__ import annotations
@@ -39,7 +42,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(os.path.dirname(HERE), "csrc", "qm_tables.h")
 
 F64_K, F64_EMIN, F64_DEG = 5, -64, 7
-F32_K, F32_EMIN, F32_DEG = 4, -149, 5
+F32_K, F32_EMIN, F32_DEG = 5, -149, 3
 
 
 def seg_const(j, k):
@@ -78,6 +81,35 @@ def seg_coeffs(args):
     return (E, j, float(c), [a[n] for n in range(deg + 1)], float(worst))
 
 
+def seg_coeffs_sub(args):
+    """FP32 segments: subtractive reduction r = m - m_j."""
+    E, j, k, deg = args
+    mp.mp.dps = 45
+    top = j == 2**k - 1
+    mj = mp.mpf(2) if top else 1 + (mp.mpf(j) + mp.mpf("0.5")) / 2**k
+    V = -E * mp.log(2) - mp.log(mj)
+    if E == -1 and top:
+        V = mp.mpf(0)
+        q0, q1 = mp.mpf(0), mp.sqrt(mp.pi / 2)
+    else:
+        q0 = T.q_exp(V)
+        q1 = mp.exp(-V) / 2 / mp.npdf(q0)
+    b = rode.taylor_exp_background(V, q0, q1, deg + 2)
+    s = [mp.mpf(0)] + [mp.mpf((-1) ** n) / n / mj**n for n in range(1, deg + 3)]  # -log(1 + r/mj)
+    a = rode.compose(b, s, deg + 2)
+    mlo = 1 + mp.mpf(j) / 2**k
+    mhi = 1 + mp.mpf(j + 1) / 2**k
+    worst = mp.mpf(0)
+    for m in (mlo, (mlo + mhi) / 2, mhi - mp.mpf(2) ** -30):
+        r = m - mj
+        x = m * mp.mpf(2) ** E
+        ref = T.q_exp(-mp.log(x)) if x != 1 else mp.mpf(0)
+        approx = sum(a[n] * r**n for n in range(deg + 1))
+        if ref != 0:
+            worst = max(worst, abs(approx / ref - 1))
+    return (E, j, float(mj), [a[n] for n in range(deg + 1)], float(worst))
+
+
 def hexd(x):
     return float(x).hex()
 
@@ -91,7 +123,7 @@ def main():
     jobs32 = [(E, j, F32_K, F32_DEG) for E in range(-1, F32_EMIN - 1, -1) for j in range(2**F32_K)]
     with mproc.Pool(max(1, (os.cpu_count() or 2))) as pool:
         r64 = pool.map(seg_coeffs, jobs64, chunksize=16)
-        r32 = pool.map(seg_coeffs, jobs32, chunksize=16)
+        r32 = pool.map(seg_coeffs_sub, jobs32, chunksize=16)
     w64 = max(r[4] for r in r64)
     w32 = max(r[4] for r in r32)
     print(f"FP64 table: {len(r64)} segments, truncation <= {w64:.3g}", file=sys.stderr)
@@ -108,7 +140,7 @@ def main():
         f"constexpr int F64_K = {F64_K};\nconstexpr int F64_EMIN = {F64_EMIN};\n",
         f"constexpr int F32_K = {F32_K};\nconstexpr int F32_EMIN = {F32_EMIN};\n\n",
         "struct alignas(64) SegF64 { double a[6]; double c; float b6, b7; };\n",
-        "struct alignas(32) SegF32 { float c, a0, a1, a2, a3, a4, a5, pad; };\n\n",
+        "struct alignas(16) SegF32 { float a0, a1, a2, a3; };\n\n",
         f"__device__ const SegF64 SEG_F64[{len(r64)}] = {{\n",
     ]
     for E, j, c, a, _ in r64:
@@ -117,7 +149,7 @@ def main():
     lines.append("};\n\n")
     lines.append(f"__device__ const SegF32 SEG_F32[{len(r32)}] = {{\n")
     for E, j, c, a, _ in r32:
-        lines.append("  {" + hexf(c) + "," + ",".join(hexf(x) for x in a[:6]) + ",0.0f},\n")
+        lines.append("  {" + ",".join(hexf(x) for x in a[:4]) + "},\n")
     lines.append("};\n\n}  // namespace tbl\n}  // namespace qm\n")
     with open(OUT, "w") as f:
         f.write("".join(lines))
