@@ -124,6 +124,27 @@ qm_status qm_sample_fused(int target, const qm_params* p, uint64_t key,
                           uint64_t ctr0, void* out, int out_is_f64, size_t n,
                           double* moments4, void* stream);
 
+/* ---- fused moments without allocation ---------------------------------------
+ * Same sums as qm_sample_fused(QM_DIST_NORMAL, NULL, key, ctr0, NULL, 0, n,
+ * moments4, stream) (up to the order of the FP64 additions), for callers that
+ * must not allocate device memory at call time: inside a stream capture or a
+ * stream-ordered pipeline that cannot synchronise, in allocator-less runtimes,
+ * or in callbacks running while a caching allocator is locked.  The paper has
+ * no counterpart; this is a property of the library interface.
+ * Scratch is a file-scope device array of 16384 x 4 doubles (512 KiB) that
+ * every device loading the library keeps until the process exits; a call
+ * makes no cudaMalloc/cudaFree and no allocating library call.
+ * n <= 2^32 (16384 blocks of 2^18 samples); larger n returns QM_ERR_INVALID
+ * with a message.  ctr0 must be a multiple of 4.  moments4: double[4]
+ * (device), overwritten.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  All calls share the one array:
+ * calls that overlap on the GPU (different streams, no ordering) race and
+ * give wrong moments; calls ordered on one stream are safe.  Each call
+ * overwrites every scratch slot it reads, so nothing is cleared between calls. */
+qm_status qm_sample_moments_noalloc(uint64_t key, uint64_t ctr0, size_t n,
+                                    double* moments4, void* stream);
+
 /* ---- recycling maps Q = F^{-1}(G(x)) (Sec. 2.1) -----------------------------
  * Supported (src, dst): (NORMAL, STUDENT_T): out = F_nu^{-1}(Phi(in))
  * (Sec. 3; nu in {1,2,3,4,5,8,10,30}, p->nu required);

@@ -51,6 +51,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "qm_philox_fill_u32": [u64, u64, vp, sz, vp],
         "qm_sample_fused": [i, vp, u64, u64, vp, i, sz, vp, vp],
         "qm_recycle": [i, i, vp, vp, vp, sz, vp],
+        "qm_sample_moments_noalloc": [u64, u64, sz, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -140,6 +141,11 @@ def qm_sample_fused(target: int, key: int, ctr0: int, out=None, out_is_f64: bool
     _check(load().qm_sample_fused(target, _params(nu), key, ctr0, _ptr(out), int(out_is_f64), n,
                                   _ptr(moments4), _stream(stream, ref)))
     return out
+
+
+def qm_sample_moments_noalloc(key: int, ctr0: int, n: int, moments4, stream=None):
+    _check(load().qm_sample_moments_noalloc(key, ctr0, n, _ptr(moments4), _stream(stream, moments4)))
+    return moments4
 
 
 def qm_recycle(src: int, dst: int, inp, out, nu=None, n=None, stream=None):
