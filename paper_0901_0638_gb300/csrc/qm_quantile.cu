@@ -124,6 +124,19 @@ struct ExpToNormal {
     }
 };
 
+struct TMap {
+    int k;
+    __device__ double operator()(double z) const { return recycle_t(k, z); }
+};
+
+// index of nu in the tabulated set, or -1
+static int t_index(double nu)
+{
+    for (int i = 0; i < ttbl::NNU; ++i)
+        if (nu == ttbl::T_NU[i]) return i;
+    return -1;
+}
+
 // ===========================================================================
 // Generic streaming map
 // ===========================================================================
@@ -529,7 +542,7 @@ __device__ __forceinline__ double normal_from_d_vote(double d, bool upper, bool 
 
 template <int KIND, bool OUT, bool MOM>
 __global__ void __launch_bounds__(256)
-k_fused_f64(uint64_t key, uint64_t blk0, size_t n, double* out, double* partials)
+k_fused_f64(uint64_t key, uint64_t blk0, size_t n, double* out, double* partials, int tk)
 {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     const size_t nblk = (n + 1) / 2;
@@ -547,6 +560,10 @@ k_fused_f64(uint64_t key, uint64_t blk0, size_t n, double* out, double* partials
             const double d = half_open53(h ? w.z : w.x, h ? w.w : w.y, upper);
             if (KIND == 0) {
                 z[h] = normal_from_d_vote(d, upper, valid);
+            } else if (KIND == 1) {
+                // Student t by recycling the normal sample (Sec. 3 map)
+                const double zn = probit_mag_f64_tbl(d);
+                z[h] = recycle_t(tk, upper ? zn : -zn);
             } else {
                 // x = -log(u), u = upper ? 1 - d : d, then the Sec. 6 map
                 const double x = upper ? -log1p(-d) : -log(d);
@@ -723,9 +740,16 @@ extern "C" qm_status qm_sample_fused(int target, const qm_params* p, uint64_t ke
         }
         return check_launch("fused normal f32");
     }
-    if ((target == QM_DIST_NORMAL || target == QM_DIST_EXPONENTIAL) && out_is_f64) {
+    if ((target == QM_DIST_NORMAL || target == QM_DIST_EXPONENTIAL || target == QM_DIST_STUDENT_T) &&
+        out_is_f64) {
+        if (target == QM_DIST_STUDENT_T) {
+            if (!p || !(p->nu > 0.0)) return fail(QM_ERR_INVALID, "qm_sample_fused: Student t needs nu > 0");
+            if (t_index(p->nu) < 0)
+                return fail(QM_ERR_UNSUPPORTED, "qm_sample_fused: nu = %g not tabulated", p->nu);
+        }
         const size_t nblk = (n + 1) / 2;
         const int g = grid_for(k_fused_f64<0, true, true>, B, nblk);
+        int tk = 0;
         double* part = nullptr;
         if (moments4) {
             part = partials_scratch(g);
@@ -733,17 +757,20 @@ extern "C" qm_status qm_sample_fused(int target, const qm_params* p, uint64_t ke
         }
         double* o = (double*)out;
         const uint64_t b0 = ctr0 / 4;
-#define QM_LAUNCH_F64(KIND)                                                              \
-    if (o && part) k_fused_f64<KIND, true, true><<<g, B, 0, s>>>(key, b0, n, o, part);   \
-    else if (o) k_fused_f64<KIND, true, false><<<g, B, 0, s>>>(key, b0, n, o, nullptr);  \
-    else k_fused_f64<KIND, false, true><<<g, B, 0, s>>>(key, b0, n, nullptr, part);
-        if (target == QM_DIST_NORMAL) { QM_LAUNCH_F64(0) } else { QM_LAUNCH_F64(2) }
+        if (target == QM_DIST_STUDENT_T) tk = t_index(p->nu);
+#define QM_LAUNCH_F64(KIND)                                                                  \
+    if (o && part) k_fused_f64<KIND, true, true><<<g, B, 0, s>>>(key, b0, n, o, part, tk);   \
+    else if (o) k_fused_f64<KIND, true, false><<<g, B, 0, s>>>(key, b0, n, o, nullptr, tk);  \
+    else k_fused_f64<KIND, false, true><<<g, B, 0, s>>>(key, b0, n, nullptr, part, tk);
+        if (target == QM_DIST_NORMAL) { QM_LAUNCH_F64(0) }
+        else if (target == QM_DIST_STUDENT_T) { QM_LAUNCH_F64(1) }
+        else { QM_LAUNCH_F64(2) }
 #undef QM_LAUNCH_F64
         if (part) k_sum_partials<<<1, 128, 0, s>>>(part, g, moments4);
         return check_launch("fused f64");
     }
     if (target == QM_DIST_STUDENT_T)
-        return fail(QM_ERR_UNSUPPORTED, "qm_sample_fused: Student t target not built yet");
+        return fail(QM_ERR_INVALID, "qm_sample_fused: Student t is FP64 only (out_is_f64 = 1)");
     return fail(QM_ERR_INVALID, "qm_sample_fused: unsupported target/precision (%d, %d)", target, out_is_f64);
 }
 
@@ -760,7 +787,17 @@ extern "C" qm_status qm_recycle(int src, int dst, const qm_params* p, const doub
     }
     if (src == QM_DIST_UNIFORM && dst == QM_DIST_NORMAL)
         return qm_normal_quantile_f64(in, out, n, QM_VAR_DEFAULT, stream);
-    if (src == QM_DIST_NORMAL && dst == QM_DIST_STUDENT_T)
-        return fail(QM_ERR_UNSUPPORTED, "qm_recycle: normal->Student t not built yet");
+    if (src == QM_DIST_NORMAL && dst == QM_DIST_STUDENT_T) {
+        if (!p) return fail(QM_ERR_INVALID, "qm_recycle: Student t needs params (nu)");
+        if (!(p->nu > 0.0)) return fail(QM_ERR_INVALID, "qm_recycle: nu must be > 0 (got %g)", p->nu);
+        const int k = t_index(p->nu);
+        if (k < 0)
+            return fail(QM_ERR_UNSUPPORTED, "qm_recycle: nu = %g not tabulated (1,2,3,4,5,8,10,30)", p->nu);
+        if (n == 0) return QM_OK;
+        if (!in || !out) return fail(QM_ERR_INVALID, "qm_recycle: null pointer");
+        if (bad_overlap(in, n * 8, out, n * 8))
+            return fail(QM_ERR_INVALID, "qm_recycle: partially overlapping in/out");
+        return launch_map(in, out, n, TMap{k}, (cudaStream_t)stream, "recycle normal->t");
+    }
     return fail(QM_ERR_UNSUPPORTED, "qm_recycle: pair (%d -> %d) not supported", src, dst);
 }
