@@ -154,6 +154,50 @@ qm_status qm_sample_moments_noalloc(uint64_t key, uint64_t ctr0, size_t n,
 qm_status qm_recycle(int src, int dst, const qm_params* p, const double* in,
                      double* out, size_t n, void* stream);
 
+/* ---- ragged batches ---------------------------------------------------------
+ * A batch is a table of independent recycling jobs evaluated by ONE
+ * persistent launch over a device-resident segment table, replayed as a CUDA
+ * graph.  Each segment is cut into tiles of block x ept elements that never
+ * span two segments, so the target is uniform within a block.
+ * Segment pairs: (NORMAL, STUDENT_T) with nu tabulated, (EXPONENTIAL,
+ * NORMAL), (UNIFORM, NORMAL); in/out device arrays of n doubles.
+ * qm_batch_create validates everything before any launch: unsupported pairs
+ * or out-of-set nu, null pointers, in/out partial overlap and overlapping
+ * outputs of two segments are rejected (QM_ERR_INVALID / QM_ERR_UNSUPPORTED).
+ * Tuning: block in {128, 256, 512}, ept in {1, 2, 4}, estrin in {0, 1}
+ * (Estrin instead of Horner for the Student-t segment polynomial; the two
+ * round differently, so bit-exact comparisons need the same choice).  With
+ * tuning == NULL the tuning cache ($QM_TUNE_CACHE, default
+ * ~/.cache/qm_tune.txt) is consulted, else (256, 2, 0).  The batch owns its
+ * device table and graph; the caller owns the data arrays.                  */
+typedef struct {
+    int src, dst;        /* distribution pair */
+    double nu;           /* Student-t degrees of freedom */
+    const double* in;    /* device, n doubles */
+    double* out;         /* device, n doubles */
+    size_t n;
+} qm_segment;
+
+typedef struct {
+    int block, ept, estrin;
+} qm_tuning;
+
+typedef struct qm_batch qm_batch;
+
+qm_status qm_batch_create(const qm_segment* segs, int nseg, const qm_tuning* tuning,
+                          qm_batch** out);
+/* One graph launch of the persistent kernel on `stream` (asynchronous). */
+qm_status qm_batch_run(qm_batch* b, void* stream);
+/* Baseline: one plain launch per segment on `stream`. */
+qm_status qm_batch_run_separate(qm_batch* b, void* stream);
+qm_status qm_batch_get_tuning(const qm_batch* b, qm_tuning* t);
+qm_status qm_batch_set_tuning(qm_batch* b, const qm_tuning* t);
+/* Autotuner: times every candidate tuning on this batch (reps graph launches
+ * each, synchronising `stream`), keeps the fastest, appends it to the tuning
+ * cache under the batch signature (segment count, size bucket, target mix). */
+qm_status qm_batch_tune(qm_batch* b, int reps, void* stream, qm_tuning* best);
+qm_status qm_batch_destroy(qm_batch* b);
+
 /* ---- diagnostics ----------------------------------------------------------- */
 const char* qm_last_error(void);
 const char* qm_version(void);

@@ -33,6 +33,15 @@ class qm_params(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_double)]
 
 
+class qm_segment(ctypes.Structure):
+    _fields_ = [("src", ctypes.c_int), ("dst", ctypes.c_int), ("nu", ctypes.c_double),
+                ("inp", ctypes.c_void_p), ("out", ctypes.c_void_p), ("n", ctypes.c_size_t)]
+
+
+class qm_tuning(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int), ("ept", ctypes.c_int), ("estrin", ctypes.c_int)]
+
+
 def load(build_if_missing: bool = True) -> ctypes.CDLL:
     """Load libqm.so (building it first if it is missing or stale)."""
     global _lib
@@ -52,6 +61,13 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "qm_sample_fused": [i, vp, u64, u64, vp, i, sz, vp, vp],
         "qm_recycle": [i, i, vp, vp, vp, sz, vp],
         "qm_sample_moments_noalloc": [u64, u64, sz, vp, vp],
+        "qm_batch_create": [vp, i, vp, vp],
+        "qm_batch_run": [vp, vp],
+        "qm_batch_run_separate": [vp, vp],
+        "qm_batch_get_tuning": [vp, vp],
+        "qm_batch_set_tuning": [vp, vp],
+        "qm_batch_tune": [vp, i, vp, vp],
+        "qm_batch_destroy": [vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -152,6 +168,53 @@ def qm_recycle(src: int, dst: int, inp, out, nu=None, n=None, stream=None):
     _check(load().qm_recycle(src, dst, _params(nu), _ptr(inp), _ptr(out), _numel(inp, n),
                              _stream(stream, inp)))
     return out
+
+
+class Batch:
+    """A ragged batch (qm_batch_*): segments are (src, dst, nu, in, out)
+    with torch CUDA tensors of doubles."""
+
+    def __init__(self, segments, tuning=None):
+        L = load()
+        arr = (qm_segment * len(segments))()
+        self._keep = []
+        for k, (src, dst, nu, inp, out) in enumerate(segments):
+            arr[k] = qm_segment(src, dst, float(nu or 0.0), _ptr(inp), _ptr(out), inp.numel())
+            self._keep += [inp, out]
+        h = ctypes.c_void_p()
+        t = None if tuning is None else ctypes.byref(qm_tuning(*tuning))
+        _check(L.qm_batch_create(arr, len(segments), t, ctypes.byref(h)))
+        self.h = h
+
+    def run(self, stream=None):
+        _check(load().qm_batch_run(self.h, _stream(stream)))
+
+    def run_separate(self, stream=None):
+        _check(load().qm_batch_run_separate(self.h, _stream(stream)))
+
+    def tuning(self):
+        t = qm_tuning()
+        _check(load().qm_batch_get_tuning(self.h, ctypes.byref(t)))
+        return (t.block, t.ept, t.estrin)
+
+    def set_tuning(self, tuning):
+        _check(load().qm_batch_set_tuning(self.h, ctypes.byref(qm_tuning(*tuning))))
+
+    def tune(self, reps=3, stream=None):
+        t = qm_tuning()
+        _check(load().qm_batch_tune(self.h, reps, _stream(stream), ctypes.byref(t)))
+        return (t.block, t.ept, t.estrin)
+
+    def close(self):
+        if self.h:
+            load().qm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def qm_last_error() -> str:

@@ -41,3 +41,28 @@ def test_argument_errors_are_synchronous(lib):
     assert lib.qm_recycle(qm.QM_DIST_UNIFORM, qm.QM_DIST_EXPONENTIAL, None, vp(4096), vp(8192), 8,
                           None) == qm.QM_ERR_UNSUPPORTED
     assert lib.qm_philox_fill_u32(1, 0, None, 8, None) == qm.QM_ERR_INVALID
+
+
+def test_batch_validation_before_any_launch(lib):
+    vp = ctypes.c_void_p
+    h = ctypes.c_void_p()
+    seg = qm.qm_segment
+    # unsupported pair
+    arr = (seg * 1)(seg(qm.QM_DIST_UNIFORM, qm.QM_DIST_EXPONENTIAL, 0.0, 4096, 8192, 8))
+    assert lib.qm_batch_create(arr, 1, None, ctypes.byref(h)) == qm.QM_ERR_INVALID
+    # nu not tabulated / invalid
+    arr = (seg * 1)(seg(qm.QM_DIST_NORMAL, qm.QM_DIST_STUDENT_T, 7.0, 4096, 8192, 8))
+    assert lib.qm_batch_create(arr, 1, None, ctypes.byref(h)) == qm.QM_ERR_UNSUPPORTED
+    arr = (seg * 1)(seg(qm.QM_DIST_NORMAL, qm.QM_DIST_STUDENT_T, -2.0, 4096, 8192, 8))
+    assert lib.qm_batch_create(arr, 1, None, ctypes.byref(h)) == qm.QM_ERR_INVALID
+    # overlapping outputs of two segments
+    arr = (seg * 2)(seg(qm.QM_DIST_EXPONENTIAL, qm.QM_DIST_NORMAL, 0.0, 4096, 1 << 20, 64),
+                    seg(qm.QM_DIST_EXPONENTIAL, qm.QM_DIST_NORMAL, 0.0, 8192, (1 << 20) + 256, 64))
+    assert lib.qm_batch_create(arr, 2, None, ctypes.byref(h)) == qm.QM_ERR_INVALID
+    assert "overlap" in qm.qm_last_error()
+    # null data pointer, bad tuning, empty table
+    arr = (seg * 1)(seg(qm.QM_DIST_EXPONENTIAL, qm.QM_DIST_NORMAL, 0.0, None, 8192, 8))
+    assert lib.qm_batch_create(arr, 1, None, ctypes.byref(h)) == qm.QM_ERR_INVALID
+    arr = (seg * 1)(seg(qm.QM_DIST_EXPONENTIAL, qm.QM_DIST_NORMAL, 0.0, 4096, 8192, 8))
+    assert lib.qm_batch_create(arr, 1, ctypes.byref(qm.qm_tuning(300, 2, 0)), ctypes.byref(h)) == qm.QM_ERR_INVALID
+    assert lib.qm_batch_create(arr, 0, None, ctypes.byref(h)) == qm.QM_ERR_INVALID
