@@ -198,6 +198,72 @@ qm_status qm_batch_set_tuning(qm_batch* b, const qm_tuning* t);
 qm_status qm_batch_tune(qm_batch* b, int reps, void* stream, qm_tuning* best);
 qm_status qm_batch_destroy(qm_batch* b);
 
+/* ---- serving: continuous batching of Monte Carlo sample requests ------------
+ * A request asks for n samples of one target from its own Philox key
+ * (counters from 0): QM_REQ_NORMAL_F32 (24-bit grid, TABLE form),
+ * QM_REQ_NORMAL_F64 (53-bit grid), QM_REQ_STUDENT_T (the FP64 normal
+ * recycled by the Sec. 3 map, nu tabulated), QM_REQ_EXP_NORMAL (Exp(1)
+ * samples -log u recycled by the Sec. 6 map).  Sample i of a request is the
+ * same value whether it is computed alone or inside any batch.
+ * The server owns a device arena of mem_budget bytes (one cudaMalloc at
+ * create): a request is admitted, in FIFO order, only when its output fits;
+ * its output stays on the device until qm_server_release(id) (or is freed
+ * as soon as it completes when release_on_done = 1).  A worker thread packs
+ * admitted requests into one launch per batch (<= max_batch requests) on one
+ * of `streams` streams; requests arriving while batches run are admitted
+ * into the next batch, and batches on different streams overlap.
+ * max_batch = 1 with streams = 1 is the plain baseline (one launch per
+ * request, FIFO on one stream).  Times are seconds on the server clock
+ * (qm_server_now).  Waits are bounded; expiry returns QM_ERR_TIMEOUT.       */
+enum { QM_REQ_NORMAL_F32 = 0, QM_REQ_NORMAL_F64 = 1, QM_REQ_STUDENT_T = 2, QM_REQ_EXP_NORMAL = 3 };
+
+typedef struct {
+    uint64_t id;
+    size_t n;
+    int kind;
+    double nu;
+    uint64_t key;
+    double t_arrival;    /* server clock (replay: seconds from the replay call) */
+} qm_request;
+
+typedef struct {
+    uint64_t id;
+    int status;
+    void* out;           /* device: n floats (NORMAL_F32) or doubles; NULL once released */
+    size_t n;
+    int is_f64;
+    int kind;
+    double nu;
+    uint64_t key;
+    double t_arrival, t_admit, t_launch, t_done;
+} qm_completion;
+
+typedef struct {
+    size_t mem_budget;   /* bytes of device arena */
+    int max_batch;       /* requests per launch (1 = plain) */
+    int streams;         /* concurrent batches, 1..8 */
+    int release_on_done; /* free outputs on completion (consumer-less replay) */
+    int device;
+} qm_server_config;
+
+typedef struct {
+    size_t launches, arena_used, arena_capacity;
+} qm_server_stats_t;
+
+typedef struct qm_server qm_server;
+
+qm_status qm_server_create(const qm_server_config* cfg, qm_server** out);
+qm_status qm_server_submit(qm_server* s, const qm_request* r);
+qm_status qm_server_poll(qm_server* s, qm_completion* out, int max, int* got);
+qm_status qm_server_release(qm_server* s, uint64_t id);
+qm_status qm_server_stats(const qm_server* s, qm_server_stats_t* st);
+double qm_server_now(const qm_server* s);
+/* Submits trace[i] at t_arrival seconds after the call (real time), waits
+ * for all nreq completions (at most timeout_s), stores them in out. */
+qm_status qm_server_replay(qm_server* s, const qm_request* trace, int nreq, double timeout_s,
+                           qm_completion* out);
+qm_status qm_server_destroy(qm_server* s);
+
 /* ---- diagnostics ----------------------------------------------------------- */
 const char* qm_last_error(void);
 const char* qm_version(void);

@@ -38,6 +38,31 @@ class qm_segment(ctypes.Structure):
                 ("inp", ctypes.c_void_p), ("out", ctypes.c_void_p), ("n", ctypes.c_size_t)]
 
 
+class qm_request(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("n", ctypes.c_size_t), ("kind", ctypes.c_int),
+                ("nu", ctypes.c_double), ("key", ctypes.c_uint64), ("t_arrival", ctypes.c_double)]
+
+
+class qm_completion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int), ("out", ctypes.c_void_p),
+                ("n", ctypes.c_size_t), ("is_f64", ctypes.c_int), ("kind", ctypes.c_int),
+                ("nu", ctypes.c_double), ("key", ctypes.c_uint64), ("t_arrival", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_launch", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class qm_server_config(ctypes.Structure):
+    _fields_ = [("mem_budget", ctypes.c_size_t), ("max_batch", ctypes.c_int), ("streams", ctypes.c_int),
+                ("release_on_done", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+class qm_server_stats_t(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_size_t), ("arena_used", ctypes.c_size_t),
+                ("arena_capacity", ctypes.c_size_t)]
+
+
+QM_REQ_NORMAL_F32, QM_REQ_NORMAL_F64, QM_REQ_STUDENT_T, QM_REQ_EXP_NORMAL = range(4)
+
+
 class qm_tuning(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int), ("ept", ctypes.c_int), ("estrin", ctypes.c_int)]
 
@@ -68,6 +93,13 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "qm_batch_set_tuning": [vp, vp],
         "qm_batch_tune": [vp, i, vp, vp],
         "qm_batch_destroy": [vp],
+        "qm_server_create": [vp, vp],
+        "qm_server_submit": [vp, vp],
+        "qm_server_poll": [vp, vp, i, vp],
+        "qm_server_release": [vp, u64],
+        "qm_server_stats": [vp, vp],
+        "qm_server_replay": [vp, vp, i, d, vp],
+        "qm_server_destroy": [vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -77,6 +109,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.qm_last_error.argtypes = []
     L.qm_version.restype = ctypes.c_char_p
     L.qm_sm_count.restype = ctypes.c_int
+    L.qm_server_now.restype = ctypes.c_double
+    L.qm_server_now.argtypes = [vp]
     _lib = L
     return L
 
@@ -208,6 +242,62 @@ class Batch:
     def close(self):
         if self.h:
             load().qm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """The continuous-batching server (qm_server_*)."""
+
+    def __init__(self, mem_budget, max_batch=256, streams=2, release_on_done=False, device=0):
+        cfg = qm_server_config(int(mem_budget), int(max_batch), int(streams), int(release_on_done),
+                               int(device))
+        h = ctypes.c_void_p()
+        _check(load().qm_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.h = h
+
+    @staticmethod
+    def requests(trace):
+        arr = (qm_request * len(trace))()
+        for k, r in enumerate(trace):
+            arr[k] = qm_request(r.get("id", k), r["n"], r["kind"], float(r.get("nu", 0.0)),
+                                r["key"], float(r.get("t_arrival", 0.0)))
+        return arr
+
+    def replay(self, trace, timeout_s=120.0):
+        arr = self.requests(trace)
+        out = (qm_completion * len(trace))()
+        _check(load().qm_server_replay(self.h, arr, len(trace), float(timeout_s), out))
+        return list(out)
+
+    def submit(self, req):
+        _check(load().qm_server_submit(self.h, ctypes.byref(self.requests([req])[0])))
+
+    def poll(self, max_items=1024):
+        out = (qm_completion * max_items)()
+        got = ctypes.c_int()
+        _check(load().qm_server_poll(self.h, out, max_items, ctypes.byref(got)))
+        return list(out[: got.value])
+
+    def release(self, rid):
+        _check(load().qm_server_release(self.h, rid))
+
+    def stats(self):
+        st = qm_server_stats_t()
+        _check(load().qm_server_stats(self.h, ctypes.byref(st)))
+        return {"launches": st.launches, "arena_used": st.arena_used, "arena_capacity": st.arena_capacity}
+
+    def now(self):
+        return load().qm_server_now(self.h)
+
+    def close(self):
+        if self.h:
+            load().qm_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

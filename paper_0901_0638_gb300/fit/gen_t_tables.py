@@ -2,7 +2,8 @@
 
 Q_nu(z) = F_nu^{-1}(Phi(z)) (Sec. 3) is odd; for 0 <= z < Z1 = 8.75 it is
 stored as local Taylor expansions on segments of width h = 1/32, centred at
-z_c = (j + 1/2) h.  Each expansion comes from the Gaussian-background
+z_c = (j + 1/2) h, except segment 0, expanded at z_c = 0 (the central series
+of Sec. 3.2, odd in z).  Each expansion comes from the Gaussian-background
 recycling ODE of Sec. 3.1,
     (1 + Q^2/n)(Q'' + z Q') = (1 + 1/n) Q Q'^2,
 started from Q(z_c) and Q'(z_c) = phi(z_c) / f_nu(Q(z_c)) -- the recurrence of
@@ -88,13 +89,17 @@ def kappa(nu):
 def seg(args):
     nu, j = args
     mp.mp.dps = 40
-    zc = (mp.mpf(j) + mp.mpf("0.5")) / H_INV
+    # segment 0 is expanded at z = 0: the odd central series of Sec. 3.2
+    # (Q(0) = 0, Q'(0) = gamma), which keeps relative accuracy as z -> 0
+    zc = mp.mpf(0) if j == 0 else (mp.mpf(j) + mp.mpf("0.5")) / H_INV
     q0 = t_map(nu, zc)
     q1 = mp.npdf(zc) / t_density(nu, q0)
     b = rode.taylor_gauss_background_t(nu, zc, q0, q1, DEG + 1)
     worst = mp.mpf(0)
     if j % 16 == 0 or j == NSEG - 1:
-        for s in (-mp.mpf(1) / (2 * H_INV), mp.mpf(1) / (2 * H_INV)):
+        ends = ((mp.mpf(1) / (4 * H_INV), mp.mpf(1) / H_INV) if j == 0 else
+                (-mp.mpf(1) / (2 * H_INV), mp.mpf(1) / (2 * H_INV)))
+        for s in ends:
             ref = t_map(nu, zc + s)
             if ref != 0:
                 approx = sum(b[n] * s**n for n in range(DEG + 1))

@@ -51,3 +51,33 @@ def f64_violations(z, w, tol, u=None, lo=1e-300, hi=1.0 - 2.0**-53):
         m &= (u >= lo) & (u <= hi)
     bad[m] = ~(np.abs(z[m] / w[m] - 1.0) <= tol)   # NaN counts as a miss
     return bad
+
+
+_cudart = None
+
+
+def cudart():
+    """The CUDA runtime library (for raw device-to-host copies in tests)."""
+    import ctypes
+    global _cudart
+    if _cudart is None:
+        for name in ("libcudart.so.13", "libcudart.so.12", "libcudart.so",
+                     "/usr/local/cuda/lib64/libcudart.so"):
+            try:
+                _cudart = ctypes.CDLL(name)
+                break
+            except OSError:
+                continue
+        if _cudart is None:
+            raise RuntimeError("libcudart not found")
+    return _cudart
+
+
+def d2h(ptr, n, dtype):
+    """Copy n elements of dtype from a raw device pointer to a numpy array."""
+    import ctypes
+    host = np.empty(n, dtype=dtype)
+    rc = cudart().cudaMemcpy(ctypes.c_void_p(host.ctypes.data), ctypes.c_void_p(ptr),
+                             ctypes.c_size_t(host.nbytes), 2)   # cudaMemcpyDeviceToHost
+    assert rc == 0, rc
+    return host
