@@ -41,6 +41,10 @@ def parse():
     p.add_argument("--n-log2", type=int, default=28, help="elements per rank = 2^n")
     p.add_argument("--variant", default="default")
     p.add_argument("--no-extras", action="store_true", help="skip variant/e2e/cpu legs")
+    p.add_argument("--workload", default="fp64", choices=["fp64", "fp32", "batch", "serve"],
+                   help="fp64: the headline line; fp32/batch/serve: the other hot-path kernels "
+                        "(for profiling and context)")
+    p.add_argument("--serve-seconds", type=float, default=2.0)
     return p.parse_args()
 
 
@@ -149,11 +153,98 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def timed(fn, stream, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def side_workload(args):
+    """fp32 / batch / serve workloads: one JSON line each (rank 0 only)."""
+    import numpy as np
+    import torch
+    import paper_0901_0638_gb300 as qm
+    from paper_0901_0638_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    qm.load()
+    line = {"metric": METRIC, "unit": "Gsamples/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "data": "synthetic"}
+    if args.workload == "fp32":
+        n = 1 << args.n_log2
+        _, u = W.uniform24(1, n, device=dev)
+        z = torch.empty_like(u)
+        ms = timed(lambda: qm.qm_normal_quantile_f32(u, z, qm.QM_VAR_DEFAULT, stream=stream),
+                   stream, args.steps, args.warmup)
+        gbs = 8 * n / (ms * 1e-3) / 1e9
+        line.update(value=n / (ms * 1e-3) / 1e9, ms_per_step=ms, dtype="f32",
+                    config={"workload": f"fp32 normal quantile, n=2^{args.n_log2} floats, "
+                                        "u=fl32((k+1/2)2^-24), k = top 24 bits of Philox seed 1"},
+                    roofline={"bound": "hbm", "achieved": gbs, "peak": 6780.7, "unit": "GB/s",
+                              "frac": gbs / 6780.7, "traffic": None})
+    elif args.workload == "batch":
+        lens, targets = W.ragged_segments(4, 256)
+        spec = []
+        keep = []
+        for j, (nj, tg) in enumerate(zip(lens, targets)):
+            if tg == 8:
+                x = W.exponential(4, nj, 0, j + 1, dev)
+                spec.append((qm.QM_DIST_EXPONENTIAL, qm.QM_DIST_NORMAL, 0.0, x, torch.empty_like(x)))
+            else:
+                x = W.normal_box_muller(4, nj, 0, j + 1, dev)
+                spec.append((qm.QM_DIST_NORMAL, qm.QM_DIST_STUDENT_T, W.NU_SET[tg], x, torch.empty_like(x)))
+        b = qm.Batch(spec)
+        tuning = b.tuning()
+        tot = sum(lens)
+        ms = timed(lambda: b.run(stream), stream, args.steps, args.warmup)
+        ms_sep = timed(lambda: b.run_separate(stream), stream, args.steps, args.warmup)
+        line.update(value=tot / (ms * 1e-3) / 1e9, ms_per_step=ms, dtype="f64",
+                    config={"workload": "ragged recycling batch: 256 segments, lengths log-uniform "
+                                        "[2^10, 2^24] (seed 4), normal->t_nu for nu in {1,2,3,4,5,8,10,30} "
+                                        "and exp->normal", "elements": tot, "tuning": tuning},
+                    separate_launches={"ms_per_step": ms_sep, "value": tot / (ms_sep * 1e-3) / 1e9})
+    else:
+        tr = W.serving_trace(5, rate=2e4, seconds=args.serve_seconds)
+        for r in tr:
+            r["id"] = r["key"]
+        tot = sum(r["n"] for r in tr)
+        res = {}
+        for name, mb, st in (("batched", 512, 2), ("plain", 1, 1)):
+            srv = qm.Server(mem_budget=8 << 30, max_batch=mb, streams=st, release_on_done=True)
+            done = srv.replay(tr, timeout_s=900)
+            lat = np.array([c.t_done - c.t_arrival for c in done])
+            span = max(c.t_done for c in done) - min(c.t_arrival for c in done)
+            res[name] = {"gsamples_s": tot / span / 1e9, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                         "p99_ms": 1e3 * float(np.percentile(lat, 99)), "makespan_s": span,
+                         "launches": srv.stats()["launches"]}
+            srv.close()
+        line.update(value=res["batched"]["gsamples_s"], ms_per_step=None, dtype="mixed",
+                    config={"workload": f"serving: Poisson 2e4 req/s for {args.serve_seconds} s (seed 5), "
+                                        "n log-uniform [2^8, 2^24], 4 target kinds, 8 GiB budget",
+                            "requests": len(tr), "samples": tot,
+                            "offered_gsamples_s": tot / args.serve_seconds / 1e9},
+                    serving=res)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload != "fp64":
+        if rank == 0:
+            side_workload(args)
+        return
 
     import torch
     import paper_0901_0638_gb300 as qm

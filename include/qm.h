@@ -115,8 +115,10 @@ qm_status qm_philox_fill_u32(uint64_t key, uint64_t ctr0, uint32_t* out,
  *       -> z = Phi^{-1}((k + 1/2) 2^-53) (FP64 exponential form);
  *   QM_DIST_STUDENT_T (p->nu required): t = F_nu^{-1}(Phi(z)) of the FP64
  *       normal above (Sec. 3 map), FP64 only;
- *   QM_DIST_EXPONENTIAL: x = -log((k + 1/2) 2^-53) mapped to the normal by
- *       the Sec. 6 recycling map, FP64 only.
+ *   QM_DIST_EXPONENTIAL: the Exp(1) sample x = -log(u), u = (k + 1/2) 2^-53,
+ *       mapped to the normal by the Sec. 6 recycling map Q(x) =
+ *       Phi^{-1}(1 - e^{-x}) = Phi^{-1}(1 - u), evaluated from the exact u
+ *       (x itself is never rounded), FP64 only.
  * out: float[n] / double[n] (device) or NULL.  moments4: double[4] (device)
  * or NULL; if given it receives sum z, sum z^2, sum z^3, sum z^4 over the n
  * samples (overwritten, not accumulated).  At least one of out / moments4. */
@@ -203,8 +205,9 @@ qm_status qm_batch_destroy(qm_batch* b);
  * (counters from 0): QM_REQ_NORMAL_F32 (24-bit grid, TABLE form),
  * QM_REQ_NORMAL_F64 (53-bit grid), QM_REQ_STUDENT_T (the FP64 normal
  * recycled by the Sec. 3 map, nu tabulated), QM_REQ_EXP_NORMAL (Exp(1)
- * samples -log u recycled by the Sec. 6 map).  Sample i of a request is the
- * same value whether it is computed alone or inside any batch.
+ * samples x = -log u recycled by the Sec. 6 map, evaluated from the exact u
+ * as in qm_sample_fused).  Sample i of a request is the same value whether
+ * it is computed alone or inside any batch.
  * The server owns a device arena of mem_budget bytes (one cudaMalloc at
  * create): a request is admitted, in FIFO order, only when its output fits;
  * its output stays on the device until qm_server_release(id) (or is freed

@@ -543,9 +543,10 @@ k_fused_f64(uint64_t key, uint64_t blk0, size_t n, double* out, double* partials
                 const double zn = probit_mag_f64_tbl(d);
                 z[h] = recycle_t(tk, upper ? zn : -zn);
             } else {
-                // x = -log(u), u = upper ? 1 - d : d, then the Sec. 6 map
-                const double x = upper ? -log1p(-d) : -log(d);
-                z[h] = ExpToNormal()(x);
+                // Exp(1) sample x = -log(u) recycled by the Sec. 6 map:
+                // Q(x) = Phi^{-1}(1 - u), evaluated from the exact u (no log)
+                const double zn = probit_mag_f64_tbl(d);
+                z[h] = upper ? -zn : zn;
             }
         }
         const size_t i0 = b * 2;

@@ -71,13 +71,14 @@ __device__ __forceinline__ double serve_f64_one(int kind, int tk, uint32_t hi, u
     const bool upper = k >= (1ull << 52);
     const uint64_t j = upper ? ((1ull << 53) - 1 - k) : k;
     const double d = ((double)j + 0.5) * 1.1102230246251565404e-16;   // exact
-    if (kind == 3) {
-        // exponential sample x = -log(u), u = (k + 1/2) 2^-53, then the
-        // exponential -> normal recycling map (Sec. 6)
-        const double x = upper ? -log1p(-d) : -log(d);
-        return exp_to_normal(x);
-    }
     const double m = probit_mag_f64_tbl(d);                 // d >= 2^-54: covered
+    if (kind == 3) {
+        // Exp(1) sample x = -log(u), u = (k + 1/2) 2^-53, recycled to the
+        // normal by Q(x) = Phi^{-1}(1 - e^{-x}) = Phi^{-1}(1 - u) (Sec. 6): the
+        // exponential coordinate of u is evaluated by the table from u's bits,
+        // so x is never rounded (z > 0 exactly when u < 1/2).
+        return upper ? -m : m;
+    }
     const double z = upper ? m : -m;
     return (kind == 2) ? recycle_t(tk, z) : z;
 }
