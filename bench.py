@@ -48,6 +48,21 @@ def parse():
     return p.parse_args()
 
 
+def shard_first(rank: int, n_per_rank: int) -> int:
+    """First element of rank's slice of the counter-based input stream."""
+    return rank * n_per_rank
+
+
+def max_over_ranks(ms: float, pg, device=None) -> float:
+    """The slowest rank's step time (weak scaling: value = world n / max)."""
+    if pg is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -268,7 +283,7 @@ def main():
                 "branchfree": qm.QM_VAR_BRANCHFREE, "hybrid_vote": qm.QM_VAR_HYBRID_VOTE,
                 "mixed_halley": qm.QM_VAR_MIXED_HALLEY, "cuda_normcdfinv": qm.QM_VAR_CUDA_LIBM}
     var = variants[args.variant]
-    u = W.mixture_f64(2, n, first=rank * n, device=dev)
+    u = W.mixture_f64(2, n, first=shard_first(rank, n), device=dev)
     z = torch.empty_like(u)
     stream = torch.cuda.current_stream(dev)
     # algorithmic DP work: table path for d >= 2^-65, deep rational below
@@ -297,11 +312,7 @@ def main():
     torch.cuda.synchronize(dev)
     barrier()
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if pg is not None:
-        t = torch.tensor([ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, pg, dev)
     value = world * n / (ms * 1e-3) / 1e9
 
     # roofline of the dominant kernel (FP64 table kernel): FP64-issue bound.

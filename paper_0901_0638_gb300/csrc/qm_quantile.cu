@@ -344,7 +344,7 @@ k_f64_table(const double* __restrict__ in, double* out, size_t n)
             const long long ub = __double_as_longlong(u);
             const bool upper = ub >= 0x3FE0000000000000ll;                // u >= 1/2
             const bool valid = ub > 0 && ub < 0x3FF0000000000000ll;       // 0 < u < 1
-            const double d = upper ? __dadd_rn(1.0, -u) : u;
+            const double d = upper ? one_minus_upper(u) : u;                 // exact
             const bool covers = valid && __double_as_longlong(d) >= 0x3BE0000000000000ll;  // 2^-65
             if (i < n && !(valid && !covers)) {
                 double m = covers ? probit_mag_f64_tbl(d) : 0.0;
