@@ -135,8 +135,10 @@ __device__ __forceinline__ double2 apply_vec(double2 a, const F& f)
     return make_double2(f(a.x), f(a.y));
 }
 
-template <typename T, int U, class F>
-__global__ void __launch_bounds__(256)
+// MINB: resident blocks per SM the compiler must allow (register cap); the
+// single-precision maps are latency bound at low occupancy.
+template <typename T, int U, class F, int MINB = 1>
+__global__ void __launch_bounds__(256, MINB)
 k_map_vec(const T* __restrict__ in, T* out, size_t n, F f)
 {
     using V = typename Vec<T>::type;
@@ -186,11 +188,12 @@ template <typename T, class F>
 static qm_status launch_map(const T* in, T* out, size_t n, F f, cudaStream_t s, const char* what)
 {
     constexpr int U = 2, B = 256;
+    constexpr int MINB = sizeof(T) == 4 ? 6 : 1;
     const bool aligned = ((uintptr_t)in % 16 == 0) && ((uintptr_t)out % 16 == 0);
     if (aligned) {
         const size_t nv = n / Vec<T>::W;
-        const int g = grid_for(k_map_vec<T, U, F>, B, (nv + U - 1) / U > 0 ? (nv + U - 1) / U : 1);
-        k_map_vec<T, U, F><<<g, B, 0, s>>>(in, out, n, f);
+        const int g = grid_for(k_map_vec<T, U, F, MINB>, B, (nv + U - 1) / U > 0 ? (nv + U - 1) / U : 1);
+        k_map_vec<T, U, F, MINB><<<g, B, 0, s>>>(in, out, n, f);
     } else {
         const int g = grid_for(k_map_scalar<T, F>, B, n);
         k_map_scalar<T, F><<<g, B, 0, s>>>(in, out, n, f);

@@ -15,10 +15,11 @@ per segment the Taylor coefficients of G(r) = Q(V - log(1 + r)).  A kernel
 evaluates |Phi^{-1}(u)| = G(r) with a short Horner chain: no logarithm, no
 division.
 
-FP64 table: E = -1 .. -64 (v <= 44.4), k = 5 (32 segments per binade);
-  entry = a0..a5, c (double) | a6 a7 (float)            -- 64 bytes.
-  (a0..a5 are evaluated in double, a6 a7 in single precision: their terms
-  are below 1e-12 of the result.)
+FP64 table: E = -1 .. -64 (v <= 44.4), k = 6 (64 segments per binade);
+  entry = a0..a3, c (double) | a4..a7 (float)           -- 64 bytes.
+  (a0..a3 are evaluated in double, a4..a7 in single precision: with 64
+  segments per binade their terms are below 3e-9, 5e-10 and 2e-14 of the
+  result, so single precision adds at most ~1e-16.)
 FP32 table: E = -1 .. -149, k = 5 (32 segments per binade), with the
   subtractive reduction r = m - m_j (m_j the segment centre, or 2 for the top
   segment, where r = 2x - 2 is exact and G(0) = 0 at u = 1/2), so
@@ -41,7 +42,7 @@ from . import targets as T
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(os.path.dirname(HERE), "csrc", "qm_tables.h")
 
-F64_K, F64_EMIN, F64_DEG = 5, -64, 7
+F64_K, F64_EMIN, F64_DEG = 6, -64, 7
 F32_K, F32_EMIN, F32_DEG = 5, -149, 3
 
 
@@ -139,13 +140,13 @@ def main():
         "#pragma once\n\nnamespace qm {\nnamespace tbl {\n\n",
         f"constexpr int F64_K = {F64_K};\nconstexpr int F64_EMIN = {F64_EMIN};\n",
         f"constexpr int F32_K = {F32_K};\nconstexpr int F32_EMIN = {F32_EMIN};\n\n",
-        "struct alignas(64) SegF64 { double a[6]; double c; float b6, b7; };\n",
+        "struct alignas(64) SegF64 { double a[4]; double c; float b[4]; float pad[2]; };\n",
         "struct alignas(16) SegF32 { float a0, a1, a2, a3; };\n\n",
         f"__device__ const SegF64 SEG_F64[{len(r64)}] = {{\n",
     ]
     for E, j, c, a, _ in r64:
-        lines.append("  {{" + ",".join(hexd(x) for x in a[:6]) + "}," + hexd(c) + "," +
-                     ",".join(hexf(x) for x in a[6:8]) + "},\n")
+        lines.append("  {{" + ",".join(hexd(x) for x in a[:4]) + "}," + hexd(c) + ",{" +
+                     ",".join(hexf(x) for x in a[4:8]) + "},{0.0f,0.0f}},\n")
     lines.append("};\n\n")
     lines.append(f"__device__ const SegF32 SEG_F32[{len(r32)}] = {{\n")
     for E, j, c, a, _ in r32:
