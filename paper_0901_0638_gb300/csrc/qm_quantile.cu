@@ -202,6 +202,58 @@ static qm_status launch_map(const T* in, T* out, size_t n, F f, cudaStream_t s, 
 }
 
 // ===========================================================================
+// FP32 TABLE map: one check per float4 for the rare edge inputs (0, 1, 1/2,
+// subnormal, out of range, NaN); the common case runs the short table path
+// on all four lanes of the vector with no per-element branch.
+// ===========================================================================
+__device__ __forceinline__ bool f32_common(float u)
+{
+    const uint32_t ub = __float_as_uint(u);
+    return (ub - 0x00800000u < 0x3f800000u - 0x00800000u) && ub != 0x3f000000u;
+}
+
+__device__ __forceinline__ float f32_fast(float u)
+{
+    const uint32_t ub = __float_as_uint(u);
+    const bool upper = ub > 0x3f000000u;
+    const float x = upper ? __fmaf_rn(-2.0f, u, 2.0f) : 2.0f * u;
+    const float g = tbl32_core(x);
+    return __uint_as_float(__float_as_uint(g) ^ (upper ? 0u : 0x80000000u));
+}
+
+template <int U>
+__global__ void __launch_bounds__(256, 6)
+k_f32_table(const float* __restrict__ in, float* out, size_t n)
+{
+    const size_t nv = n / 4;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const float4* vin = reinterpret_cast<const float4*>(in);
+    float4* vout = reinterpret_cast<float4*>(out);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride * U) {
+        float4 a[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k)
+            if (i + k * stride < nv) a[k] = __ldcs(vin + i + k * stride);
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            if (i + k * stride >= nv) continue;
+            const float4 v = a[k];
+            float4 z;
+            if (f32_common(v.x) && f32_common(v.y) && f32_common(v.z) && f32_common(v.w)) {
+                z = make_float4(f32_fast(v.x), f32_fast(v.y), f32_fast(v.z), f32_fast(v.w));
+            } else {
+                z = make_float4(probit_f32_tbl(v.x), probit_f32_tbl(v.y), probit_f32_tbl(v.z),
+                                probit_f32_tbl(v.w));
+            }
+            __stcs(vout + i + k * stride, z);
+        }
+    }
+    const size_t tail = nv * 4;
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n - tail) out[tail + t] = probit_f32_tbl(in[tail + t]);
+}
+
+// ===========================================================================
 // FP64 hybrid with the warp vote (Sec. 7.3): every lane holds one element;
 // if all 32 t_2 coordinates are below 15.5 the warp takes the t_2 rational,
 // otherwise the whole warp takes the exponential form.
@@ -618,7 +670,13 @@ extern "C" qm_status qm_normal_quantile_f32(const float* u, float* z, size_t n, 
     case QM_VAR_BRANCHFREE: return launch_map(u, z, n, F32Paper(), s, "f32 branch-free");
     case QM_VAR_CUDA_LIBM: return launch_map(u, z, n, F32Libm(), s, "f32 normcdfinvf");
     case QM_VAR_DEFAULT:
-    case QM_VAR_TABLE: return launch_map(u, z, n, F32Table(), s, "f32 table");
+    case QM_VAR_TABLE: {
+        if ((uintptr_t)u % 16 != 0 || (uintptr_t)z % 16 != 0)
+            return launch_map(u, z, n, F32Table(), s, "f32 table (unaligned)");
+        const int g = grid_for(k_f32_table<2>, 256, (n / 4 + 1) / 2 + 1);
+        k_f32_table<2><<<g, 256, 0, s>>>(u, z, n);
+        return check_launch("f32 table");
+    }
     default: return fail(QM_ERR_INVALID, "qm_normal_quantile_f32: variant %d not available in FP32", variant);
     }
 }
