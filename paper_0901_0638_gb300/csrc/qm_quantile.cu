@@ -22,6 +22,7 @@
 #include "qm.h"
 #include "qm_device.cuh"
 #include "qm_host.h"
+#include "qm_tables_deep.h"
 
 namespace qm {
 
@@ -370,11 +371,30 @@ k_f64_compact(const double* __restrict__ in, double* out, size_t n)
 }
 
 // ===========================================================================
-// FP64 TABLE: table-driven exponential coordinate for d >= 2^-65, the deep
-// tail compacted per tile and evaluated densely with the deep rational.
+// FP64 TABLE: table-driven exponential coordinate for every normal d (main
+// and deep tables), subnormal d (u < 2.2e-308) compacted per tile and
+// evaluated densely with the deep rational.
 // Reflection, domain tests and the sign use integer operations on the bits
 // (the FP64 pipe is the bottleneck on this part).
 // ===========================================================================
+// |Phi^{-1}| for normal d in [2^-1022, 1/2): main table (k = 6) for
+// E >= -64, deep table (k = 5) below; one code path, the table chosen by
+// integer selects.
+__device__ __forceinline__ double probit_mag_f64_tbl_full(double d)
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(d) + (1ull << 52);   // x = 2d
+    const int E0 = (int)(b >> 52) - 1023;
+    const int E = min(E0, -1);                          // d = 1/2 (x = 1): +0 below
+    const double m = __longlong_as_double((long long)((b & 0x000fffffffffffffull) | 0x3ff0000000000000ull));
+    const int j6 = (int)((b >> (52 - tbl::F64_K)) & ((1u << tbl::F64_K) - 1));
+    const int j5 = (int)((b >> (52 - tbl::DEEP_K)) & ((1u << tbl::DEEP_K) - 1));
+    const tbl::SegF64* e = (E >= tbl::F64_EMIN)
+        ? &tbl::SEG_F64[(-1 - E) * (1 << tbl::F64_K) + j6]
+        : &tbl::SEG_F64_DEEP[(tbl::DEEP_EHI - E) * (1 << tbl::DEEP_K) + j5];
+    const double g = f64_seg_eval(e, m);
+    return (E0 >= 0) ? 0.0 : g;
+}
+
 __global__ void __launch_bounds__(kCompactBlock)
 k_f64_table(const double* __restrict__ in, double* out, size_t n)
 {
@@ -400,9 +420,9 @@ k_f64_table(const double* __restrict__ in, double* out, size_t n)
             const bool upper = ub >= 0x3FE0000000000000ll;                // u >= 1/2
             const bool valid = ub > 0 && ub < 0x3FF0000000000000ll;       // 0 < u < 1
             const double d = upper ? one_minus_upper(u) : u;                 // exact
-            const bool covers = valid && __double_as_longlong(d) >= 0x3BE0000000000000ll;  // 2^-65
+            const bool covers = valid && __double_as_longlong(d) >= 0x0010000000000000ll;  // normal d
             if (i < n && !(valid && !covers)) {
-                double m = covers ? probit_mag_f64_tbl(d) : 0.0;
+                double m = covers ? probit_mag_f64_tbl_full(d) : 0.0;
                 long long mb = __double_as_longlong(m) & 0x7fffffffffffffffll;
                 if (!valid) {
                     const bool zero = (ub & 0x7fffffffffffffffll) == 0;

@@ -20,6 +20,9 @@ FP64 table: E = -1 .. -64 (v <= 44.4), k = 6 (64 segments per binade);
   (a0..a3 are evaluated in double, a4..a7 in single precision: with 64
   segments per binade their terms are below 3e-9, 5e-10 and 2e-14 of the
   result, so single precision adds at most ~1e-16.)
+FP64 deep table (qm_tables_deep.h, used by the streaming FP64 kernel only):
+  E = -65 .. -1022 (x = 2d normal, 44.4 < v <= 708), k = 5, same entry
+  layout and degree (their single-precision terms are below 2e-10).
 FP32 table: E = -1 .. -149, k = 5 (32 segments per binade), with the
   subtractive reduction r = m - m_j (m_j the segment centre, or 2 for the top
   segment, where r = 2x - 2 is exact and G(0) = 0 at u = 1/2), so
@@ -41,6 +44,8 @@ from . import targets as T
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(os.path.dirname(HERE), "csrc", "qm_tables.h")
+OUT_DEEP = os.path.join(os.path.dirname(HERE), "csrc", "qm_tables_deep.h")
+DEEP_K, DEEP_EHI, DEEP_ELO = 5, -65, -1022
 
 F64_K, F64_EMIN, F64_DEG = 6, -64, 7
 F32_K, F32_EMIN, F32_DEG = 5, -149, 3
@@ -122,9 +127,28 @@ def hexf(x):
 def main():
     jobs64 = [(E, j, F64_K, F64_DEG) for E in range(-1, F64_EMIN - 1, -1) for j in range(2**F64_K)]
     jobs32 = [(E, j, F32_K, F32_DEG) for E in range(-1, F32_EMIN - 1, -1) for j in range(2**F32_K)]
+    jobsd = [(E, j, DEEP_K, F64_DEG) for E in range(DEEP_EHI, DEEP_ELO - 1, -1) for j in range(2**DEEP_K)]
     with mproc.Pool(max(1, (os.cpu_count() or 2))) as pool:
         r64 = pool.map(seg_coeffs, jobs64, chunksize=16)
         r32 = pool.map(seg_coeffs_sub, jobs32, chunksize=16)
+        rd = pool.map(seg_coeffs, jobsd, chunksize=32)
+    wd = max(r[4] for r in rd)
+    print(f"FP64 deep table: {len(rd)} segments, truncation <= {wd:.3g}", file=sys.stderr)
+    dl = [
+        "// Generated by paper_0901_0638_gb300/fit/gen_tables.py -- do not edit.\n",
+        "// Deep-tail extension of the FP64 segment table (same entry layout):\n",
+        f"// E = {DEEP_EHI}..{DEEP_ELO}, k = {DEEP_K}, degree {F64_DEG}, max truncation {wd:.3g}.\n",
+        "// Index (-65 - E) 2^k + j.  Include in one translation unit only.\n",
+        "#pragma once\n#include \"qm_tables.h\"\n\nnamespace qm {\nnamespace tbl {\n\n",
+        f"constexpr int DEEP_K = {DEEP_K};\nconstexpr int DEEP_EHI = {DEEP_EHI};\nconstexpr int DEEP_ELO = {DEEP_ELO};\n\n",
+        f"__device__ const SegF64 SEG_F64_DEEP[{len(rd)}] = {{\n",
+    ]
+    for E, j, c, a, _ in rd:
+        dl.append("  {{" + ",".join(hexd(x) for x in a[:4]) + "}," + hexd(c) + ",{" +
+                  ",".join(hexf(x) for x in a[4:8]) + "},{0.0f,0.0f}},\n")
+    dl.append("};\n\n}  // namespace tbl\n}  // namespace qm\n")
+    with open(OUT_DEEP, "w") as f:
+        f.write("".join(dl))
     w64 = max(r[4] for r in r64)
     w32 = max(r[4] for r in r32)
     print(f"FP64 table: {len(r64)} segments, truncation <= {w64:.3g}", file=sys.stderr)
