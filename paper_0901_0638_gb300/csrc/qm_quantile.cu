@@ -21,6 +21,7 @@
 
 #include "qm.h"
 #include "qm_device.cuh"
+#include "qm_exp_map.cuh"
 #include "qm_host.h"
 #include "qm_tables_deep.h"
 
@@ -100,7 +101,7 @@ struct F64Mixed {
 struct F64Libm { __device__ double operator()(double u) const { return normcdfinv(u); } };
 
 struct ExpToNormal {
-    __device__ double operator()(double x) const { return exp_to_normal(x); }
+    __device__ double operator()(double x) const { return exp_to_normal_tbl(x); }
 };
 
 struct TMap {

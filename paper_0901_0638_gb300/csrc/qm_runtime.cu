@@ -21,6 +21,7 @@
 
 #include "qm.h"
 #include "qm_device.cuh"
+#include "qm_exp_map.cuh"
 #include "qm_host.h"
 
 namespace qm {
@@ -60,7 +61,7 @@ k_batch(const DevSeg* __restrict__ segs, int nseg, unsigned long long ntiles)
             const size_t i = base + (size_t)k * blockDim.x + threadIdx.x;
             double y;
             if (sg.kind == KIND_T) y = recycle_t<ESTRIN>(sg.tk, x[k]);
-            else if (sg.kind == KIND_EXP) y = exp_to_normal(x[k]);
+            else if (sg.kind == KIND_EXP) y = exp_to_normal_tbl(x[k]);
             else y = probit_f64_any(x[k]);
             if (i < sg.n) __stcs(sg.out + i, y);
         }
@@ -76,7 +77,7 @@ k_single(const double* __restrict__ in, double* out, size_t n, int kind, int tk)
         const double x = __ldcs(in + i);
         double y;
         if (kind == KIND_T) y = recycle_t<false>(tk, x);
-        else if (kind == KIND_EXP) y = exp_to_normal(x);
+        else if (kind == KIND_EXP) y = exp_to_normal_tbl(x);
         else y = probit_f64_any(x);
         __stcs(out + i, y);
     }
