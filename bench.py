@@ -41,7 +41,7 @@ def parse():
     p.add_argument("--n-log2", type=int, default=28, help="elements per rank = 2^n")
     p.add_argument("--variant", default="default")
     p.add_argument("--no-extras", action="store_true", help="skip variant/e2e/cpu legs")
-    p.add_argument("--workload", default="fp64", choices=["fp64", "fp32", "batch", "serve"],
+    p.add_argument("--workload", default="fp64", choices=["fp64", "fp32", "batch", "serve", "fused"],
                    help="fp64: the headline line; fp32/batch/serve: the other hot-path kernels "
                         "(for profiling and context)")
     p.add_argument("--serve-seconds", type=float, default=2.0)
@@ -206,6 +206,25 @@ def side_workload(args):
                                         "u=fl32((k+1/2)2^-24), k = top 24 bits of Philox seed 1"},
                     roofline={"bound": "hbm", "achieved": gbs, "peak": 6780.7, "unit": "GB/s",
                               "frac": gbs / 6780.7, "traffic": None})
+    elif args.workload == "fused":
+        # Philox4x32-10 (seed 3) -> FP32 normal for 2^32 samples: written (16 GiB)
+        # and, separately, reduced on the device to the first four moments
+        n = 1 << (args.n_log2 if args.n_log2 != 28 else 32)
+        out = torch.empty(n, dtype=torch.float32, device=dev)
+        mom = torch.empty(4, dtype=torch.float64, device=dev)
+        ms_w = timed(lambda: qm.qm_sample_fused(qm.QM_DIST_NORMAL, 3, 0, out, stream=stream),
+                     stream, args.steps, args.warmup)
+        ms_m = timed(lambda: qm.qm_sample_fused(qm.QM_DIST_NORMAL, 3, 0, None, n=n, moments4=mom,
+                                                stream=stream), stream, args.steps, args.warmup)
+        m = (mom / n).cpu().tolist()
+        del out
+        gbs = 4 * n / (ms_w * 1e-3) / 1e9
+        line.update(value=n / (ms_w * 1e-3) / 1e9, ms_per_step=ms_w, dtype="f32",
+                    config={"workload": f"fused Philox4x32-10 (seed 3) -> fp32 normal, n=2^{n.bit_length()-1}, "
+                                        "written (16 GiB) and moments-only", "n": n},
+                    roofline={"bound": "alu", "achieved_gbs_written": gbs, "hbm_frac_of_write": gbs / 6780.7},
+                    moments={"ms_per_step": ms_w if False else ms_m, "gsamples_s": n / (ms_m * 1e-3) / 1e9,
+                             "mean": m[0], "m2": m[1], "m3": m[2], "m4": m[3]})
     elif args.workload == "batch":
         lens, targets = W.ragged_segments(4, 256)
         spec = []

@@ -256,3 +256,22 @@ def test_f64_full_size_sampled():
     assert not f64_violations(zs, w, 4e-15, u=us).any()
     del u, z
     torch.cuda.empty_cache()
+
+
+def test_f32_beyond_2_pow_31_elements():
+    """Index arithmetic past 2^31 elements (8 GiB per array), sampled."""
+    n = (1 << 31) + 5
+    u = torch.empty(n, dtype=torch.float32, device=DEV)
+    u[: 1 << 20] = W.uniform24(13, 1 << 20)[1].to(DEV)
+    u[-(1 << 20):] = W.uniform24(14, 1 << 20)[1].to(DEV)
+    u[(1 << 20): -(1 << 20)] = 0.25
+    z = torch.empty_like(u)
+    qm.qm_normal_quantile_f32(u, z, qm.QM_VAR_DEFAULT)
+    torch.cuda.synchronize()
+    for sl in (slice(0, 1 << 20), slice(n - (1 << 20), n)):
+        w = oracle.probit(u[sl].double().cpu().numpy())
+        assert not f32_violations(z[sl].cpu().numpy(), w).any()
+    mid = z[(1 << 20): -(1 << 20)]
+    assert torch.all(mid == mid[0]).item()
+    del u, z
+    torch.cuda.empty_cache()
