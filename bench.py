@@ -45,6 +45,8 @@ def parse():
                    help="fp64: the headline line; fp32/batch/serve: the other hot-path kernels "
                         "(for profiling and context)")
     p.add_argument("--serve-seconds", type=float, default=2.0)
+    p.add_argument("--batch-hi", type=int, default=24,
+                   help="ragged batch: segment lengths log-uniform in [2^10, 2^hi]")
     return p.parse_args()
 
 
@@ -223,10 +225,10 @@ def side_workload(args):
                     config={"workload": f"fused Philox4x32-10 (seed 3) -> fp32 normal, n=2^{n.bit_length()-1}, "
                                         "written (16 GiB) and moments-only", "n": n},
                     roofline={"bound": "alu", "achieved_gbs_written": gbs, "hbm_frac_of_write": gbs / 6780.7},
-                    moments={"ms_per_step": ms_w if False else ms_m, "gsamples_s": n / (ms_m * 1e-3) / 1e9,
+                    moments={"ms_per_step": ms_m, "gsamples_s": n / (ms_m * 1e-3) / 1e9,
                              "mean": m[0], "m2": m[1], "m3": m[2], "m4": m[3]})
     elif args.workload == "batch":
-        lens, targets = W.ragged_segments(4, 256)
+        lens, targets = W.ragged_segments(4, 256, hi=args.batch_hi)
         spec = []
         keep = []
         for j, (nj, tg) in enumerate(zip(lens, targets)):
