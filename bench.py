@@ -341,8 +341,14 @@ def main():
     # roofline of the dominant kernel (k_f64_table): FP64-issue bound.
     flops = (n - n_sub - n_edge) * 10 + n_sub * 100
     achieved = flops / (ms * 1e-3) / 1e12
+    # DRAM traffic of k_f64_table from one ncu capture of the 2^24 case
+    # (profiles/k_f64_table_fp64_mixture_2p28.md: 136.5 MB read + 87.9 MB
+    # written), scaled by the elements processed to one 2^n launch
+    traffic = (136.549e6 + 87.884e6) * (n / (1 << 24)) if args.variant == "default" else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": None,
+                "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": traffic,
+                "traffic_note": "bytes per launch, scaled x(n/2^24) from a 2^24 capture; writes still in "
+                                "L2 at kernel exit are not counted (algorithmic: 16 B/element)",
                 "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe table); measured DFMA issue 1.20 TFLOP/s",
                 "hbm_view": {"achieved_gbs": 16 * n / (ms * 1e-3) / 1e9, "peak_gbs": 6780.7,
                              "frac": 16 * n / (ms * 1e-3) / 1e9 / 6780.7}}

@@ -29,7 +29,7 @@ static __device__ __align__(256) double g_partials[kMaxBlocks * 4];
 // Block b reduces samples [b kChunk, (b+1) kChunk) into g-scratch slot b,
 // every slot it owns being overwritten (nothing needs clearing between calls).
 __global__ void __launch_bounds__(kBlock)
-k_moments_chunked(uint64_t key, uint64_t blk0, size_t n, double* partials)
+k_moments_chunked(PhiloxKeys K, uint64_t blk0, size_t n, double* partials)
 {
     const size_t first = (size_t)blockIdx.x * kChunk;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
@@ -39,7 +39,7 @@ k_moments_chunked(uint64_t key, uint64_t blk0, size_t n, double* partials)
     for (size_t b = threadIdx.x; b < kChunk / 4; b += kBlock) {
         const size_t i0 = first + b * 4;
         if (i0 >= n) break;
-        const uint4 w = philox_block(key, blk0 + first / 4 + b);
+        const uint4 w = philox_block_keys(K, blk0 + first / 4 + b);
         const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -50,7 +50,7 @@ k_moments_chunked(uint64_t key, uint64_t blk0, size_t n, double* partials)
             f3 = __fmaf_rn(x2, x, f3);
             f4 = __fmaf_rn(x2, x2, f4);
         }
-        if (++cnt == 4) {
+        if (++cnt == 16) {              // FP32 partials over 64 samples
             acc[0] += f1; acc[1] += f2; acc[2] += f3; acc[3] += f4;
             f1 = f2 = f3 = f4 = 0.f;
             cnt = 0;
@@ -129,7 +129,7 @@ extern "C" qm_status qm_sample_moments_noalloc(uint64_t key, uint64_t ctr0, size
     if (!scratch) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const int nblocks = n == 0 ? 0 : (int)((n + kChunk - 1) / kChunk);
-    if (nblocks > 0) k_moments_chunked<<<nblocks, kBlock, 0, s>>>(key, ctr0 / 4, n, scratch);
+    if (nblocks > 0) k_moments_chunked<<<nblocks, kBlock, 0, s>>>(philox_keys(key), ctr0 / 4, n, scratch);
     k_sum_slots<<<1, 128, 0, s>>>(scratch, nblocks, moments4);
     return check_launch("moments (no allocation)");
 }

@@ -458,7 +458,7 @@ __device__ __forceinline__ uint32_t word_of(uint4 b, unsigned j)
 }
 
 __global__ void __launch_bounds__(256)
-k_philox_fill(uint64_t key, uint64_t ctr0, uint32_t* out, size_t n)
+k_philox_fill(PhiloxKeys K, uint64_t ctr0, uint32_t* out, size_t n)
 {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     const uint64_t first_blk = ctr0 >> 2;
@@ -466,7 +466,7 @@ k_philox_fill(uint64_t key, uint64_t ctr0, uint32_t* out, size_t n)
     // thread t produces words of blocks first_blk + t, + stride, ...
     const size_t nblk = (off + n + 3) / 4;
     for (size_t b = (size_t)blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += stride) {
-        const uint4 w = philox_block(key, first_blk + b);
+        const uint4 w = philox_block_keys(K, first_blk + b);
 #pragma unroll
         for (unsigned j = 0; j < 4; ++j) {
             const long long i = (long long)(b * 4 + j) - (long long)off;
@@ -515,11 +515,11 @@ __global__ void k_sum_partials(const double* partials, int nblocks, double* mome
     if (lane == 0) moments[k] = v;
 }
 
-// Moments are accumulated per thread in FP32 over 16 samples (4 Philox
+// Moments are accumulated per thread in FP32 over 64 samples (16 Philox
 // blocks), then folded into FP64 accumulators.
 template <bool OUT, bool MOM>
 __global__ void __launch_bounds__(256)
-k_fused_normal_f32(uint64_t key, uint64_t blk0, size_t n, float* out, double* partials)
+k_fused_normal_f32(PhiloxKeys K, uint64_t blk0, size_t n, float* out, double* partials)
 {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     const size_t nblk = (n + 3) / 4;
@@ -528,7 +528,7 @@ k_fused_normal_f32(uint64_t key, uint64_t blk0, size_t n, float* out, double* pa
     int cnt = 0;
     const bool vec_ok = OUT && ((uintptr_t)out % 16 == 0);
     for (size_t b = (size_t)blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += stride) {
-        const uint4 w = philox_block(key, blk0 + b);
+        const uint4 w = philox_block_keys(K, blk0 + b);
         float z[4];
         z[0] = probit_grid24_tbl(w.x >> 8);
         z[1] = probit_grid24_tbl(w.y >> 8);
@@ -555,7 +555,7 @@ k_fused_normal_f32(uint64_t key, uint64_t blk0, size_t n, float* out, double* pa
                 f3 = __fmaf_rn(x2, x, f3);
                 f4 = __fmaf_rn(x2, x2, f4);
             }
-            if (++cnt == 4) {
+            if (++cnt == 16) {
                 acc[0] += f1; acc[1] += f2; acc[2] += f3; acc[3] += f4;
                 f1 = f2 = f3 = f4 = 0.f;
                 cnt = 0;
@@ -596,7 +596,7 @@ __device__ __forceinline__ double normal_from_d_vote(double d, bool upper, bool 
 
 template <int KIND, bool OUT, bool MOM>
 __global__ void __launch_bounds__(256)
-k_fused_f64(uint64_t key, uint64_t blk0, size_t n, double* out, double* partials, int tk)
+k_fused_f64(PhiloxKeys K, uint64_t blk0, size_t n, double* out, double* partials, int tk)
 {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     const size_t nblk = (n + 1) / 2;
@@ -606,7 +606,7 @@ k_fused_f64(uint64_t key, uint64_t blk0, size_t n, double* out, double* partials
     for (size_t wb = warp0; wb < nblk; wb += stride) {
         const size_t b = wb + lane;
         const bool valid = b < nblk;
-        const uint4 w = philox_block(key, blk0 + b);
+        const uint4 w = philox_block_keys(K, blk0 + b);
         double z[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -764,11 +764,11 @@ extern "C" qm_status qm_philox_fill_u32(uint64_t key, uint64_t ctr0, uint32_t* o
     if (n == 0) return QM_OK;
     if (!out) return fail(QM_ERR_INVALID, "qm_philox_fill_u32: null pointer");
     const int g = grid_for(k_philox_fill, 256, (n + 3) / 4 + 1);
-    k_philox_fill<<<g, 256, 0, (cudaStream_t)stream>>>(key, ctr0, out, n);
+    k_philox_fill<<<g, 256, 0, (cudaStream_t)stream>>>(philox_keys(key), ctr0, out, n);
     return check_launch("philox fill");
 }
 
-extern "C" qm_status qm_sample_fused(int target, const qm_params* p, uint64_t key, uint64_t ctr0,
+extern "C" qm_status qm_sample_fused(int target, const qm_params* p, uint64_t key_in, uint64_t ctr0,
                                     void* out, int out_is_f64, size_t n, double* moments4,
                                     void* stream)
 {
@@ -792,12 +792,13 @@ extern "C" qm_status qm_sample_fused(int target, const qm_params* p, uint64_t ke
             g = grid_for(k_fused_normal_f32<true, true>, B, nblk);
             part = partials_scratch(g);
             if (!part) return fail(QM_ERR_NOMEM, "qm_sample_fused: scratch allocation failed");
-            if (out) k_fused_normal_f32<true, true><<<g, B, 0, s>>>(key, ctr0 / 4, n, (float*)out, part);
-            else k_fused_normal_f32<false, true><<<g, B, 0, s>>>(key, ctr0 / 4, n, nullptr, part);
+            const PhiloxKeys K = philox_keys(key_in);
+            if (out) k_fused_normal_f32<true, true><<<g, B, 0, s>>>(K, ctr0 / 4, n, (float*)out, part);
+            else k_fused_normal_f32<false, true><<<g, B, 0, s>>>(K, ctr0 / 4, n, nullptr, part);
             k_sum_partials<<<1, 128, 0, s>>>(part, g, moments4);
         } else {
             g = grid_for(k_fused_normal_f32<true, false>, B, nblk);
-            k_fused_normal_f32<true, false><<<g, B, 0, s>>>(key, ctr0 / 4, n, (float*)out, nullptr);
+            k_fused_normal_f32<true, false><<<g, B, 0, s>>>(philox_keys(key_in), ctr0 / 4, n, (float*)out, nullptr);
         }
         return check_launch("fused normal f32");
     }
@@ -818,6 +819,7 @@ extern "C" qm_status qm_sample_fused(int target, const qm_params* p, uint64_t ke
         }
         double* o = (double*)out;
         const uint64_t b0 = ctr0 / 4;
+        const PhiloxKeys key = philox_keys(key_in);
         if (target == QM_DIST_STUDENT_T) tk = t_index(p->nu);
 #define QM_LAUNCH_F64(KIND)                                                                  \
     if (o && part) k_fused_f64<KIND, true, true><<<g, B, 0, s>>>(key, b0, n, o, part, tk);   \

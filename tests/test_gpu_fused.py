@@ -54,9 +54,9 @@ def test_fused_moments_against_fp64_reduction_and_normal_law():
     ref = torch.stack([z.sum(), (z**2).sum(), (z**3).sum(), (z**4).sum()])
     absz = z.abs()
     scale = torch.stack([absz.sum(), (absz**2).sum(), (absz**3).sum(), (absz**4).sum()])
-    # FP32 partials over 16 samples: per-sample rounding <= ~(16 + 3) 2^-24
+    # FP32 partials over 64 samples: per-sample rounding <= ~(64 + 3) 2^-24
     # of |z|^k, so the sums agree to that fraction of sum |z|^k.
-    assert torch.all((mom - ref).abs() <= 20 * 2.0**-24 * scale), (mom, ref)
+    assert torch.all((mom - ref).abs() <= 67 * 2.0**-24 * scale), (mom, ref)
     m = (mom / n).cpu().numpy()
     # 5 sigma bounds for the sample moments of N(0,1) at n = 2^24
     sd = np.sqrt(np.array([1.0, 2.0, 15.0, 96.0]) / n)
