@@ -54,7 +54,7 @@ typedef enum {
 
 /* Algorithm variants of the normal quantile. */
 typedef enum {
-    QM_VAR_DEFAULT = 0,      /* TABLE (FP32 and FP64)                           */
+    QM_VAR_DEFAULT = 0,      /* FP32: TABLE; FP64: FIXED                        */
     QM_VAR_BRANCHFREE = 1,   /* exponential coordinate, one rational for the
                                 whole range (FP32: Sec. 6.1 form z = v P/Q on
                                 v <= 25; FP64: Sec. 7.2 form on v <= 42 plus a
@@ -69,11 +69,17 @@ typedef enum {
     QM_VAR_SQRT_FORM = 5,    /* FP32: exponential coordinate with a two-float
                                 logarithm, z = v sqrt(R(v)), R = (Q(v)/v)^2     */
     QM_VAR_CUDA_LIBM = 6,    /* comparator: CUDA's normcdfinvf / normcdfinv     */
-    QM_VAR_TABLE = 7         /* exponential coordinate without log or divide:
+    QM_VAR_TABLE = 7,        /* exponential coordinate without log or divide:
                                 x = 2d = 2^E m, segment (E, top bits of m),
                                 r = m c - 1, |z| = local expansion G(r) of Q(v)
                                 from the recycling ODE (FP64: d >= 2^-65, the
                                 deep tail compacted to the deep rational)       */
+    QM_VAR_FIXED = 8         /* FP64: the same segment expansions (Sec. 2.3,
+                                Sec. 6) in an exact integer offset t from the
+                                segment anchor, evaluated in 64-bit fixed
+                                point with one FP64 FMA, |z| = a0 + t H(t);
+                                every 0 < u < 1 (subnormal u too) takes the
+                                same path.  The FP64 default.                   */
 } qm_variant;
 
 typedef struct {
@@ -83,7 +89,7 @@ typedef struct {
 /* ---- normal quantile ------------------------------------------------------
  * z[i] = Phi^{-1}(u[i]) for i < n (Sec. 1, Eq. 1).  FP32 variants: DEFAULT,
  * BRANCHFREE, SQRT_FORM, TABLE, CUDA_LIBM; FP64 variants: DEFAULT, BRANCHFREE,
- * HYBRID_VOTE, MIXED_HALLEY, COMPACT, TABLE, CUDA_LIBM (others:
+ * HYBRID_VOTE, MIXED_HALLEY, COMPACT, TABLE, FIXED, CUDA_LIBM (others:
  * QM_ERR_INVALID).
  * u, z: contiguous arrays of n elements (device).                           */
 qm_status qm_normal_quantile_f32(const float* u, float* z, size_t n,
@@ -129,10 +135,11 @@ qm_status qm_sample_fused(int target, const qm_params* p, uint64_t key,
 /* ---- fused moments without allocation ---------------------------------------
  * Same sums as qm_sample_fused(QM_DIST_NORMAL, NULL, key, ctr0, NULL, 0, n,
  * moments4, stream) (up to the order of the FP64 additions), for callers that
- * must not allocate device memory at call time: inside a stream capture or a
- * stream-ordered pipeline that cannot synchronise, in allocator-less runtimes,
- * or in callbacks running while a caching allocator is locked.  The paper has
- * no counterpart; this is a property of the library interface.
+ * must not allocate device memory at call time: cudaMalloc can synchronise
+ * the device, which a latency-bound pipeline cannot afford; embedded runtimes
+ * plan all device memory up front and have no allocator to call; code that
+ * runs while a caching allocator holds its lock would deadlock on it.  The
+ * paper has no counterpart; this is a property of the library interface.
  * Scratch is a file-scope device array of 16384 x 4 doubles (512 KiB) that
  * every device loading the library keeps until the process exits; a call
  * makes no cudaMalloc/cudaFree and no allocating library call.

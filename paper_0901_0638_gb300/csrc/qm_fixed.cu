@@ -1,0 +1,177 @@
+// qm_fixed.cu -- FP64 normal quantile from the exponential-coordinate segment
+// table, evaluated in 64-bit fixed point (QM_VAR_FIXED, the FP64 default).
+//
+// Phi^{-1}(u) through the paper's change of variable v = -log(2d),
+// d = min(u, 1-u) (Sec. 6, Sec. 7.2), without forming v: x = 2d = M 2^(E-52)
+// with a 53-bit integer significand M; (E, top K bits of M) select a segment
+// whose local expansion G of Q(v) = Phi^{-1}(1 - e^{-v}/2) comes from the
+// recycling ODE Q'' + Q' = Q Q'^2 (Sec. 2.3, Sec. 6).  With the unsigned
+// offset t_u = T 2^-52 from the segment anchor (T an exact integer) and
+// tau = t_u 2^K in [0, 1]:
+//
+//     |z| = a0 + sigma t_u |H|,   |H| = beta_0 + tau (beta_1 + tau (beta_2 + tau F)),
+//     F   = beta_3 + tau (beta_4 + tau (beta_5 + tau beta_6))   (single precision)
+//
+// The Horner steps for beta_0..beta_2 run on signed 64-bit accumulators times
+// tau as an unsigned Q0.64 integer (unsigned mulhi plus a sign correction),
+// the reflection d = 1 - u and the normalisation of x are integer
+// operations, and t_u and |H| become doubles by bit assembly, so the only
+// FP64 instruction per element is the final FMA.  GB300 issues FP64 at about
+// 1/62 of its FP32 rate; the integer pipes carry the rest.
+//
+// Every 0 < u < 1 (subnormal u included) takes the same path: binades
+// e = -1 - E < 64 have 64 segments, deeper ones (down to x = 2^-1073) 32.
+// u = 1/2 gives +0, u = 0 gives -inf, u = 1 gives +inf, anything else NaN.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qm.h"
+#include "qm_fx_tables.h"
+#include "qm_host.h"
+
+namespace qm {
+namespace {
+
+constexpr int kBlock = 256;
+
+// floor(a b / 2^64) for signed a and unsigned b
+__device__ __forceinline__ long long mulhi_su(long long a, unsigned long long b)
+{
+    const unsigned long long h = __umul64hi((unsigned long long)a, b);
+    return (long long)(h - (a < 0 ? b : 0ull));
+}
+
+// |Phi^{-1}(u)| bits for 0 < u < 1 (other inputs give an unused value; the
+// table index is in range for every bit pattern).
+__device__ __forceinline__ unsigned long long probit_mag_fx(unsigned long long ub)
+{
+    // x = 2d = S 2^(base - 52): u >= 1/2 -> S = 2^52 - frac (1 - u exact),
+    // u < 1/2 -> S = significand of u (no implicit bit when subnormal)
+    const bool upper = ub >= 0x3FE0000000000000ull;
+    const unsigned long long frac = ub & 0x000FFFFFFFFFFFFFull;
+    const int eb = (int)(ub >> 52) & 0x7ff;
+    const unsigned long long S = upper ? (1ull << 52) - frac : (eb ? (frac | (1ull << 52)) : frac);
+    const int base = upper ? 0 : max(eb, 1) - 1022;
+    const int lz = __clzll(S | 1ull) - 11;
+    const unsigned long long Mx = S << lz;                      // 2^52 <= Mx < 2^53
+    const int e = -1 - (base - lz);                             // binade: x in [2^-e-1, 2^-e)
+    const int ec = min(max(e, 0), fxt::E_LAST);
+    const bool mainb = ec < fxt::E_MAIN;
+    const int K = mainb ? fxt::K_MAIN : fxt::K_DEEP;
+    const int sK = 52 - K;
+    const unsigned j = (unsigned)(Mx >> sK) & ((1u << K) - 1u);
+    const int idx = mainb ? (ec << fxt::K_MAIN) + (int)j
+                          : fxt::N_MAIN + ((ec - fxt::E_MAIN) << fxt::K_DEEP) + (int)j;
+    const bool top = (ec == 0) && (j == (1u << fxt::K_MAIN) - 1u);
+    // offset from the anchor: segment start, or x = 1 on the top segment
+    const unsigned long long Tu = top ? (1ull << 53) - Mx : Mx & ((1ull << sK) - 1ull);
+    const unsigned long long Tau = (Tu << (12 + K)) - (Tu >> sK);   // tau 2^64 (tau = 1 -> 1 - 2^-64)
+
+    const fxt::SegFx* p = &fxt::SEG_FX[idx];
+    const double2 q0 = __ldg(reinterpret_cast<const double2*>(p));                 // a0, B0
+    const longlong2 q1 = __ldg(reinterpret_cast<const longlong2*>(p) + 1);         // B1, B2
+    const float4 q2 = __ldg(reinterpret_cast<const float4*>(p) + 2);               // beta_3..6
+    const int4 q3 = __ldg(reinterpret_cast<const int4*>(p) + 3);                   // s0, 2^c, sh
+
+    // single-precision tail from the top bits of the offset
+    const float tf = __uint_as_float(0x4B000000u | (unsigned)(Tu >> 25)) - 8388608.0f;
+    const float tau_f = tf * __uint_as_float((unsigned)(127 + K - 27) << 23);
+    float F = __fmaf_rn(q2.w, tau_f, q2.z);
+    F = __fmaf_rn(F, tau_f, q2.y);
+    F = __fmaf_rn(F, tau_f, q2.x);
+    const int i3 = __float2int_rn(F * __int_as_float(q3.y));
+    long long acc = (long long)((unsigned long long)(long long)i3 << q3.z);
+    acc = q1.y + mulhi_su(acc, Tau);
+    acc = q1.x + mulhi_su(acc, Tau);
+    acc = __double_as_longlong(q0.y) + mulhi_su(acc, Tau);        // |H| 2^-s0, in (0, 2^62)
+
+    // |H| as a double: normalise, round to 53 bits, insert the exponent
+    const unsigned long long ha = (unsigned long long)acc;
+    const int lh = __clzll(ha);
+    const unsigned long long hm = ((ha << lh) + 0x400ull) >> 11;
+    const unsigned long long hbits = hm + ((unsigned long long)(1022 + 63 - lh + q3.x) << 52);
+    // sigma t_u as a double (exact: Tu < 2^47)
+    const int lt = __clzll(Tu | 1ull);
+    const unsigned long long tm = Tu << (lt - 11);
+    const unsigned long long tbits = (Tu == 0) ? 0ull
+        : (tm + ((unsigned long long)(1033 - lt) << 52)) | (top ? 0ull : (1ull << 63));
+    const double g = __fma_rn(__longlong_as_double((long long)tbits),
+                              __longlong_as_double((long long)hbits), q0.x);
+    return (e < 0) ? 0ull : (unsigned long long)__double_as_longlong(g);
+}
+
+__device__ __forceinline__ double probit_fx(double u)
+{
+    const unsigned long long ub = (unsigned long long)__double_as_longlong(u);
+    unsigned long long mb = probit_mag_fx(ub);
+    const bool valid = (long long)ub > 0 && ub < 0x3FF0000000000000ull;     // 0 < u < 1
+    if (!valid) {
+        mb = (ub & 0x7fffffffffffffffull) == 0 ? 0xfff0000000000000ull      // +-0 -> -inf
+           : (ub == 0x3FF0000000000000ull ? 0x7ff0000000000000ull           // 1 -> +inf
+                                          : 0x7ff8000000000000ull);         // NaN
+    } else if (ub < 0x3FE0000000000000ull) {
+        mb |= 1ull << 63;                                                    // u < 1/2
+    }
+    return __longlong_as_double((long long)mb);
+}
+
+template <int U>
+__global__ void __launch_bounds__(kBlock)
+k_f64_fixed(const double* __restrict__ in, double* out, size_t n)
+{
+    const size_t nv = n / 2;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const double2* vin = reinterpret_cast<const double2*>(in);
+    double2* vout = reinterpret_cast<double2*>(out);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride * U) {
+        double2 a[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k)
+            if (i + k * stride < nv) a[k] = __ldcs(vin + i + k * stride);
+#pragma unroll
+        for (int k = 0; k < U; ++k)
+            if (i + k * stride < nv)
+                __stcs(vout + i + k * stride, make_double2(probit_fx(a[k].x), probit_fx(a[k].y)));
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) out[n - 1] = probit_fx(in[n - 1]);
+}
+
+__global__ void __launch_bounds__(kBlock)
+k_f64_fixed_scalar(const double* in, double* out, size_t n)
+{
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        out[i] = probit_fx(in[i]);
+}
+
+template <class Kern>
+int grid_of(Kern k, size_t items)
+{
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, kBlock, 0) != cudaSuccess || bps < 1)
+        bps = 1;
+    const int sms = sm_count() > 0 ? sm_count() : 1;
+    size_t g = (items + kBlock - 1) / kBlock;
+    const size_t cap = (size_t)sms * bps;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+}  // namespace
+
+// Launch on `s`; u and z are device arrays of n doubles (in place allowed).
+qm_status launch_f64_fixed(const double* u, double* z, size_t n, void* stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((uintptr_t)u % 16 == 0 && (uintptr_t)z % 16 == 0) {
+        const int g = grid_of(k_f64_fixed<2>, (n / 2 + 1) / 2);
+        k_f64_fixed<2><<<g, kBlock, 0, s>>>(u, z, n);
+    } else {
+        const int g = grid_of(k_f64_fixed_scalar, n);
+        k_f64_fixed_scalar<<<g, kBlock, 0, s>>>(u, z, n);
+    }
+    return check_launch("f64 fixed");
+}
+
+}  // namespace qm

@@ -1,9 +1,10 @@
 // qm_noalloc.cu -- fused Philox -> normal moments without any allocation.
 //
 // Some callers cannot allocate device memory at the point where they need
-// the moments: code running inside a CUDA-graph capture or a stream-ordered
-// pipeline that must not synchronise, allocator-less embedded runtimes, and
-// callbacks that run while a caching allocator holds its lock.  For them this
+// the moments: cudaMalloc can synchronise the device, which a latency-bound
+// pipeline cannot afford; embedded runtimes plan all device memory up front
+// and have no allocator to call; code that runs while a caching allocator
+// holds its lock would deadlock on it.  For them this
 // entry point keeps its reduction scratch in a file-scope device array that is
 // part of the loaded module, so a call performs no cudaMalloc/cudaFree and no
 // allocating library call.  The array (kMaxBlocks x 4 doubles = 512 KiB) lives

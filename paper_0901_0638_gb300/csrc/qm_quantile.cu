@@ -521,6 +521,9 @@ template <bool OUT, bool MOM>
 __global__ void __launch_bounds__(256)
 k_fused_normal_f32(PhiloxKeys K, uint64_t blk0, size_t n, float* out, double* partials)
 {
+    __shared__ float4 stbl[kF32SmemSeg];
+    stage_f32_table(stbl);
+    __syncthreads();
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     const size_t nblk = (n + 3) / 4;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
@@ -530,10 +533,10 @@ k_fused_normal_f32(PhiloxKeys K, uint64_t blk0, size_t n, float* out, double* pa
     for (size_t b = (size_t)blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += stride) {
         const uint4 w = philox_block_keys(K, blk0 + b);
         float z[4];
-        z[0] = probit_grid24_tbl(w.x >> 8);
-        z[1] = probit_grid24_tbl(w.y >> 8);
-        z[2] = probit_grid24_tbl(w.z >> 8);
-        z[3] = probit_grid24_tbl(w.w >> 8);
+        z[0] = probit_grid24_tbl_s(w.x >> 8, stbl);
+        z[1] = probit_grid24_tbl_s(w.y >> 8, stbl);
+        z[2] = probit_grid24_tbl_s(w.z >> 8, stbl);
+        z[3] = probit_grid24_tbl_s(w.w >> 8, stbl);
         const size_t i0 = b * 4;
         const bool full = i0 + 4 <= n;
         if (OUT) {
@@ -714,12 +717,13 @@ extern "C" qm_status qm_normal_quantile_f64(const double* u, double* z, size_t n
     case QM_VAR_BRANCHFREE: return launch_map(u, z, n, F64BranchFree(), s, "f64 branch-free");
     case QM_VAR_MIXED_HALLEY: return launch_map(u, z, n, F64Mixed(), s, "f64 mixed");
     case QM_VAR_CUDA_LIBM: return launch_map(u, z, n, F64Libm(), s, "f64 normcdfinv");
+    case QM_VAR_DEFAULT:
+    case QM_VAR_FIXED: return launch_f64_fixed(u, z, n, stream);
     case QM_VAR_HYBRID_VOTE: {
         const int g = grid_for(k_f64_hybrid_vote<2>, 256, (n + 1) / 2);
         k_f64_hybrid_vote<2><<<g, 256, 0, s>>>(u, z, n);
         return check_launch("f64 hybrid vote");
     }
-    case QM_VAR_DEFAULT:
     case QM_VAR_TABLE: {
         if (u == z) {
             // the deep-tail queue re-reads the input after in-place stores

@@ -1,0 +1,237 @@
+"""Generate csrc/qm_fx_tables.h: the FP64 normal-quantile segment table for
+evaluation in 64-bit fixed point.
+
+The expansion is the one of gen_tables.py, in the paper's exponential
+coordinate v = -log(2d), d = min(u, 1-u) (Sec. 6): x = 2d = 2^E m with
+m in [1, 2); the top K bits of m select a segment of width 2^-K.  Around the
+segment centre m_c (m_c = 2 on the top segment of the top binade, where z = 0
+at x = 1) the recycling ODE of the exponential background,
+Q'' + Q' = Q Q'^2 (Sec. 2.3, Sec. 6), gives the Taylor coefficients of
+
+    |Phi^{-1}(u)| = G(t) = Q(V - log(1 + t/m_c)),  t = m - m_c,
+    V = -E ln2 - ln m_c.
+
+The kernel evaluates G in an unsigned offset t_u >= 0 from an anchor: the
+segment start m_lo (t_u = m - m_lo), or x = 1 on the top segment
+(t_u = 2 - m, G odd in t so z -> 0 with full relative accuracy).  The
+polynomial is the centre expansion re-expanded about the anchor (the same
+polynomial, so the same truncation error):
+
+    G = a_0 + sigma t_u |H(t_u)|,  |H| = sum_{k=0}^{6} beta_k tau^k,
+    tau = t_u 2^K in [0, 1],  sigma = -1 (+1 on the top segment).
+
+On GB300 the FP64 pipe issues about 1/62 of the FP32 rate, so beta_0..beta_2
+are applied by a fixed-point Horner chain on 64-bit integers with tau as an
+unsigned Q0.64 number (acc_k = B_k + mulhi(acc_{k+1}, tau 2^64), every acc in
+units of 2^s0), beta_3..beta_6 by a single-precision chain F entering as
+acc_3 = rn(F 2^c) << sh; then z = fma(sigma t_u, acc_0 2^s0, a_0) is the only
+double-precision operation.
+
+Binades: e = -1 - E in [0, 64) with K = 6, e in [64, 1072] with K = 5, so
+every double 0 < u < 1 (subnormal u included: x is normalised as an
+integer) falls in a segment.
+
+Entry (64 bytes): a0 (double), B0, B1, B2 (int64), beta_3..beta_6 (float),
+s0, 2^c (float), sh, pad.
+
+The generator checks every segment by emulating the kernel's integer and
+double-precision steps exactly (single-precision steps to within one
+rounding) at the anchor, the far end and interior points, against the
+mpmath quantile, and prints the worst relative error.
+Usage:  python -m paper_0901_0638_gb300.fit.gen_fx_tables
+"""
+from __future__ import annotations
+
+import math
+import multiprocessing as mproc
+import os
+import sys
+from fractions import Fraction
+
+import mpmath as mp
+import numpy as np
+
+from . import rode
+from . import targets as T
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+OUT = os.path.join(os.path.dirname(HERE), "csrc", "qm_fx_tables.h")
+
+DEG = 7                 # a_0..a_7
+NI = 3                  # beta_0..beta_2 in fixed point
+K_MAIN, E_MAIN = 6, 64  # binade index e = -1 - E in [0, 64): K = 6
+K_DEEP, E_LAST = 5, 1072  # e in [64, 1072]: K = 5 (x down to 2^-1073)
+N_MAIN = E_MAIN << K_MAIN
+N_ALL = N_MAIN + ((E_LAST - E_MAIN + 1) << K_DEEP)
+
+
+def seg_k(e):
+    return K_MAIN if e < E_MAIN else K_DEEP
+
+
+def seg_index(e, j):
+    return (e << K_MAIN) + j if e < E_MAIN else N_MAIN + ((e - E_MAIN) << K_DEEP) + j
+
+
+def is_top(e, j, K):
+    return e == 0 and j == 2**K - 1
+
+
+def centre_int(e, j, K):
+    """Integer segment centre M_c of the 53-bit significand M of x."""
+    if is_top(e, j, K):
+        return 2**53
+    return 2**52 + j * 2**(52 - K) + 2**(51 - K)
+
+
+def taylor(e, j, K):
+    """Coefficients of G about the anchor, in t_u (see the module docstring)."""
+    mp.mp.dps = 50
+    E = -1 - e
+    top = is_top(e, j, K)
+    mc = mp.mpf(centre_int(e, j, K)) / 2**52
+    if top:
+        V = mp.mpf(0)
+        q0, q1 = mp.mpf(0), mp.sqrt(mp.pi / 2)
+    else:
+        V = -E * mp.log(2) - mp.log(mc)
+        q0 = T.q_exp(V)
+        q1 = mp.exp(-V) / 2 / mp.npdf(q0)   # Q' = (e^{-v}/2) / phi(Q)
+    b = rode.taylor_exp_background(V, q0, q1, DEG + 2)
+    s = [mp.mpf(0)] + [mp.mpf((-1) ** n) / n / mc**n for n in range(1, DEG + 3)]   # -log(1 + t/mc)
+    a = rode.compose(b, s, DEG + 2)[:DEG + 1]
+    if top:
+        return [a[k] * (-1) ** k for k in range(DEG + 1)]         # t_u = -t
+    h2 = mp.mpf(2) ** (-K - 1)                                    # t = t_u - 2^-K / 2
+    g = [mp.mpf(0)] * (DEG + 1)
+    for k in range(DEG + 1):
+        for i in range(k + 1):
+            g[i] += a[k] * mp.binomial(k, i) * (-h2) ** (k - i)
+    return g
+
+
+def f32(x):
+    return float(np.float32(float(x)))
+
+
+def quantise(e, j, K, g):
+    beta = [g[k + 1] * mp.mpf(2) ** (-K * k) for k in range(DEG)]
+    sigma = 1 if beta[0] > 0 else -1
+    assert sigma == (1 if is_top(e, j, K) else -1), (e, j)
+    beta = [sigma * x for x in beta]
+    hmax = sum(abs(x) for x in beta)                              # tau in [0, 1]
+    s0 = int(mp.floor(mp.log(hmax, 2))) + 1 - 62                  # |acc| < 2^62
+    B = [int(mp.nint(beta[k] / mp.mpf(2) ** s0)) for k in range(NI)]
+    bf = [f32(beta[k]) for k in range(NI, DEG)]
+    fmax = sum(abs(beta[k]) for k in range(NI, DEG))
+    c = 30 - int(mp.ceil(mp.log(fmax, 2)))                        # |F 2^c| <= 2^30
+    sh = -s0 - c
+    if sh < 0:
+        c += sh
+        sh = 0
+    assert 0 <= sh <= 62 and -120 < c < 120, (e, j, c, sh)
+    return {"a0": float(g[0]), "B": B, "bf": bf, "s0": s0, "c": c, "sh": sh, "sigma": sigma}
+
+
+def emulate(q, K, top, Tu):
+    """The kernel's arithmetic for the integer offset Tu; returns the double z."""
+    Tau = (Tu << (12 + K)) - (Tu >> (52 - K))                     # tau = 1 -> 1 - 2^-64
+    assert 0 <= Tau < 2**64
+    tf = f32(float(Tu >> 25)) * 2.0 ** (K - 27)
+    F = np.float32(q["bf"][-1])
+    for cf in reversed(q["bf"][:-1]):
+        F = np.float32(float(F) * tf + cf)
+    i3 = int(round(float(np.float32(float(F) * 2.0 ** q["c"]))))
+    assert abs(i3) < 2**31
+    acc = i3 << q["sh"]
+    for k in reversed(range(NI)):
+        acc = q["B"][k] + ((acc * Tau) >> 64)
+        assert abs(acc) < 2**63
+    assert 0 < acc < 2**62
+    lz = 64 - acc.bit_length()
+    mant = ((acc << lz) + 0x400) >> 11                            # rounded 53-bit significand
+    hd = float(Fraction(mant) * Fraction(2) ** (63 - lz - 52 + q["s0"]))
+    t = Fraction(Tu) * Fraction(2) ** -52 * q["sigma"]
+    return float(t * Fraction(hd) + Fraction(q["a0"]))
+
+
+def truth(e, Mx):
+    mp.mp.dps = 40
+    x = mp.mpf(Mx) * mp.mpf(2) ** (-1 - e - 52)
+    if x == 1:
+        return mp.mpf(0)
+    return T.upper_probit(x / 2)
+
+
+def job(args):
+    e, j = args
+    K = seg_k(e)
+    top = is_top(e, j, K)
+    g = taylor(e, j, K)
+    q = quantise(e, j, K, g)
+    full = 2**(52 - K)
+    if top:
+        pts = [1, 2, 3, full // 2, full - 1, full]
+    elif e < E_MAIN:
+        pts = [0, 1, full // 3, full // 2, full - 1]
+    else:
+        pts = [0, full // 2, full - 1]
+    worst = 0.0
+    for Tu in pts:
+        z = emulate(q, K, top, Tu)
+        Mx = 2**53 - Tu if top else 2**52 + j * full + Tu
+        w = truth(e, Mx)
+        if w != 0:
+            worst = max(worst, float(abs(mp.mpf(z) / w - 1)))
+    return (e, j, q, worst)
+
+
+def hexd(x):
+    return float(x).hex()
+
+
+def hexf(x):
+    return float(np.float32(x)).hex() + "f"
+
+
+def main():
+    jobs = [(e, j) for e in range(0, E_LAST + 1) for j in range(2**seg_k(e))]
+    with mproc.Pool(max(1, os.cpu_count() or 1)) as pool:
+        res = pool.map(job, jobs, chunksize=32)
+    res.sort(key=lambda r: seg_index(r[0], r[1]))
+    assert len(res) == N_ALL
+    worst = max(r[3] for r in res)
+    print(f"fixed-point FP64 table: {len(res)} segments, emulated worst relative error {worst:.3g}",
+          file=sys.stderr)
+    lines = [
+        "// Generated by paper_0901_0638_gb300/fit/gen_fx_tables.py -- do not edit.\n",
+        "// FP64 normal quantile, exponential coordinate, segment expansions of\n",
+        "// G(t) = Q(V - log(1 + t/m_c)) from the recycling ODE Q'' + Q' = Q Q'^2,\n",
+        "// re-expanded about the anchor and stored for fixed-point evaluation:\n",
+        "// G = a0 + sigma t_u |H|, |H| = sum beta_k tau^k, tau = t_u 2^K in [0, 1],\n",
+        "// beta_0..2 as int64 B_k = beta_k 2^-s0, beta_3..6 as float.\n",
+        f"// Binade e = -1 - E: K = {K_MAIN} for e < {E_MAIN}, K = {K_DEEP} for e = {E_MAIN}..{E_LAST}.\n",
+        f"// Index e 2^{K_MAIN} + j (e < {E_MAIN}), {N_MAIN} + (e - {E_MAIN}) 2^{K_DEEP} + j.\n",
+        f"// Emulated worst relative error over the checked points: {worst:.3g}.\n",
+        "#pragma once\n#include <stdint.h>\n\nnamespace qm {\nnamespace fxt {\n\n",
+        f"constexpr int K_MAIN = {K_MAIN};\nconstexpr int E_MAIN = {E_MAIN};\n",
+        f"constexpr int K_DEEP = {K_DEEP};\nconstexpr int E_LAST = {E_LAST};\n",
+        f"constexpr int N_MAIN = {N_MAIN};\nconstexpr int N_ALL = {N_ALL};\n\n",
+        "struct alignas(64) SegFx {\n"
+        "    double a0;\n    long long B0, B1, B2;\n    float f3, f4, f5, f6;\n"
+        "    int s0;\n    float csc;\n    int sh;\n    int pad;\n};\n\n",
+        f"__device__ const SegFx SEG_FX[{N_ALL}] = {{\n",
+    ]
+    for e, j, q, _ in res:
+        B = q["B"]
+        lines.append("  {" + hexd(q["a0"]) + "," + ",".join(f"{b}ll" for b in B) + "," +
+                     ",".join(hexf(x) for x in q["bf"]) + f",{q['s0']}," +
+                     hexf(2.0 ** q["c"]) + f",{q['sh']},0}},\n")
+    lines.append("};\n\n}  // namespace fxt\n}  // namespace qm\n")
+    with open(OUT, "w") as f:
+        f.write("".join(lines))
+    print("wrote", OUT, file=sys.stderr)
+
+
+if __name__ == "__main__":
+    main()

@@ -22,7 +22,7 @@ F32_VARIANTS = {"default": qm.QM_VAR_DEFAULT, "sqrt_form": qm.QM_VAR_SQRT_FORM,
                 "table": qm.QM_VAR_TABLE}
 F64_VARIANTS = {"default": qm.QM_VAR_DEFAULT, "branchfree": qm.QM_VAR_BRANCHFREE,
                 "hybrid_vote": qm.QM_VAR_HYBRID_VOTE, "mixed_halley": qm.QM_VAR_MIXED_HALLEY,
-                "compact": qm.QM_VAR_COMPACT, "table": qm.QM_VAR_TABLE}
+                "compact": qm.QM_VAR_COMPACT, "table": qm.QM_VAR_TABLE, "fixed": qm.QM_VAR_FIXED}
 
 
 def run_f32(u_host: np.ndarray, variant) -> np.ndarray:
@@ -216,10 +216,37 @@ def test_f64_symmetry_bit_exact():
     k = rng.integers(1, 2**52, size=1 << 18, dtype=np.int64)
     u = k.astype(np.float64) * 2.0**-53
     v = (2**53 - k).astype(np.float64) * 2.0**-53
-    for name in ("branchfree", "compact", "hybrid_vote", "mixed_halley", "table"):
+    for name in ("branchfree", "compact", "hybrid_vote", "mixed_halley", "table", "fixed"):
         a = run_f64(u, F64_VARIANTS[name])
         b = run_f64(v, F64_VARIANTS[name])
         assert np.array_equal(a, -b), name
+
+
+def test_f64_fixed_every_segment():
+    """Every segment of the fixed-point table (x = 2d = M 2^(E-52), binades
+    E = -1..-1073, 64 or 32 segments each) at its start, start + 1 ulp,
+    centre and last point, for u = d and, where 1 - d is exact, u = 1 - d."""
+    ms, es = [], []
+    for e in range(0, 1073):
+        K = 6 if e < 64 else 5
+        j = np.arange(2**K, dtype=np.int64)
+        lo = 2**52 + j * 2**(52 - K)
+        for off in (0, 1, 2**(51 - K), 2**(52 - K) - 1):
+            ms.append(lo + off)
+            es.append(np.full(j.size, e))
+    M = np.concatenate(ms).astype(np.float64)          # exact (< 2^53)
+    E = np.concatenate(es)
+    d = np.ldexp(M, -E - 54)                           # u = d = x/2
+    up = E <= 50
+    u = np.concatenate([d, 1.0 - d[up]])
+    w = oracle.probit(u)
+    z = run_f64(u, qm.QM_VAR_FIXED)
+    bad = f64_violations(z, w, 4e-15, u=u)
+    assert not bad.any(), (int(bad.sum()), u[bad][:5], z[bad][:5], w[bad][:5])
+    sub = (u > 0) & (u < 1e-300)
+    assert np.all(rel_err(z[sub], w[sub]) < 1e-12)
+    dom = (u >= 1e-300) & (u <= 1 - 2.0**-53)
+    print(f"fixed, every segment: max rel {rel_err(z, w)[dom].max():.3g}")
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 1023, 1025, 65537])

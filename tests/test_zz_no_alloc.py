@@ -1,8 +1,9 @@
 """The allocation-free moments entry point (qm_sample_moments_noalloc).
 
-Callers that cannot allocate at call time -- code inside a stream capture, an
-allocator-less runtime, a callback that runs while a caching allocator is
-locked -- get the fused Philox -> normal moments from a static scratch array.
+Callers that cannot allocate at call time -- a latency-bound pipeline that
+cannot let cudaMalloc synchronise the device, an embedded runtime that plans
+all device memory up front, code that runs while a caching allocator holds its
+lock -- get the fused Philox -> normal moments from a static scratch array.
 This file is collected last on purpose: if it fails, a run that stops at the
 first failure has already run every other test.  It must pass alone in a fresh
 process and after the other tests.
