@@ -5,19 +5,21 @@
 // d = min(u, 1-u) (Sec. 6, Sec. 7.2), without forming v: x = 2d = M 2^(E-52)
 // with a 53-bit integer significand M; (E, top K bits of M) select a segment
 // whose local expansion G of Q(v) = Phi^{-1}(1 - e^{-v}/2) comes from the
-// recycling ODE Q'' + Q' = Q Q'^2 (Sec. 2.3, Sec. 6).  With the unsigned
-// offset t_u = T 2^-52 from the segment anchor (T an exact integer) and
-// tau = t_u 2^K in [0, 1]:
+// recycling ODE Q'' + Q' = Q Q'^2 (Sec. 2.3, Sec. 6).  With the offset
+// t_u = T 2^-52 > 0 back from the segment's end (T an exact integer; the end
+// of the top segment is x = 1, where z = 0) and tau = t_u 2^K in (0, 1]:
 //
-//     |z| = a0 + sigma t_u |H|,   |H| = beta_0 + tau (beta_1 + tau (beta_2 + tau F)),
+//     |z| = a0 + t_u H,   H = beta_0 + tau (beta_1 + tau (beta_2 + tau F)) > 0,
 //     F   = beta_3 + tau (beta_4 + tau (beta_5 + tau beta_6))   (single precision)
 //
 // The Horner steps for beta_0..beta_2 run on signed 64-bit accumulators times
 // tau as an unsigned Q0.64 integer (unsigned mulhi plus a sign correction),
 // the reflection d = 1 - u and the normalisation of x are integer
-// operations, and t_u and |H| become doubles by bit assembly, so the only
+// operations, and t_u and H become doubles by bit assembly, so the only
 // FP64 instruction per element is the final FMA.  GB300 issues FP64 at about
-// 1/62 of its FP32 rate; the integer pipes carry the rest.
+// 1/62 of its FP32 rate; the integer pipes carry the rest.  A segment's 64
+// bytes arrive in two 256-bit loads (each lane gathers a random segment, and
+// the L1 cost of a gather grows with the number of load instructions).
 //
 // Every 0 < u < 1 (subnormal u included) takes the same path: binades
 // e = -1 - E < 64 have 64 segments, deeper ones (down to x = 2^-1073) 32.
@@ -33,6 +35,14 @@ namespace qm {
 namespace {
 
 constexpr int kBlock = 256;
+
+// 32 bytes from the read-only path in one 256-bit load
+__device__ __forceinline__ void ld256(const void* p, unsigned long long& a, unsigned long long& b,
+                                      unsigned long long& c, unsigned long long& d)
+{
+    asm("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];"
+        : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
+}
 
 // floor(a b / 2^64) for signed a and unsigned b
 __device__ __forceinline__ long long mulhi_su(long long a, unsigned long long b)
@@ -62,41 +72,37 @@ __device__ __forceinline__ unsigned long long probit_mag_fx(unsigned long long u
     const unsigned j = (unsigned)(Mx >> sK) & ((1u << K) - 1u);
     const int idx = mainb ? (ec << fxt::K_MAIN) + (int)j
                           : fxt::N_MAIN + ((ec - fxt::E_MAIN) << fxt::K_DEEP) + (int)j;
-    const bool top = (ec == 0) && (j == (1u << fxt::K_MAIN) - 1u);
-    // offset from the anchor: segment start, or x = 1 on the top segment
-    const unsigned long long Tu = top ? (1ull << 53) - Mx : Mx & ((1ull << sK) - 1ull);
+    // offset back from the segment end: Tu in [1, 2^sK]
+    const unsigned long long Tu = (1ull << sK) - (Mx & ((1ull << sK) - 1ull));
     const unsigned long long Tau = (Tu << (12 + K)) - (Tu >> sK);   // tau 2^64 (tau = 1 -> 1 - 2^-64)
 
     const fxt::SegFx* p = &fxt::SEG_FX[idx];
-    const double2 q0 = __ldg(reinterpret_cast<const double2*>(p));                 // a0, B0
-    const longlong2 q1 = __ldg(reinterpret_cast<const longlong2*>(p) + 1);         // B1, B2
-    const float4 q2 = __ldg(reinterpret_cast<const float4*>(p) + 2);               // beta_3..6
-    const int4 q3 = __ldg(reinterpret_cast<const int4*>(p) + 3);                   // s0, 2^c, sh
+    unsigned long long a0b, B0, B1, B2, f34, f56, s0c, shp;
+    ld256(p, a0b, B0, B1, B2);                                     // a0, B0, B1, B2
+    ld256(reinterpret_cast<const char*>(p) + 32, f34, f56, s0c, shp);   // beta_3..6, s0, 2^c, sh
 
     // single-precision tail from the top bits of the offset
     const float tf = __uint_as_float(0x4B000000u | (unsigned)(Tu >> 25)) - 8388608.0f;
     const float tau_f = tf * __uint_as_float((unsigned)(127 + K - 27) << 23);
-    float F = __fmaf_rn(q2.w, tau_f, q2.z);
-    F = __fmaf_rn(F, tau_f, q2.y);
-    F = __fmaf_rn(F, tau_f, q2.x);
-    const int i3 = __float2int_rn(F * __int_as_float(q3.y));
-    long long acc = (long long)((unsigned long long)(long long)i3 << q3.z);
-    acc = q1.y + mulhi_su(acc, Tau);
-    acc = q1.x + mulhi_su(acc, Tau);
-    acc = __double_as_longlong(q0.y) + mulhi_su(acc, Tau);        // |H| 2^-s0, in (0, 2^62)
+    float F = __fmaf_rn(__uint_as_float((unsigned)(f56 >> 32)), tau_f, __uint_as_float((unsigned)f56));
+    F = __fmaf_rn(F, tau_f, __uint_as_float((unsigned)(f34 >> 32)));
+    F = __fmaf_rn(F, tau_f, __uint_as_float((unsigned)f34));
+    const int i3 = __float2int_rn(F * __uint_as_float((unsigned)(s0c >> 32)));
+    long long acc = (long long)((unsigned long long)(long long)i3 << (unsigned)shp);
+    acc = (long long)B2 + mulhi_su(acc, Tau);
+    acc = (long long)B1 + mulhi_su(acc, Tau);
+    acc = (long long)B0 + mulhi_su(acc, Tau);                     // H 2^-s0, in (0, 2^62)
 
-    // |H| as a double: normalise, round to 53 bits, insert the exponent
+    // H as a double: normalise, round to 53 bits, insert the exponent
     const unsigned long long ha = (unsigned long long)acc;
     const int lh = __clzll(ha);
     const unsigned long long hm = ((ha << lh) + 0x400ull) >> 11;
-    const unsigned long long hbits = hm + ((unsigned long long)(1022 + 63 - lh + q3.x) << 52);
-    // sigma t_u as a double (exact: Tu < 2^47)
-    const int lt = __clzll(Tu | 1ull);
-    const unsigned long long tm = Tu << (lt - 11);
-    const unsigned long long tbits = (Tu == 0) ? 0ull
-        : (tm + ((unsigned long long)(1033 - lt) << 52)) | (top ? 0ull : (1ull << 63));
+    const unsigned long long hbits = hm + ((unsigned long long)(1022 + 63 - lh + (int)(unsigned)s0c) << 52);
+    // t_u as a double (exact: 1 <= Tu <= 2^47)
+    const int lt = __clzll(Tu);
+    const unsigned long long tbits = (Tu << (lt - 11)) + ((unsigned long long)(1033 - lt) << 52);
     const double g = __fma_rn(__longlong_as_double((long long)tbits),
-                              __longlong_as_double((long long)hbits), q0.x);
+                              __longlong_as_double((long long)hbits), __longlong_as_double((long long)a0b));
     return (e < 0) ? 0ull : (unsigned long long)__double_as_longlong(g);
 }
 

@@ -11,32 +11,32 @@ Q'' + Q' = Q Q'^2 (Sec. 2.3, Sec. 6), gives the Taylor coefficients of
     |Phi^{-1}(u)| = G(t) = Q(V - log(1 + t/m_c)),  t = m - m_c,
     V = -E ln2 - ln m_c.
 
-The kernel evaluates G in an unsigned offset t_u >= 0 from an anchor: the
-segment start m_lo (t_u = m - m_lo), or x = 1 on the top segment
-(t_u = 2 - m, G odd in t so z -> 0 with full relative accuracy).  The
-polynomial is the centre expansion re-expanded about the anchor (the same
-polynomial, so the same truncation error):
+The kernel evaluates G in the unsigned offset t_u = m_end - m > 0 from the
+segment's end m_end (x = 1 on the top segment, where G is odd in t and
+z -> 0 keeps full relative accuracy).  The polynomial is the centre expansion
+re-expanded about the end (the same polynomial, so the same truncation
+error); |z| grows away from the end, so H > 0 on every segment:
 
-    G = a_0 + sigma t_u |H(t_u)|,  |H| = sum_{k=0}^{6} beta_k tau^k,
-    tau = t_u 2^K in [0, 1],  sigma = -1 (+1 on the top segment).
+    G = a_0 + t_u H(t_u),  H = sum_{k=0}^{6} beta_k tau^k,
+    tau = t_u 2^K in (0, 1].
 
 On GB300 the FP64 pipe issues about 1/62 of the FP32 rate, so beta_0..beta_2
 are applied by a fixed-point Horner chain on 64-bit integers with tau as an
 unsigned Q0.64 number (acc_k = B_k + mulhi(acc_{k+1}, tau 2^64), every acc in
 units of 2^s0), beta_3..beta_6 by a single-precision chain F entering as
-acc_3 = rn(F 2^c) << sh; then z = fma(sigma t_u, acc_0 2^s0, a_0) is the only
+acc_3 = rn(F 2^c) << sh; then z = fma(t_u, acc_0 2^s0, a_0) is the only
 double-precision operation.
 
 Binades: e = -1 - E in [0, 64) with K = 6, e in [64, 1072] with K = 5, so
 every double 0 < u < 1 (subnormal u included: x is normalised as an
 integer) falls in a segment.
 
-Entry (64 bytes): a0 (double), B0, B1, B2 (int64), beta_3..beta_6 (float),
-s0, 2^c (float), sh, pad.
+Entry (64 bytes, two 32-byte halves): a0 (double), B0, B1, B2 (int64) |
+beta_3..beta_6 (float), s0, 2^c (float), sh, pad.
 
 The generator checks every segment by emulating the kernel's integer and
 double-precision steps exactly (single-precision steps to within one
-rounding) at the anchor, the far end and interior points, against the
+rounding) at both ends and interior points of the segment, against the
 mpmath quantile, and prints the worst relative error.
 Usage:  python -m paper_0901_0638_gb300.fit.gen_fx_tables
 """
@@ -100,13 +100,11 @@ def taylor(e, j, K):
     b = rode.taylor_exp_background(V, q0, q1, DEG + 2)
     s = [mp.mpf(0)] + [mp.mpf((-1) ** n) / n / mc**n for n in range(1, DEG + 3)]   # -log(1 + t/mc)
     a = rode.compose(b, s, DEG + 2)[:DEG + 1]
-    if top:
-        return [a[k] * (-1) ** k for k in range(DEG + 1)]         # t_u = -t
-    h2 = mp.mpf(2) ** (-K - 1)                                    # t = t_u - 2^-K / 2
+    h2 = mp.mpf(0) if top else mp.mpf(2) ** (-K - 1)              # t = h2 - t_u
     g = [mp.mpf(0)] * (DEG + 1)
     for k in range(DEG + 1):
         for i in range(k + 1):
-            g[i] += a[k] * mp.binomial(k, i) * (-h2) ** (k - i)
+            g[i] += a[k] * mp.binomial(k, i) * h2 ** (k - i) * (-1) ** i
     return g
 
 
@@ -116,9 +114,7 @@ def f32(x):
 
 def quantise(e, j, K, g):
     beta = [g[k + 1] * mp.mpf(2) ** (-K * k) for k in range(DEG)]
-    sigma = 1 if beta[0] > 0 else -1
-    assert sigma == (1 if is_top(e, j, K) else -1), (e, j)
-    beta = [sigma * x for x in beta]
+    assert beta[0] > 0, (e, j)
     hmax = sum(abs(x) for x in beta)                              # tau in [0, 1]
     s0 = int(mp.floor(mp.log(hmax, 2))) + 1 - 62                  # |acc| < 2^62
     B = [int(mp.nint(beta[k] / mp.mpf(2) ** s0)) for k in range(NI)]
@@ -130,10 +126,10 @@ def quantise(e, j, K, g):
         c += sh
         sh = 0
     assert 0 <= sh <= 62 and -120 < c < 120, (e, j, c, sh)
-    return {"a0": float(g[0]), "B": B, "bf": bf, "s0": s0, "c": c, "sh": sh, "sigma": sigma}
+    return {"a0": float(g[0]), "B": B, "bf": bf, "s0": s0, "c": c, "sh": sh}
 
 
-def emulate(q, K, top, Tu):
+def emulate(q, K, Tu):
     """The kernel's arithmetic for the integer offset Tu; returns the double z."""
     Tau = (Tu << (12 + K)) - (Tu >> (52 - K))                     # tau = 1 -> 1 - 2^-64
     assert 0 <= Tau < 2**64
@@ -151,7 +147,7 @@ def emulate(q, K, top, Tu):
     lz = 64 - acc.bit_length()
     mant = ((acc << lz) + 0x400) >> 11                            # rounded 53-bit significand
     hd = float(Fraction(mant) * Fraction(2) ** (63 - lz - 52 + q["s0"]))
-    t = Fraction(Tu) * Fraction(2) ** -52 * q["sigma"]
+    t = Fraction(Tu) * Fraction(2) ** -52
     return float(t * Fraction(hd) + Fraction(q["a0"]))
 
 
@@ -166,20 +162,17 @@ def truth(e, Mx):
 def job(args):
     e, j = args
     K = seg_k(e)
-    top = is_top(e, j, K)
     g = taylor(e, j, K)
     q = quantise(e, j, K, g)
     full = 2**(52 - K)
-    if top:
-        pts = [1, 2, 3, full // 2, full - 1, full]
-    elif e < E_MAIN:
-        pts = [0, 1, full // 3, full // 2, full - 1]
+    if e < E_MAIN:
+        pts = [1, 2, 3, full // 3, full // 2, full - 1, full]
     else:
-        pts = [0, full // 2, full - 1]
+        pts = [1, full // 2, full]
     worst = 0.0
     for Tu in pts:
-        z = emulate(q, K, top, Tu)
-        Mx = 2**53 - Tu if top else 2**52 + j * full + Tu
+        z = emulate(q, K, Tu)
+        Mx = 2**52 + (j + 1) * full - Tu
         w = truth(e, Mx)
         if w != 0:
             worst = max(worst, float(abs(mp.mpf(z) / w - 1)))
@@ -207,8 +200,8 @@ def main():
         "// Generated by paper_0901_0638_gb300/fit/gen_fx_tables.py -- do not edit.\n",
         "// FP64 normal quantile, exponential coordinate, segment expansions of\n",
         "// G(t) = Q(V - log(1 + t/m_c)) from the recycling ODE Q'' + Q' = Q Q'^2,\n",
-        "// re-expanded about the anchor and stored for fixed-point evaluation:\n",
-        "// G = a0 + sigma t_u |H|, |H| = sum beta_k tau^k, tau = t_u 2^K in [0, 1],\n",
+        "// re-expanded about the segment end and stored for fixed-point evaluation:\n",
+        "// G = a0 + t_u H, H = sum beta_k tau^k > 0, tau = (m_end - m) 2^K in (0, 1],\n",
         "// beta_0..2 as int64 B_k = beta_k 2^-s0, beta_3..6 as float.\n",
         f"// Binade e = -1 - E: K = {K_MAIN} for e < {E_MAIN}, K = {K_DEEP} for e = {E_MAIN}..{E_LAST}.\n",
         f"// Index e 2^{K_MAIN} + j (e < {E_MAIN}), {N_MAIN} + (e - {E_MAIN}) 2^{K_DEEP} + j.\n",
