@@ -4,7 +4,8 @@
 Workload (one step): the FP64 normal quantile z = Phi^{-1}(u) over n = 2^28
 doubles resident in HBM -- the seed-2 tail-stress mixture (90 % k 2^-53
 uniforms, 10 % 2^-e m with e up to 990, mirrored with probability 1/2) --
-through the library's default FP64 path (qm_normal_quantile_f64).  Inputs and
+through the library's default FP64 path (qm_normal_quantile_f64, the
+fixed-point segment kernel k_f64_fixed).  Inputs and
 outputs (2 GiB each) are far larger than L2, so no flush is needed.
 
 Prints ONE JSON line (rank 0).  Under torchrun each rank processes its own
@@ -30,6 +31,13 @@ if ROOT not in sys.path:
 
 METRIC = "Φ^{-1} Gsamples/s FP32/FP64 & % roofline; batched p50/p99 latency vs plain"
 NOMINAL_FP64_TFLOPS = 1.25     # GB300 nominal dense FP64 (profiling recipe table)
+SMS, SCHEDULERS, LANES, MAX_SM_GHZ = 152, 4, 32, 2.07
+ISSUE_PEAK_TINSTR = SMS * SCHEDULERS * LANES * MAX_SM_GHZ / 1e3   # thread-instructions/ns -> T/s
+# k_f64_fixed: thread-instructions issued per element and DRAM bytes per
+# element, from the ncu capture of the 2^24-element case of this workload
+# (profiles/k_f64_fixed_fp64_mixture.md); re-measured whenever the kernel changes
+FIXED_INSTR_PER_ELEM = 169.3
+FIXED_DRAM_BYTES_PER_ELEM = (136.409e6 + 88.087e6) / 2**24   # writes still in L2 at exit not counted
 
 
 def parse():
@@ -300,15 +308,15 @@ def main():
 
     qm.load()
     n = 1 << args.n_log2
-    variants = {"default": qm.QM_VAR_DEFAULT, "table": qm.QM_VAR_TABLE, "compact": qm.QM_VAR_COMPACT,
+    variants = {"default": qm.QM_VAR_DEFAULT, "fixed": qm.QM_VAR_FIXED, "table": qm.QM_VAR_TABLE,
+                "compact": qm.QM_VAR_COMPACT,
                 "branchfree": qm.QM_VAR_BRANCHFREE, "hybrid_vote": qm.QM_VAR_HYBRID_VOTE,
                 "mixed_halley": qm.QM_VAR_MIXED_HALLEY, "cuda_normcdfinv": qm.QM_VAR_CUDA_LIBM}
     var = variants[args.variant]
     u = W.mixture_f64(2, n, first=shard_first(rank, n), device=dev)
     z = torch.empty_like(u)
     stream = torch.cuda.current_stream(dev)
-    # algorithmic FP64 work: table path for every normal d (5 FP64 FMAs,
-    # 10 flops), the subnormal-d rational below (~50 FP64 ops, 100 flops)
+    # input classes of the mixture (context for the line)
     d = torch.minimum(u, 1.0 - u)
     n_deep = int(((d > 0) & (d < 2.0 ** -65)).sum())
     n_sub = int(((d > 0) & (d < 2.0 ** -1022)).sum())
@@ -338,20 +346,35 @@ def main():
     ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, pg, dev)
     value = world * n / (ms * 1e-3) / 1e9
 
-    # roofline of the dominant kernel (k_f64_table): FP64-issue bound.
-    flops = (n - n_sub - n_edge) * 10 + n_sub * 100
-    achieved = flops / (ms * 1e-3) / 1e12
-    # DRAM traffic of k_f64_table from one ncu capture of the 2^24 case
-    # (profiles/k_f64_table_fp64_mixture_2p28.md: 136.5 MB read + 87.9 MB
-    # written), scaled by the elements processed to one 2^n launch
-    traffic = (136.549e6 + 87.884e6) * (n / (1 << 24)) if args.variant == "default" else None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": traffic,
-                "traffic_note": "bytes per launch, scaled x(n/2^24) from a 2^24 capture; writes still in "
-                                "L2 at kernel exit are not counted (algorithmic: 16 B/element)",
-                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe table); measured DFMA issue 1.20 TFLOP/s",
-                "hbm_view": {"achieved_gbs": 16 * n / (ms * 1e-3) / 1e9, "peak_gbs": 6780.7,
-                             "frac": 16 * n / (ms * 1e-3) / 1e9 / 6780.7}}
+    # roofline of the dominant kernel.  k_f64_fixed (the default) runs the
+    # segment polynomial on the integer pipes with one FP64 FMA per element:
+    # it is bound by instruction issue, so its work unit is the issued
+    # thread-instruction (ncu count per element) against the issue peak of
+    # 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz; the HBM and FP64 views
+    # are reported beside it.
+    secs = ms * 1e-3
+    hbm_view = {"achieved_gbs": 16 * n / secs / 1e9, "peak_gbs": 6780.7,
+                "frac": 16 * n / secs / 1e9 / 6780.7, "bytes_per_element": 16}
+    if args.variant in ("default", "fixed"):
+        achieved = FIXED_INSTR_PER_ELEM * n / secs / 1e12
+        traffic = FIXED_DRAM_BYTES_PER_ELEM * n if FIXED_DRAM_BYTES_PER_ELEM else None
+        roofline = {"bound": "alu", "kernel": "k_f64_fixed", "achieved": achieved,
+                    "peak": ISSUE_PEAK_TINSTR, "unit": "Tinstr/s", "frac": achieved / ISSUE_PEAK_TINSTR,
+                    "traffic": traffic,
+                    "traffic_note": "DRAM bytes per launch, per-element figure of the 2^24 capture x n "
+                                    "(algorithmic: 16 B/element; writes still in L2 at exit not counted)",
+                    "work_per_element": f"{FIXED_INSTR_PER_ELEM} issued thread-instructions (ncu)",
+                    "peak_source": "issue slots: 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz",
+                    "hbm_view": hbm_view,
+                    "fp64_view": {"dfma_per_element": 1, "achieved_tflops": 2 * n / secs / 1e12,
+                                  "peak_tflops": NOMINAL_FP64_TFLOPS}}
+    else:
+        flops = (n - n_sub - n_edge) * 10 + n_sub * 100
+        achieved = flops / secs / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": None,
+                    "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe table); measured DFMA issue "
+                                   "1.20 TFLOP/s", "hbm_view": hbm_view}
 
     extras = {}
     cpu = None
@@ -361,7 +384,7 @@ def main():
         ev_a = torch.cuda.Event(enable_timing=True)
         ev_b = torch.cuda.Event(enable_timing=True)
         for name, v in variants.items():
-            if name == args.variant:
+            if name == args.variant or (name == "fixed" and args.variant == "default"):
                 continue
             qm.qm_normal_quantile_f64(u, z, v, stream=stream)
             torch.cuda.synchronize(dev)
@@ -443,8 +466,8 @@ def main():
                            "n_per_gpu": n, "variant": args.variant, "l2": "inputs larger than L2 (4 GiB)",
                            "deep_tail_elements": n_deep, "subnormal_d_elements": n_sub,
                            "edge_elements": n_edge,
-                           "algorithmic_fp64_flops_per_element": "10 (5 FMA) per normal d, "
-                                                                 "~100 per subnormal d, 0 at u in {0,1}"},
+                           "dominant_kernel": "k_f64_fixed" if args.variant in ("default", "fixed")
+                                              else args.variant},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": args.steps, "clocks": clocks, "variants": extras}
         print(json.dumps(line), flush=True)

@@ -109,16 +109,16 @@ __device__ __forceinline__ unsigned long long probit_mag_fx(unsigned long long u
 __device__ __forceinline__ double probit_fx(double u)
 {
     const unsigned long long ub = (unsigned long long)__double_as_longlong(u);
-    unsigned long long mb = probit_mag_fx(ub);
-    const bool valid = (long long)ub > 0 && ub < 0x3FF0000000000000ull;     // 0 < u < 1
-    if (!valid) {
-        mb = (ub & 0x7fffffffffffffffull) == 0 ? 0xfff0000000000000ull      // +-0 -> -inf
-           : (ub == 0x3FF0000000000000ull ? 0x7ff0000000000000ull           // 1 -> +inf
-                                          : 0x7ff8000000000000ull);         // NaN
-    } else if (ub < 0x3FE0000000000000ull) {
-        mb |= 1ull << 63;                                                    // u < 1/2
-    }
-    return __longlong_as_double((long long)mb);
+    const unsigned hi = (unsigned)(ub >> 32);
+    const unsigned long long mb = probit_mag_fx(ub);
+    const bool valid = hi < 0x3FF00000u && ub != 0ull;                    // 0 < u < 1
+    const unsigned sgn = hi < 0x3FE00000u ? 0x80000000u : 0u;              // u < 1/2
+    const unsigned sp = ((ub << 1) == 0ull) ? 0xfff00000u                  // +-0 -> -inf
+                      : (ub == 0x3FF0000000000000ull ? 0x7ff00000u         // 1 -> +inf
+                                                     : 0x7ff80000u);       // NaN
+    const unsigned rhi = valid ? ((unsigned)(mb >> 32) | sgn) : sp;
+    const unsigned rlo = valid ? (unsigned)mb : 0u;
+    return __hiloint2double((int)rhi, (int)rlo);
 }
 
 template <int U>
@@ -151,14 +151,14 @@ k_f64_fixed_scalar(const double* in, double* out, size_t n)
 }
 
 template <class Kern>
-int grid_of(Kern k, size_t items)
+int grid_of(Kern k, size_t items, int waves = 1)
 {
     int bps = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, kBlock, 0) != cudaSuccess || bps < 1)
         bps = 1;
     const int sms = sm_count() > 0 ? sm_count() : 1;
     size_t g = (items + kBlock - 1) / kBlock;
-    const size_t cap = (size_t)sms * bps;
+    const size_t cap = (size_t)sms * bps * waves;
     if (g > cap) g = cap;
     if (g < 1) g = 1;
     return (int)g;
@@ -171,10 +171,13 @@ qm_status launch_f64_fixed(const double* u, double* z, size_t n, void* stream)
 {
     cudaStream_t s = (cudaStream_t)stream;
     if ((uintptr_t)u % 16 == 0 && (uintptr_t)z % 16 == 0) {
-        const int g = grid_of(k_f64_fixed<2>, (n / 2 + 1) / 2);
-        k_f64_fixed<2><<<g, kBlock, 0, s>>>(u, z, n);
+        // one double2 per thread per pass over a grid of up to 16 x the
+        // resident blocks (measured faster than a persistent grid: the
+        // kernel is issue bound and late blocks fill the tail)
+        const int g = grid_of(k_f64_fixed<1>, n / 2, 16);
+        k_f64_fixed<1><<<g, kBlock, 0, s>>>(u, z, n);
     } else {
-        const int g = grid_of(k_f64_fixed_scalar, n);
+        const int g = grid_of(k_f64_fixed_scalar, n, 16);
         k_f64_fixed_scalar<<<g, kBlock, 0, s>>>(u, z, n);
     }
     return check_launch("f64 fixed");
