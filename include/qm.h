@@ -156,12 +156,38 @@ qm_status qm_sample_moments_noalloc(uint64_t key, uint64_t ctr0, size_t n,
 
 /* ---- recycling maps Q = F^{-1}(G(x)) (Sec. 2.1) -----------------------------
  * Supported (src, dst): (NORMAL, STUDENT_T): out = F_nu^{-1}(Phi(in))
- * (Sec. 3; nu in {1,2,3,4,5,8,10,30}, p->nu required);
+ * (Sec. 3; p->nu required: nu in {1,2,3,4,5,8,10,30} from tables fitted
+ * offline, any other real nu in [QM_T_NU_MIN, QM_T_NU_MAX] from tables built
+ * on the host at the first call with that nu on a device -- the recurrence of
+ * Sec. 3.2 integrated from the tail coordinate of Sec. 3.3, see
+ * qm_t_table_build -- then uploaded (a synchronous cudaMalloc + copy of
+ * ~18 KB, kept until exit; at most 256 distinct nu per process, then
+ * QM_ERR_NOMEM); nu outside both: QM_ERR_UNSUPPORTED);
  * (EXPONENTIAL, NORMAL): out = Phi^{-1}(1 - e^{-in}) (Sec. 2.3, Sec. 6);
  * (UNIFORM, NORMAL): out = Phi^{-1}(in) (FP64 default variant).
  * Anything else: QM_ERR_UNSUPPORTED.  in, out: double[n] (device).        */
 qm_status qm_recycle(int src, int dst, const qm_params* p, const double* in,
                      double* out, size_t n, void* stream);
+
+/* ---- normal -> Student t tables for any real nu (host only, no GPU) ---------
+ * The tables qm_recycle builds for an untabulated nu, returned in host memory
+ * for inspection and testing.  Q_nu(z) = F_nu^{-1}(Phi(z)) on 0 <= z < 8.75 is
+ * cut into QM_T_NSEG segments of width 1/32; seg_coef[10 j + k] is the
+ * coefficient of s^k of the expansion of Q_nu about z_j = (j + 1/2)/32
+ * (z_0 = 0, the central series of Sec. 3.2), s = z - z_j.  The expansions come
+ * from the Gaussian-background recycling ODE (Sec. 3.1), integrated in long
+ * double backwards from the tail (the stable direction) and checked against
+ * the central series.  tail[0] = nu, tail[1] = log kappa, kappa =
+ * nu B(nu/2, 1/2), tail[2] = degree D = QM_T_TAIL_TERMS - 1, tail[3 + k] = R_k:
+ * for z >= 8.75, Q = sqrt(nu) w^{-1/nu} R(w^{2/nu}), w = kappa (1 - Phi(z))
+ * (Sec. 3.3), R from series reversion of the exact Student tail.
+ * seg_coef: 10 QM_T_NSEG doubles; tail: 3 + QM_T_TAIL_TERMS doubles (host).
+ * nu outside [QM_T_NU_MIN, QM_T_NU_MAX]: QM_ERR_UNSUPPORTED.                 */
+#define QM_T_NSEG 280
+#define QM_T_TAIL_TERMS 30
+#define QM_T_NU_MIN 0.75
+#define QM_T_NU_MAX 100.0
+qm_status qm_t_table_build(double nu, double* seg_coef, double* tail);
 
 /* ---- ragged batches ---------------------------------------------------------
  * A batch is a table of independent recycling jobs evaluated by ONE

@@ -85,6 +85,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "qm_philox_fill_u32": [u64, u64, vp, sz, vp],
         "qm_sample_fused": [i, vp, u64, u64, vp, i, sz, vp, vp],
         "qm_recycle": [i, i, vp, vp, vp, sz, vp],
+        "qm_t_table_build": [d, vp, vp],
         "qm_sample_moments_noalloc": [u64, u64, sz, vp, vp],
         "qm_batch_create": [vp, i, vp, vp],
         "qm_batch_run": [vp, vp],
@@ -202,6 +203,20 @@ def qm_recycle(src: int, dst: int, inp, out, nu=None, n=None, stream=None):
     _check(load().qm_recycle(src, dst, _params(nu), _ptr(inp), _ptr(out), _numel(inp, n),
                              _stream(stream, inp)))
     return out
+
+
+QM_T_NSEG, QM_T_TAIL_TERMS, QM_T_NU_MIN, QM_T_NU_MAX = 280, 30, 0.75, 100.0
+
+
+def qm_t_table_build(nu: float):
+    """Host-built normal -> Student t tables for nu (no GPU): (seg, tail) with
+    seg[j, k] the coefficient of s^k about the centre of segment j and tail =
+    (nu, log kappa, degree, R_0..R_degree)."""
+    import numpy as np
+    seg = np.zeros((QM_T_NSEG, 10), dtype=np.float64)
+    tail = np.zeros(3 + QM_T_TAIL_TERMS, dtype=np.float64)
+    _check(load().qm_t_table_build(float(nu), seg.ctypes.data, tail.ctypes.data))
+    return seg, tail
 
 
 class Batch:

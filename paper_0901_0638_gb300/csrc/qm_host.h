@@ -16,4 +16,13 @@ bool bad_overlap(const void* a, size_t abytes, const void* b, size_t bbytes);
 // device arrays of n doubles, in place allowed; stream is a cudaStream_t.
 qm_status launch_f64_fixed(const double* u, double* z, size_t n, void* stream);
 
+// Normal -> Student t tables for nu in [QM_T_NU_MIN, QM_T_NU_MAX] (qm_tdyn.cu):
+// host build (seg: NSEG x 10 coefficients, tail: nu, log kappa, degree, R_k)
+// and the current device's copy, built and uploaded at first use.
+qm_status t_table_build(double nu, double* seg, double* tail);
+qm_status t_table_device(double nu, const void** seg_dev, const double** tail_dev);
+// Index of nu in the tabulated set (or -1) and, for other nu in range, the
+// run-time tables: fills k, seg, tail of a TSel-shaped record (qm_device.cuh).
+qm_status t_select(double nu, int* k, const void** seg_dev, const double** tail_dev);
+
 }  // namespace qm

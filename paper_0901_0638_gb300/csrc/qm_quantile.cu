@@ -109,6 +109,12 @@ struct TMap {
     __device__ double operator()(double z) const { return recycle_t(k, z); }
 };
 
+struct TDynMap {
+    const ttbl::SegT* seg;
+    const double* tail;
+    __device__ double operator()(double z) const { return recycle_t_dyn(seg, tail, z); }
+};
+
 // index of nu in the tabulated set, or -1
 static int t_index(double nu)
 {
@@ -599,7 +605,7 @@ __device__ __forceinline__ double normal_from_d_vote(double d, bool upper, bool 
 
 template <int KIND, bool OUT, bool MOM>
 __global__ void __launch_bounds__(256)
-k_fused_f64(PhiloxKeys K, uint64_t blk0, size_t n, double* out, double* partials, int tk)
+k_fused_f64(PhiloxKeys K, uint64_t blk0, size_t n, double* out, double* partials, TSel tk)
 {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     const size_t nblk = (n + 1) / 2;
@@ -620,7 +626,7 @@ k_fused_f64(PhiloxKeys K, uint64_t blk0, size_t n, double* out, double* partials
             } else if (KIND == 1) {
                 // Student t by recycling the normal sample (Sec. 3 map)
                 const double zn = probit_mag_f64_tbl(d);
-                z[h] = recycle_t(tk, upper ? zn : -zn);
+                z[h] = recycle_t_sel(tk, upper ? zn : -zn);
             } else {
                 // Exp(1) sample x = -log(u) recycled by the Sec. 6 map:
                 // Q(x) = Phi^{-1}(1 - u), evaluated from the exact u (no log)
@@ -810,12 +816,18 @@ extern "C" qm_status qm_sample_fused(int target, const qm_params* p, uint64_t ke
         out_is_f64) {
         if (target == QM_DIST_STUDENT_T) {
             if (!p || !(p->nu > 0.0)) return fail(QM_ERR_INVALID, "qm_sample_fused: Student t needs nu > 0");
-            if (t_index(p->nu) < 0)
-                return fail(QM_ERR_UNSUPPORTED, "qm_sample_fused: nu = %g not tabulated", p->nu);
         }
         const size_t nblk = (n + 1) / 2;
         const int g = grid_for(k_fused_f64<0, true, true>, B, nblk);
-        int tk = 0;
+        TSel tk{0, 0, nullptr, nullptr};
+        if (target == QM_DIST_STUDENT_T) {
+            const void* tseg = nullptr;
+            const double* ttail = nullptr;
+            const qm_status st = t_select(p->nu, &tk.k, &tseg, &ttail);
+            if (st != QM_OK) return st;
+            tk.seg = (const ttbl::SegT*)tseg;
+            tk.tail = ttail;
+        }
         double* part = nullptr;
         if (moments4) {
             part = partials_scratch(g);
@@ -824,7 +836,6 @@ extern "C" qm_status qm_sample_fused(int target, const qm_params* p, uint64_t ke
         double* o = (double*)out;
         const uint64_t b0 = ctr0 / 4;
         const PhiloxKeys key = philox_keys(key_in);
-        if (target == QM_DIST_STUDENT_T) tk = t_index(p->nu);
 #define QM_LAUNCH_F64(KIND)                                                                  \
     if (o && part) k_fused_f64<KIND, true, true><<<g, B, 0, s>>>(key, b0, n, o, part, tk);   \
     else if (o) k_fused_f64<KIND, true, false><<<g, B, 0, s>>>(key, b0, n, o, nullptr, tk);  \
@@ -858,13 +869,21 @@ extern "C" qm_status qm_recycle(int src, int dst, const qm_params* p, const doub
         if (!p) return fail(QM_ERR_INVALID, "qm_recycle: Student t needs params (nu)");
         if (!(p->nu > 0.0)) return fail(QM_ERR_INVALID, "qm_recycle: nu must be > 0 (got %g)", p->nu);
         const int k = t_index(p->nu);
-        if (k < 0)
-            return fail(QM_ERR_UNSUPPORTED, "qm_recycle: nu = %g not tabulated (1,2,3,4,5,8,10,30)", p->nu);
+        if (k < 0 && !(p->nu >= QM_T_NU_MIN && p->nu <= QM_T_NU_MAX))
+            return fail(QM_ERR_UNSUPPORTED, "qm_recycle: nu = %g outside [%g, %g] and not tabulated",
+                        p->nu, QM_T_NU_MIN, QM_T_NU_MAX);
         if (n == 0) return QM_OK;
         if (!in || !out) return fail(QM_ERR_INVALID, "qm_recycle: null pointer");
         if (bad_overlap(in, n * 8, out, n * 8))
             return fail(QM_ERR_INVALID, "qm_recycle: partially overlapping in/out");
-        return launch_map(in, out, n, TMap{k}, (cudaStream_t)stream, "recycle normal->t");
+        if (k >= 0) return launch_map(in, out, n, TMap{k}, (cudaStream_t)stream, "recycle normal->t");
+        const void* seg = nullptr;
+        const double* tail = nullptr;
+        int kk = -1;
+        const qm_status st = t_select(p->nu, &kk, &seg, &tail);
+        if (st != QM_OK) return st;
+        return launch_map(in, out, n, TDynMap{(const ttbl::SegT*)seg, tail}, (cudaStream_t)stream,
+                          "recycle normal->t (run-time table)");
     }
     return fail(QM_ERR_UNSUPPORTED, "qm_recycle: pair (%d -> %d) not supported", src, dst);
 }

@@ -34,8 +34,8 @@ struct DevSeg {
     unsigned long long n;
     unsigned long long tile0;
     int kind;
-    int tk;
-    int pad[2];
+    int pad;
+    TSel t;
 };
 
 template <int EPT, bool ESTRIN>
@@ -60,7 +60,7 @@ k_batch(const DevSeg* __restrict__ segs, int nseg, unsigned long long ntiles)
         for (int k = 0; k < EPT; ++k) {
             const size_t i = base + (size_t)k * blockDim.x + threadIdx.x;
             double y;
-            if (sg.kind == KIND_T) y = recycle_t<ESTRIN>(sg.tk, x[k]);
+            if (sg.kind == KIND_T) y = recycle_t_sel<ESTRIN>(sg.t, x[k]);
             else if (sg.kind == KIND_EXP) y = exp_to_normal_tbl(x[k]);
             else y = probit_f64_any(x[k]);
             if (i < sg.n) __stcs(sg.out + i, y);
@@ -70,24 +70,17 @@ k_batch(const DevSeg* __restrict__ segs, int nseg, unsigned long long ntiles)
 
 // One plain launch per segment (the comparison baseline for the batch).
 __global__ void __launch_bounds__(256)
-k_single(const double* __restrict__ in, double* out, size_t n, int kind, int tk)
+k_single(const double* __restrict__ in, double* out, size_t n, int kind, TSel t)
 {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const double x = __ldcs(in + i);
         double y;
-        if (kind == KIND_T) y = recycle_t<false>(tk, x);
+        if (kind == KIND_T) y = recycle_t_sel<false>(t, x);
         else if (kind == KIND_EXP) y = exp_to_normal_tbl(x);
         else y = probit_f64_any(x);
         __stcs(out + i, y);
     }
-}
-
-int t_index_host(double nu)
-{
-    for (int i = 0; i < ttbl::NNU; ++i)
-        if (nu == ttbl::T_NU[i]) return i;
-    return -1;
 }
 
 using BatchKernel = void (*)(const DevSeg*, int, unsigned long long);
@@ -222,8 +215,12 @@ extern "C" qm_status qm_batch_create(const qm_segment* segs, int nseg, const qm_
         DevSeg d{};
         if (s.src == QM_DIST_NORMAL && s.dst == QM_DIST_STUDENT_T) {
             if (!(s.nu > 0.0)) return fail(QM_ERR_INVALID, "qm_batch_create: segment %d: nu must be > 0", i);
-            d.tk = t_index_host(s.nu);
-            if (d.tk < 0) return fail(QM_ERR_UNSUPPORTED, "qm_batch_create: segment %d: nu = %g not tabulated", i, s.nu);
+            const void* tseg = nullptr;
+            const double* ttail = nullptr;
+            const qm_status st = t_select(s.nu, &d.t.k, &tseg, &ttail);
+            if (st != QM_OK) return st;
+            d.t.seg = (const ttbl::SegT*)tseg;
+            d.t.tail = ttail;
             d.kind = KIND_T;
         } else if (s.src == QM_DIST_EXPONENTIAL && s.dst == QM_DIST_NORMAL) {
             d.kind = KIND_EXP;
@@ -326,7 +323,7 @@ extern "C" qm_status qm_batch_run_separate(qm_batch* b, void* stream)
     for (const DevSeg& s : b->host) {
         if (!s.n) continue;
         int g = (int)std::min<size_t>((s.n + 255) / 256, (size_t)sms * 8);
-        k_single<<<g, 256, 0, (cudaStream_t)stream>>>(s.in, s.out, s.n, s.kind, s.tk);
+        k_single<<<g, 256, 0, (cudaStream_t)stream>>>(s.in, s.out, s.n, s.kind, s.t);
     }
     return check_launch("qm_batch_run_separate");
 }

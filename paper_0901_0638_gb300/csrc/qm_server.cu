@@ -33,16 +33,14 @@
 
 namespace qm {
 
-int t_index_host(double nu);
-
 struct ReqDev {
     void* out;
     unsigned long long n;
     unsigned long long key;
     unsigned long long tile0;
     int kind;
-    int tk;
-    int pad[2];
+    int pad;
+    TSel t;
 };
 
 constexpr int kServeBlock = 256;
@@ -65,7 +63,7 @@ __device__ __forceinline__ void serve_f32(const ReqDev& r, unsigned long long pb
     }
 }
 
-__device__ __forceinline__ double serve_f64_one(int kind, int tk, uint32_t hi, uint32_t lo)
+__device__ __forceinline__ double serve_f64_one(int kind, const TSel& t, uint32_t hi, uint32_t lo)
 {
     const uint64_t k = ((uint64_t)(hi >> 11) << 32) | lo;
     const bool upper = k >= (1ull << 52);
@@ -80,7 +78,7 @@ __device__ __forceinline__ double serve_f64_one(int kind, int tk, uint32_t hi, u
         return upper ? -m : m;
     }
     const double z = upper ? m : -m;
-    return (kind == 2) ? recycle_t(tk, z) : z;
+    return (kind == 2) ? recycle_t_sel(t, z) : z;
 }
 
 __global__ void __launch_bounds__(kServeBlock)
@@ -105,8 +103,8 @@ k_serve(const ReqDev* __restrict__ reqs, int nreq, unsigned long long ntiles)
             } else {
                 const uint4 w = philox_block(r.key, pb);
                 double* o = static_cast<double*>(r.out);
-                const double z0 = serve_f64_one(r.kind, r.tk, w.x, w.y);
-                const double z1 = serve_f64_one(r.kind, r.tk, w.z, w.w);
+                const double z0 = serve_f64_one(r.kind, r.t, w.x, w.y);
+                const double z1 = serve_f64_one(r.kind, r.t, w.z, w.w);
                 const unsigned long long i0 = pb * 2;
                 if (i0 + 2 <= r.n && ((uintptr_t)(o + i0) % 16 == 0)) {
                     __stcs(reinterpret_cast<double2*>(o + i0), make_double2(z0, z1));
@@ -312,7 +310,14 @@ static void worker_loop(qm_server* s)
                 d.n = c.n;
                 d.key = c.key;
                 d.kind = c.kind;
-                d.tk = (c.kind == QM_REQ_STUDENT_T) ? t_index_host(c.nu) : 0;
+                d.t.k = 0;
+                if (c.kind == QM_REQ_STUDENT_T) {
+                    const void* tseg = nullptr;
+                    const double* ttail = nullptr;
+                    t_select(c.nu, &d.t.k, &tseg, &ttail);   // validated (and built) at submit
+                    d.t.seg = (const ttbl::SegT*)tseg;
+                    d.t.tail = ttail;
+                }
                 d.tile0 = t0;
                 t0 += req_tiles(d);
                 table.push_back(d);
@@ -389,8 +394,13 @@ extern "C" qm_status qm_server_submit(qm_server* s, const qm_request* r)
     if (!s || !r) return fail(QM_ERR_INVALID, "qm_server_submit: null argument");
     if (r->kind < QM_REQ_NORMAL_F32 || r->kind > QM_REQ_EXP_NORMAL)
         return fail(QM_ERR_INVALID, "qm_server_submit: bad kind %d", r->kind);
-    if (r->kind == QM_REQ_STUDENT_T && t_index_host(r->nu) < 0)
-        return fail(QM_ERR_UNSUPPORTED, "qm_server_submit: nu = %g not tabulated", r->nu);
+    if (r->kind == QM_REQ_STUDENT_T) {
+        int k;
+        const void* tseg;
+        const double* ttail;
+        const qm_status st = t_select(r->nu, &k, &tseg, &ttail);   // builds untabulated tables here
+        if (st != QM_OK) return st;
+    }
     const size_t bytes = r->n * (r->kind == QM_REQ_NORMAL_F32 ? 4 : 8);
     if (bytes > s->arena.capacity())
         return fail(QM_ERR_NOMEM, "qm_server_submit: request of %zu bytes exceeds the budget", bytes);

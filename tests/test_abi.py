@@ -50,8 +50,8 @@ def test_batch_validation_before_any_launch(lib):
     # unsupported pair
     arr = (seg * 1)(seg(qm.QM_DIST_UNIFORM, qm.QM_DIST_EXPONENTIAL, 0.0, 4096, 8192, 8))
     assert lib.qm_batch_create(arr, 1, None, ctypes.byref(h)) == qm.QM_ERR_INVALID
-    # nu not tabulated / invalid
-    arr = (seg * 1)(seg(qm.QM_DIST_NORMAL, qm.QM_DIST_STUDENT_T, 7.0, 4096, 8192, 8))
+    # nu outside the supported range / invalid
+    arr = (seg * 1)(seg(qm.QM_DIST_NORMAL, qm.QM_DIST_STUDENT_T, 150.0, 4096, 8192, 8))
     assert lib.qm_batch_create(arr, 1, None, ctypes.byref(h)) == qm.QM_ERR_UNSUPPORTED
     arr = (seg * 1)(seg(qm.QM_DIST_NORMAL, qm.QM_DIST_STUDENT_T, -2.0, 4096, 8192, 8))
     assert lib.qm_batch_create(arr, 1, None, ctypes.byref(h)) == qm.QM_ERR_INVALID

@@ -59,6 +59,29 @@ def test_batch_small_ragged_vs_oracle_and_alone():
     b.close()
 
 
+def test_batch_with_untabulated_nu():
+    """Segments with any real nu (run-time tables) next to tabulated ones."""
+    lens = [3000, 1025, 77, 4096, 513]
+    nus = [2.7, 13.0, 0.8, 4.0, 2.7]
+    segs, ins, outs = [], [], []
+    for j, (n, nu) in enumerate(zip(lens, nus)):
+        x = W.normal_box_muller(11, n, 0, j + 1, DEV)
+        segs.append((qm.QM_DIST_NORMAL, qm.QM_DIST_STUDENT_T, nu, x, torch.full_like(x, float("nan"))))
+    for tuning in ((256, 2, 0), (128, 4, 1)):
+        b = qm.Batch(segs, tuning=tuning)
+        b.run()
+        torch.cuda.synchronize()
+        for (src, dst, nu, x, o) in segs:
+            w = oracle.recycle_t(nu, x.cpu().numpy())
+            assert not f64_violations(o.cpu().numpy(), w, 1e-12).any(), (tuning, nu)
+            if tuning[2] == 0:
+                alone = torch.empty_like(x)
+                qm.qm_recycle(src, dst, x, alone, nu=nu)
+                torch.cuda.synchronize()
+                assert torch.equal(alone, o), nu
+        b.close()
+
+
 def test_batch_tuning_candidates_and_autotuner(tmp_path, monkeypatch):
     monkeypatch.setenv("QM_TUNE_CACHE", str(tmp_path / "tune.txt"))
     rng = np.random.default_rng(8)

@@ -1,7 +1,8 @@
 """GPU parity of the recycling maps against the CPU FP64 oracle.
 
 Normal -> Student t, Q_nu(z) = F_nu^{-1}(Phi(z)) (Sec. 3), for every
-tabulated nu; tolerance 1e-12 relative (exact for 0, infinities and NaN)."""
+tabulated nu and for untabulated real nu (tables built on the host at first
+use); tolerance 1e-12 relative (exact for 0, infinities and NaN)."""
 import math
 
 import numpy as np
@@ -50,17 +51,30 @@ def test_recycle_normal_to_t(nu):
     assert math.copysign(1.0, t[-4]) == -1.0
 
 
+@pytest.mark.parametrize("nu", [0.75, 1.5, 2.5, 6.3, 17.0, 50.0, 100.0])
+def test_recycle_normal_to_t_any_nu(nu):
+    z = z_cases()
+    w = oracle.recycle_t(nu, z)
+    t = run_t(nu, z)
+    r = rel_err(t, w)
+    print(f"nu={nu} (run-time table): max rel {r.max():.3g}")
+    assert not f64_violations(t, w, 1e-12).any()
+    assert np.array_equal(run_t(nu, -z[np.isfinite(z)]), -t[np.isfinite(z)])
+    assert np.array_equal(run_t(nu, z), t, equal_nan=True)   # second call: cached table, same result
+
+
 def test_recycle_t_argument_errors():
     z = torch.zeros(4, dtype=torch.float64, device=DEV)
-    with pytest.raises(qm.QMError) as e:
-        qm.qm_recycle(qm.QM_DIST_NORMAL, qm.QM_DIST_STUDENT_T, z, z, nu=7.0)
-    assert e.value.status == qm.QM_ERR_UNSUPPORTED
+    for nu in (0.5, 150.0):
+        with pytest.raises(qm.QMError) as e:
+            qm.qm_recycle(qm.QM_DIST_NORMAL, qm.QM_DIST_STUDENT_T, z, z, nu=nu)
+        assert e.value.status == qm.QM_ERR_UNSUPPORTED
     with pytest.raises(qm.QMError) as e:
         qm.qm_recycle(qm.QM_DIST_NORMAL, qm.QM_DIST_STUDENT_T, z, z, nu=-1.0)
     assert e.value.status == qm.QM_ERR_INVALID
 
 
-@pytest.mark.parametrize("nu", [1.0, 4.0, 30.0])
+@pytest.mark.parametrize("nu", [1.0, 4.0, 30.0, 6.5])
 def test_fused_student_t(nu):
     n = (1 << 15) + 3
     key, ctr0 = 21, 0

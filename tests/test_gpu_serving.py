@@ -85,6 +85,19 @@ def test_batched_results_equal_alone_and_match_oracle():
     alone_srv.close()
 
 
+def test_student_t_requests_with_untabulated_nu():
+    """Requests with any real nu in range (run-time tables, built at submit)."""
+    srv = qm.Server(mem_budget=1 << 28, max_batch=16, streams=2)
+    trace = [{"id": i, "n": 3000 + 17 * i, "kind": qm.QM_REQ_STUDENT_T, "nu": nu, "key": 700 + i,
+              "t_arrival": 0.0} for i, nu in enumerate([2.7, 0.9, 4.0, 55.0, 2.7])]
+    done = srv.replay(trace)
+    assert len(done) == len(trace) and all(c.status == 0 for c in done)
+    for c in done:
+        check_parity(c, fetch(c))
+        srv.release(c.id)
+    srv.close()
+
+
 def test_memory_admission_bounds_in_flight_bytes():
     budget = 4 << 20
     trace = [{"id": i, "n": 1 << 17, "kind": qm.QM_REQ_NORMAL_F64, "key": 100 + i, "t_arrival": 0.0}
@@ -120,7 +133,7 @@ def test_server_argument_errors():
         srv.submit({"n": 16, "kind": 9, "key": 1})
     assert e.value.status == qm.QM_ERR_INVALID
     with pytest.raises(qm.QMError) as e:
-        srv.submit({"n": 16, "kind": qm.QM_REQ_STUDENT_T, "nu": 7.0, "key": 1})
+        srv.submit({"n": 16, "kind": qm.QM_REQ_STUDENT_T, "nu": 0.5, "key": 1})
     assert e.value.status == qm.QM_ERR_UNSUPPORTED
     with pytest.raises(qm.QMError) as e:
         srv.submit({"n": 1 << 20, "kind": qm.QM_REQ_NORMAL_F64, "key": 1})   # 8 MiB > 1 MiB
