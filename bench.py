@@ -49,7 +49,8 @@ def parse():
     p.add_argument("--n-log2", type=int, default=28, help="elements per rank = 2^n")
     p.add_argument("--variant", default="default")
     p.add_argument("--no-extras", action="store_true", help="skip variant/e2e/cpu legs")
-    p.add_argument("--workload", default="fp64", choices=["fp64", "fp32", "batch", "serve", "fused"],
+    p.add_argument("--workload", default="fp64", choices=["fp64", "fp32", "batch", "serve", "fused",
+                                                          "hyperbolic"],
                    help="fp64: the headline line; fp32/batch/serve: the other hot-path kernels "
                         "(for profiling and context)")
     p.add_argument("--serve-seconds", type=float, default=2.0)
@@ -235,6 +236,27 @@ def side_workload(args):
                     roofline={"bound": "alu", "achieved_gbs_written": gbs, "hbm_frac_of_write": gbs / 6780.7},
                     moments={"ms_per_step": ms_m, "gsamples_s": n / (ms_m * 1e-3) / 1e9,
                              "mean": m[0], "m2": m[1], "m3": m[2], "m4": m[3]})
+    elif args.workload == "hyperbolic":
+        # exponential -> hyperbolic recycling (alpha, beta, delta) = (1.3, 0.4, 0.7)
+        # over 2^n two-sided exponential base samples resident in HBM
+        n = 1 << args.n_log2
+        a, b, d = 1.3, 0.4, 0.7
+        g = torch.Generator(device=dev)
+        g.manual_seed(6)
+        e = torch.empty(n, dtype=torch.float64, device=dev).exponential_(generator=g)
+        side = torch.rand(n, dtype=torch.float64, device=dev, generator=g) < 0.5
+        v = torch.where(side, e / (a - b), -e / (a + b))
+        del e, side
+        x = torch.empty_like(v)
+        h = qm.Hyperbolic(a, b, d)
+        ms = timed(lambda: h.recycle(v, x, stream=stream), stream, args.steps, args.warmup)
+        line.update(value=n / (ms * 1e-3) / 1e9, ms_per_step=ms, dtype="f64",
+                    config={"workload": f"exponential -> hyperbolic recycling (alpha, beta, delta) = "
+                                        f"({a}, {b}, {d}), n=2^{args.n_log2} two-sided exponential samples"},
+                    roofline={"bound": "alu", "note": "FP64 Horner (5 FMA + 1 add per element) on "
+                                                      "segment tables; 16 B/element",
+                              "hbm_frac": 16 * n / (ms * 1e-3) / 1e9 / 6780.7})
+        h.close()
     elif args.workload == "batch":
         lens, targets = W.ragged_segments(4, 256, hi=args.batch_hi)
         spec = []

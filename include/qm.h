@@ -189,6 +189,42 @@ qm_status qm_recycle(int src, int dst, const qm_params* p, const double* in,
 #define QM_T_NU_MAX 100.0
 qm_status qm_t_table_build(double nu, double* seg_coef, double* tail);
 
+/* ---- exponential -> hyperbolic recycling (Sec. 8.1) --------------------------
+ * Target: the hyperbolic density f(x) = exp(-alpha sqrt(delta^2 + x^2) +
+ * beta x) / Z (location 0; Z = 2 alpha delta K_1(delta gamma) / gamma,
+ * gamma = sqrt(alpha^2 - beta^2)).  Base: the two-sided exponential with the
+ * same mass split at 0: density p_+ (alpha-beta) e^{-(alpha-beta) v} for v > 0
+ * and p_- (alpha+beta) e^{(alpha+beta) v} for v < 0, p_+ = P(X > 0).
+ * x = Q(v) = F^{-1}(G_0(v)) maps base samples to hyperbolic samples; Q solves
+ * the paper's right/left recycling ODEs with Q(0) = 0 and
+ * Q'(0+-) = f_0(0+-)/f(0).
+ * qm_hyp_create builds the map for one parameter set on the host (long
+ * double: Taylor series of the ODEs integrated backwards from the tails, on
+ * segments of |v| with 32 per binade 2^E <= |v| < 2^(E+1), E >= QM_HYP_E_MIN,
+ * degree 9 per segment, and the series about 0 below), uploads it (one
+ * cudaMalloc of ~260 KB, owned by the handle) and returns the handle.
+ * Errors: alpha <= 0, |beta| >= alpha, delta <= 0: QM_ERR_INVALID; alpha - |beta|
+ * < 1e-3 alpha or alpha delta outside [1e-4, 1e4]: QM_ERR_UNSUPPORTED.
+ * qm_hyp_recycle: x[i] = Q(v[i]) for device arrays of n doubles (in place
+ * allowed); +-inf -> +-inf, NaN -> NaN; |v| beyond what a double sample of the
+ * base can reach (p e^{-rate |v|} < 2^-1074) is extrapolated from the last
+ * segment.  qm_hyp_info: p_+, p_-, Q'(0+), Q'(0-), log Z (host double[5]).
+ * qm_hyp_table_build (host only, no GPU): the same tables in host memory --
+ * seg_right / seg_left: (1 + 32 QM_HYP_MAX_BINADES) x 10 doubles each; entry 0
+ * the series about 0 (coefficient k of v^k), entry 1 + 32 (E - QM_HYP_E_MIN)
+ * + j the expansion about 2^E (1 + (2j+1)/64) for the right (v > 0) and left
+ * (|v| for v < 0, values -Q(-|v|)) sides; e_max[2] the last binade per side;
+ * info as qm_hyp_info.                                                       */
+#define QM_HYP_E_MIN (-30)
+#define QM_HYP_MAX_BINADES 64
+typedef struct qm_hyp qm_hyp;
+qm_status qm_hyp_create(double alpha, double beta, double delta, qm_hyp** out);
+qm_status qm_hyp_recycle(const qm_hyp* h, const double* v, double* x, size_t n, void* stream);
+qm_status qm_hyp_info(const qm_hyp* h, double* info);
+qm_status qm_hyp_destroy(qm_hyp* h);
+qm_status qm_hyp_table_build(double alpha, double beta, double delta, double* seg_right,
+                             double* seg_left, int* e_max, double* info);
+
 /* ---- ragged batches ---------------------------------------------------------
  * A batch is a table of independent recycling jobs evaluated by ONE
  * persistent launch over a device-resident segment table, replayed as a CUDA

@@ -86,6 +86,11 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "qm_sample_fused": [i, vp, u64, u64, vp, i, sz, vp, vp],
         "qm_recycle": [i, i, vp, vp, vp, sz, vp],
         "qm_t_table_build": [d, vp, vp],
+        "qm_hyp_create": [d, d, d, vp],
+        "qm_hyp_recycle": [vp, vp, vp, sz, vp],
+        "qm_hyp_info": [vp, vp],
+        "qm_hyp_destroy": [vp],
+        "qm_hyp_table_build": [d, d, d, vp, vp, vp, vp],
         "qm_sample_moments_noalloc": [u64, u64, sz, vp, vp],
         "qm_batch_create": [vp, i, vp, vp],
         "qm_batch_run": [vp, vp],
@@ -217,6 +222,57 @@ def qm_t_table_build(nu: float):
     tail = np.zeros(3 + QM_T_TAIL_TERMS, dtype=np.float64)
     _check(load().qm_t_table_build(float(nu), seg.ctypes.data, tail.ctypes.data))
     return seg, tail
+
+
+QM_HYP_E_MIN, QM_HYP_MAX_BINADES = -30, 64
+
+
+def qm_hyp_table_build(alpha: float, beta: float, delta: float):
+    """Host-built exponential -> hyperbolic tables (no GPU): (right, left,
+    e_max, info) -- right/left[i, k] coefficient k of entry i (entry 0 the
+    series about 0, entry 1 + 32 (E - E_MIN) + j the expansion about
+    2^E (1 + (2j+1)/64)), e_max the last binade per side, info = (p_+, p_-,
+    Q'(0+), Q'(0-), log Z)."""
+    import numpy as np
+    per = 1 + 32 * QM_HYP_MAX_BINADES
+    right = np.zeros((per, 10), dtype=np.float64)
+    left = np.zeros((per, 10), dtype=np.float64)
+    e_max = np.zeros(2, dtype=np.int32)
+    info = np.zeros(5, dtype=np.float64)
+    _check(load().qm_hyp_table_build(float(alpha), float(beta), float(delta), right.ctypes.data,
+                                     left.ctypes.data, e_max.ctypes.data, info.ctypes.data))
+    return right, left, e_max, info
+
+
+class Hyperbolic:
+    """Exponential -> hyperbolic recycling map for one parameter set
+    (qm_hyp_*): x = Q(v) for two-sided exponential samples v."""
+
+    def __init__(self, alpha: float, beta: float, delta: float):
+        h = ctypes.c_void_p()
+        _check(load().qm_hyp_create(float(alpha), float(beta), float(delta), ctypes.byref(h)))
+        self._h = h
+
+    def recycle(self, v, x, n=None, stream=None):
+        _check(load().qm_hyp_recycle(self._h, _ptr(v), _ptr(x), _numel(v, n), _stream(stream, v)))
+        return x
+
+    def info(self):
+        out = (ctypes.c_double * 5)()
+        _check(load().qm_hyp_info(self._h, out))
+        return {"p_plus": out[0], "p_minus": out[1], "slope_plus": out[2], "slope_minus": out[3],
+                "log_z": out[4]}
+
+    def close(self):
+        if self._h:
+            load().qm_hyp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:
