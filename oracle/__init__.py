@@ -16,6 +16,9 @@ What each routine computes, and the passage it restates:
 * ``recycle_exp`` -- Q(x) = Phi^{-1}(1 - e^{-x}), exponential -> normal
                      (Sec. 2.3 and Sec. 6).
 * ``philox_stream`` -- Philox4x32-10 words (Salmon et al., SC'11).
+* ``hyperbolic.recycle_hyperbolic`` -- Q(v) = F^{-1}(G_0(v)), two-sided
+                     exponential -> hyperbolic (Sec. 8.1), by quadrature and
+                     Brent's method (``oracle/hyperbolic.py``, numpy/scipy).
 """
 from __future__ import annotations
 
