@@ -225,6 +225,33 @@ qm_status qm_hyp_destroy(qm_hyp* h);
 qm_status qm_hyp_table_build(double alpha, double beta, double delta, double* seg_right,
                              double* seg_left, int* e_max, double* info);
 
+/* ---- Gaussian copula with recycled marginals (Sec. 9) ------------------------
+ * Samples x in R^d with a Gaussian copula of correlation L L^T and the given
+ * marginals, folding "normal -> uniform -> marginal" into the recycling map
+ * of each coordinate (the remark of the paper's conclusion): per sample,
+ * eps_k = Phi^{-1}((m_k + 1/2) 2^-53) from 53-bit Philox integers (two per
+ * Philox block; sample i uses blocks ctr0/4 + i ceil(d/2) + b), y = L eps,
+ * x_j = Q_j(y_j) with Q_j the identity (QM_DIST_NORMAL) or the Sec. 3 map to
+ * Student t with nu_j (QM_DIST_STUDENT_T; tabulated or run-time tables as in
+ * qm_recycle).
+ * qm_copula_create: chol = host d x d row-major lower-triangular Cholesky
+ * factor with positive diagonal (1 <= d <= QM_COPULA_MAX_DIM), margins = host
+ * array of d; copies both to the device (one cudaMalloc, owned by the
+ * handle).  Errors: bad d, non-finite or non-lower-triangular L, L[j][j] <= 0:
+ * QM_ERR_INVALID; other margin kinds or out-of-range nu: QM_ERR_UNSUPPORTED.
+ * qm_copula_sample: out = device double[d n], column-major (x_j of sample i
+ * at out[j n + i]); ctr0 a multiple of 4.                                    */
+#define QM_COPULA_MAX_DIM 16
+typedef struct {
+    int kind;            /* QM_DIST_NORMAL or QM_DIST_STUDENT_T */
+    double nu;           /* Student-t degrees of freedom */
+} qm_margin;
+typedef struct qm_copula qm_copula;
+qm_status qm_copula_create(int d, const double* chol, const qm_margin* margins, qm_copula** out);
+qm_status qm_copula_sample(const qm_copula* c, uint64_t key, uint64_t ctr0, double* out, size_t n,
+                           void* stream);
+qm_status qm_copula_destroy(qm_copula* c);
+
 /* ---- ragged batches ---------------------------------------------------------
  * A batch is a table of independent recycling jobs evaluated by ONE
  * persistent launch over a device-resident segment table, replayed as a CUDA

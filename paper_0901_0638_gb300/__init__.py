@@ -91,6 +91,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "qm_hyp_info": [vp, vp],
         "qm_hyp_destroy": [vp],
         "qm_hyp_table_build": [d, d, d, vp, vp, vp, vp],
+        "qm_copula_create": [i, vp, vp, vp],
+        "qm_copula_sample": [vp, u64, u64, vp, sz, vp],
+        "qm_copula_destroy": [vp],
         "qm_sample_moments_noalloc": [u64, u64, sz, vp, vp],
         "qm_batch_create": [vp, i, vp, vp],
         "qm_batch_run": [vp, vp],
@@ -266,6 +269,43 @@ class Hyperbolic:
     def close(self):
         if self._h:
             load().qm_hyp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+QM_COPULA_MAX_DIM = 16
+
+
+class qm_margin(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("nu", ctypes.c_double)]
+
+
+class Copula:
+    """Gaussian copula with recycled marginals (qm_copula_*): chol is a d x d
+    lower-triangular Cholesky factor (host array), margins a list of
+    (kind, nu) with kind QM_DIST_NORMAL or QM_DIST_STUDENT_T."""
+
+    def __init__(self, chol, margins):
+        import numpy as np
+        L = np.ascontiguousarray(np.asarray(chol, dtype=np.float64))
+        d = L.shape[0]
+        arr = (qm_margin * d)(*[qm_margin(int(k), float(nu or 0.0)) for k, nu in margins])
+        h = ctypes.c_void_p()
+        _check(load().qm_copula_create(d, L.ctypes.data, arr, ctypes.byref(h)))
+        self._h, self.d = h, d
+
+    def sample(self, key: int, ctr0: int, out, n: int, stream=None):
+        _check(load().qm_copula_sample(self._h, key, ctr0, _ptr(out), n, _stream(stream, out)))
+        return out
+
+    def close(self):
+        if self._h:
+            load().qm_copula_destroy(self._h)
             self._h = None
 
     def __del__(self):

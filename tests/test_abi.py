@@ -66,3 +66,16 @@ def test_batch_validation_before_any_launch(lib):
     arr = (seg * 1)(seg(qm.QM_DIST_EXPONENTIAL, qm.QM_DIST_NORMAL, 0.0, 4096, 8192, 8))
     assert lib.qm_batch_create(arr, 1, ctypes.byref(qm.qm_tuning(300, 2, 0)), ctypes.byref(h)) == qm.QM_ERR_INVALID
     assert lib.qm_batch_create(arr, 0, None, ctypes.byref(h)) == qm.QM_ERR_INVALID
+
+
+def test_copula_validation_before_any_device_call(lib):
+    import numpy as np
+    L = np.ascontiguousarray(np.triu(np.ones((3, 3))))
+    m = (qm.qm_margin * 3)(*[qm.qm_margin(qm.QM_DIST_NORMAL, 0.0)] * 3)
+    h = ctypes.c_void_p()
+    assert lib.qm_copula_create(3, L.ctypes.data, m, ctypes.byref(h)) == qm.QM_ERR_INVALID
+    assert lib.qm_copula_create(17, L.ctypes.data, m, ctypes.byref(h)) == qm.QM_ERR_INVALID
+    L = np.ascontiguousarray(np.eye(3))
+    L[1, 1] = 0.0
+    assert lib.qm_copula_create(3, L.ctypes.data, m, ctypes.byref(h)) == qm.QM_ERR_INVALID
+    assert lib.qm_copula_sample(None, 1, 0, None, 8, None) == qm.QM_ERR_INVALID
