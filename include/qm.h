@@ -9,13 +9,17 @@
  *     v = |u - 1/2| / sqrt(u - u^2) (Sec. 7.3), each followed by one rational
  *     approximation;
  *   - the recycling maps Q(x) = F^{-1}(G(x)) of Sec. 2.1: normal -> Student t
- *     (Sec. 3) and exponential -> normal (Sec. 2.3, Sec. 6);
- *   - fused counter-based generation (Philox4x32-10) + transform.
+ *     (Sec. 3), exponential -> normal (Sec. 2.3, Sec. 6) and two-sided
+ *     exponential -> hyperbolic (Sec. 8.1);
+ *   - fused counter-based generation (Philox4x32-10) + transform, and the
+ *     Gaussian copula with recycled marginals (Sec. 9).
  *
  * Conventions (all entry points):
  *   - Data pointers are DEVICE pointers owned by the caller unless stated.
- *     The library owns only workspaces it allocates in *_create calls (and a
- *     small per-device scratch for reductions, allocated on first use).
+ *     The library owns only workspaces it allocates in *_create calls, a
+ *     small per-device scratch for reductions, and the run-time Student-t
+ *     tables of untabulated nu (both allocated on first use, kept until the
+ *     process exits).
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Calls are asynchronous on it; argument errors are returned
  *     synchronously before any launch; launch failures return QM_ERR_CUDA.

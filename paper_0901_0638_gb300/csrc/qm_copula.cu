@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <utility>
 #include <vector>
 
 #include "qm.h"
@@ -44,6 +45,9 @@ __device__ __forceinline__ double normal_from_words(uint32_t hi, uint32_t lo)
     return upper ? m : -m;
 }
 
+// D: the dimension at compile time, so that y = L eps unrolls to exactly the
+// D(D+1)/2 products of the lower triangle
+template <int D>
 __global__ void __launch_bounds__(128)
 k_copula(const CopulaDev* __restrict__ cp, PhiloxKeys K, uint64_t blk0, double* out, size_t n)
 {
@@ -54,35 +58,60 @@ k_copula(const CopulaDev* __restrict__ cp, PhiloxKeys K, uint64_t blk0, double* 
         for (int i = threadIdx.x; i < (int)(sizeof(CopulaDev) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
     }
     __syncthreads();
-    const int d = c.d;
-    const int nb = (d + 1) / 2;
+    constexpr int nb = (D + 1) / 2;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        double y[kMaxD];
+        double y[D];
 #pragma unroll
-        for (int j = 0; j < kMaxD; ++j) y[j] = 0.0;
+        for (int j = 0; j < D; ++j) y[j] = 0.0;
 #pragma unroll
-        for (int b = 0; b < (kMaxD + 1) / 2; ++b) {
-            if (b >= nb) break;
+        for (int b = 0; b < nb; ++b) {
             const uint4 w = philox_block_keys(K, blk0 + (uint64_t)i * nb + b);
             const double e0 = normal_from_words(w.x, w.y);
             const double e1 = normal_from_words(w.z, w.w);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int k = 2 * b + h;
+                if (k >= D) break;
                 const double e = h ? e1 : e0;
 #pragma unroll
-                for (int j = 0; j < kMaxD; ++j)
-                    if (j >= k && j < d && k < d) y[j] = __fma_rn(c.L[j * (j + 1) / 2 + k], e, y[j]);
+                for (int j = k; j < D; ++j) y[j] = __fma_rn(c.L[j * (j + 1) / 2 + k], e, y[j]);
             }
         }
 #pragma unroll
-        for (int j = 0; j < kMaxD; ++j) {
-            if (j >= d) break;
-            const double x = (c.kind[j] == QM_DIST_STUDENT_T) ? recycle_t_sel(c.t[j], y[j]) : y[j];
+        for (int j = 0; j < D; ++j) {
+            double x = y[j];
+            if (c.kind[j] == QM_DIST_STUDENT_T) x = recycle_t_call(c.t[j], x);
             __stcs(out + (size_t)j * n + i, x);
         }
     }
+}
+
+template <int D>
+qm_status launch_d(const CopulaDev* dev, PhiloxKeys K, uint64_t blk0, double* out, size_t n, cudaStream_t s)
+{
+    int bps = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_copula<D>, 128, 0);
+    const size_t cap = (size_t)(sm_count() > 0 ? sm_count() : 1) * (bps > 0 ? bps : 1);
+    size_t g = (n + 127) / 128;
+    if (g > cap) g = cap;
+    k_copula<D><<<(int)g, 128, 0, s>>>(dev, K, blk0, out, n);
+    return check_launch("copula sample");
+}
+
+template <int... Ds>
+qm_status launch_dispatch(int d, const CopulaDev* dev, PhiloxKeys K, uint64_t blk0, double* out, size_t n,
+                          cudaStream_t s, std::integer_sequence<int, Ds...>)
+{
+    qm_status st = QM_ERR_INVALID;
+    ((d == Ds + 1 ? (st = launch_d<Ds + 1>(dev, K, blk0, out, n, s), 0) : 0), ...);
+    return st;
+}
+
+qm_status launch_copula(int d, const CopulaDev* dev, PhiloxKeys K, uint64_t blk0, double* out, size_t n,
+                        cudaStream_t s)
+{
+    return launch_dispatch(d, dev, K, blk0, out, n, s, std::make_integer_sequence<int, kMaxD>{});
 }
 
 }  // namespace
@@ -144,13 +173,7 @@ extern "C" qm_status qm_copula_sample(const qm_copula* c, uint64_t key, uint64_t
     if (ctr0 % 4 != 0) return fail(QM_ERR_INVALID, "qm_copula_sample: ctr0 must be a multiple of 4");
     if (n == 0) return QM_OK;
     if (!out) return fail(QM_ERR_INVALID, "qm_copula_sample: null output");
-    int bps = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_copula, 128, 0);
-    const size_t cap = (size_t)(sm_count() > 0 ? sm_count() : 1) * (bps > 0 ? bps : 1);
-    size_t g = (n + 127) / 128;
-    if (g > cap) g = cap;
-    k_copula<<<(int)g, 128, 0, (cudaStream_t)stream>>>(c->dev, philox_keys(key), ctr0 / 4, out, n);
-    return check_launch("copula sample");
+    return launch_copula(c->host.d, c->dev, philox_keys(key), ctr0 / 4, out, n, (cudaStream_t)stream);
 }
 
 extern "C" qm_status qm_copula_destroy(qm_copula* c)

@@ -279,18 +279,38 @@ __device__ __forceinline__ double hyp_side_eval(const HypSide& S, double a)
     return seg_poly(S.seg[idx], s);
 }
 
+__device__ __forceinline__ double hyp_eval(const HypSide& R, const HypSide& L, double v)
+{
+    const uint64_t vb = (uint64_t)__double_as_longlong(v);
+    const double a = __longlong_as_double((long long)(vb & 0x7fffffffffffffffull));
+    // pick the side's table first and evaluate once (selecting between two
+    // evaluations would run both)
+    const bool neg = (vb >> 63) != 0;
+    const HypSide S{neg ? L.seg : R.seg, neg ? L.e_max : R.e_max};
+    double x = hyp_side_eval(S, a);
+    if ((vb & 0x7fffffffffffffffull) >= 0x7ff0000000000000ull) x = a;   // inf, NaN
+    return with_sign_of(x, vb);
+}
+
+// VEC: two elements per thread through 16-byte loads and stores (in and out
+// 16-byte aligned), the odd last element by thread 0 of block 0.
+template <bool VEC>
 __global__ void __launch_bounds__(256)
 k_hyp(HypSide R, HypSide L, const double* __restrict__ in, double* out, size_t n)
 {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const double v = __ldcs(in + i);
-        const uint64_t vb = (uint64_t)__double_as_longlong(v);
-        const double a = __longlong_as_double((long long)(vb & 0x7fffffffffffffffull));
-        double x;
-        if ((vb & 0x7fffffffffffffffull) >= 0x7ff0000000000000ull) x = a;   // inf, NaN
-        else x = (vb >> 63) ? hyp_side_eval(L, a) : hyp_side_eval(R, a);
-        __stcs(out + i, with_sign_of(x, vb));
+    if (VEC) {
+        const size_t nv = n / 2;
+        const double2* vin = reinterpret_cast<const double2*>(in);
+        double2* vout = reinterpret_cast<double2*>(out);
+        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
+            const double2 v = __ldcs(vin + i);
+            __stcs(vout + i, make_double2(hyp_eval(R, L, v.x), hyp_eval(R, L, v.y)));
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) out[n - 1] = hyp_eval(R, L, in[n - 1]);
+    } else {
+        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+            __stcs(out + i, hyp_eval(R, L, __ldcs(in + i)));
     }
 }
 
@@ -357,12 +377,16 @@ extern "C" qm_status qm_hyp_recycle(const qm_hyp* h, const double* v, double* x,
     if (n == 0) return QM_OK;
     if (!v || !x) return fail(QM_ERR_INVALID, "qm_hyp_recycle: null pointer");
     if (bad_overlap(v, n * 8, x, n * 8)) return fail(QM_ERR_INVALID, "qm_hyp_recycle: partially overlapping in/out");
+    const bool vec = (uintptr_t)v % 16 == 0 && (uintptr_t)x % 16 == 0;
     int bps = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_hyp, 256, 0);
-    const size_t cap = (size_t)(sm_count() > 0 ? sm_count() : 1) * (bps > 0 ? bps : 1);
-    size_t g = (n + 255) / 256;
+    if (vec) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_hyp<true>, 256, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_hyp<false>, 256, 0);
+    const size_t cap = (size_t)(sm_count() > 0 ? sm_count() : 1) * (bps > 0 ? bps : 1) * 8;
+    size_t g = ((vec ? n / 2 : n) + 255) / 256;
     if (g > cap) g = cap;
-    k_hyp<<<(int)g, 256, 0, (cudaStream_t)stream>>>(h->right, h->left, v, x, n);
+    if (g < 1) g = 1;
+    if (vec) k_hyp<true><<<(int)g, 256, 0, (cudaStream_t)stream>>>(h->right, h->left, v, x, n);
+    else k_hyp<false><<<(int)g, 256, 0, (cudaStream_t)stream>>>(h->right, h->left, v, x, n);
     return check_launch("hyperbolic recycle");
 }
 

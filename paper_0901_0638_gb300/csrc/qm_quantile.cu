@@ -104,24 +104,11 @@ struct ExpToNormal {
     __device__ double operator()(double x) const { return exp_to_normal_tbl(x); }
 };
 
-struct TMap {
-    int k;
-    __device__ double operator()(double z) const { return recycle_t(k, z); }
-};
-
 struct TDynMap {
     const ttbl::SegT* seg;
     const double* tail;
     __device__ double operator()(double z) const { return recycle_t_dyn(seg, tail, z); }
 };
-
-// index of nu in the tabulated set, or -1
-static int t_index(double nu)
-{
-    for (int i = 0; i < ttbl::NNU; ++i)
-        if (nu == ttbl::T_NU[i]) return i;
-    return -1;
-}
 
 // ===========================================================================
 // Generic streaming map
@@ -868,22 +855,22 @@ extern "C" qm_status qm_recycle(int src, int dst, const qm_params* p, const doub
     if (src == QM_DIST_NORMAL && dst == QM_DIST_STUDENT_T) {
         if (!p) return fail(QM_ERR_INVALID, "qm_recycle: Student t needs params (nu)");
         if (!(p->nu > 0.0)) return fail(QM_ERR_INVALID, "qm_recycle: nu must be > 0 (got %g)", p->nu);
-        const int k = t_index(p->nu);
-        if (k < 0 && !(p->nu >= QM_T_NU_MIN && p->nu <= QM_T_NU_MAX))
+        bool tabulated = false;
+        for (int i = 0; i < ttbl::NNU; ++i) tabulated |= (p->nu == ttbl::T_NU[i]);
+        if (!tabulated && !(p->nu >= QM_T_NU_MIN && p->nu <= QM_T_NU_MAX))
             return fail(QM_ERR_UNSUPPORTED, "qm_recycle: nu = %g outside [%g, %g] and not tabulated",
                         p->nu, QM_T_NU_MIN, QM_T_NU_MAX);
         if (n == 0) return QM_OK;
         if (!in || !out) return fail(QM_ERR_INVALID, "qm_recycle: null pointer");
         if (bad_overlap(in, n * 8, out, n * 8))
             return fail(QM_ERR_INVALID, "qm_recycle: partially overlapping in/out");
-        if (k >= 0) return launch_map(in, out, n, TMap{k}, (cudaStream_t)stream, "recycle normal->t");
         const void* seg = nullptr;
         const double* tail = nullptr;
         int kk = -1;
         const qm_status st = t_select(p->nu, &kk, &seg, &tail);
         if (st != QM_OK) return st;
         return launch_map(in, out, n, TDynMap{(const ttbl::SegT*)seg, tail}, (cudaStream_t)stream,
-                          "recycle normal->t (run-time table)");
+                          "recycle normal->t");
     }
     return fail(QM_ERR_UNSUPPORTED, "qm_recycle: pair (%d -> %d) not supported", src, dst);
 }

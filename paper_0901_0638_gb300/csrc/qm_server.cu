@@ -78,7 +78,8 @@ __device__ __forceinline__ double serve_f64_one(int kind, const TSel& t, uint32_
         return upper ? -m : m;
     }
     const double z = upper ? m : -m;
-    return (kind == 2) ? recycle_t_sel(t, z) : z;
+    if (kind == 2) return recycle_t_call(t, z);
+    return z;
 }
 
 __global__ void __launch_bounds__(kServeBlock)

@@ -301,6 +301,56 @@ qm_status t_table_device(double nu, const void** seg_dev, const double** tail_de
     return QM_OK;
 }
 
+namespace {
+
+// The offline tables of the tabulated nu, as device pointers: the segments in
+// this module's copy of SEG_T, the tail (nu, log kappa, TAIL_DEG, R_k) in a
+// small buffer built once per device.
+struct StaticT {
+    int device;
+    const ttbl::SegT* seg;
+    double* tail;          // NNU x (3 + TAIL_DEG + 1)
+};
+std::vector<StaticT> g_static;
+constexpr int kStaticTail = 3 + ttbl::TAIL_DEG + 1;
+
+qm_status static_tables(int dev, const StaticT** out)
+{
+    for (const StaticT& e : g_static)
+        if (e.device == dev) {
+            *out = &e;
+            return QM_OK;
+        }
+    StaticT e{dev, nullptr, nullptr};
+    void* seg = nullptr;
+    if (cudaGetSymbolAddress(&seg, ttbl::SEG_T) != cudaSuccess)
+        return fail(QM_ERR_CUDA, "Student t: table address lookup failed");
+    double kappa[ttbl::NNU], rt[ttbl::NNU][ttbl::TAIL_DEG + 1];
+    if (cudaMemcpyFromSymbol(kappa, ttbl::T_KAPPA, sizeof(kappa)) != cudaSuccess ||
+        cudaMemcpyFromSymbol(rt, ttbl::T_TAIL, sizeof(rt)) != cudaSuccess)
+        return fail(QM_ERR_CUDA, "Student t: table read failed");
+    std::vector<double> tail(ttbl::NNU * kStaticTail);
+    for (int k = 0; k < ttbl::NNU; ++k) {
+        double* t = &tail[k * kStaticTail];
+        t[0] = ttbl::T_NU[k];
+        t[1] = std::log(kappa[k]);
+        t[2] = ttbl::TAIL_DEG;
+        for (int c = 0; c <= ttbl::TAIL_DEG; ++c) t[3 + c] = rt[k][c];
+    }
+    if (cudaMalloc(&e.tail, sizeof(double) * tail.size()) != cudaSuccess)
+        return fail(QM_ERR_NOMEM, "Student t: table allocation failed");
+    if (cudaMemcpy(e.tail, tail.data(), sizeof(double) * tail.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(e.tail);
+        return fail(QM_ERR_CUDA, "Student t: table upload failed");
+    }
+    e.seg = (const ttbl::SegT*)seg;
+    g_static.push_back(e);
+    *out = &g_static.back();
+    return QM_OK;
+}
+
+}  // namespace
+
 qm_status t_select(double nu, int* k, const void** seg_dev, const double** tail_dev)
 {
     *seg_dev = nullptr;
@@ -308,6 +358,14 @@ qm_status t_select(double nu, int* k, const void** seg_dev, const double** tail_
     for (int i = 0; i < ttbl::NNU; ++i)
         if (nu == ttbl::T_NU[i]) {
             *k = i;
+            int dev = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess) return fail(QM_ERR_CUDA, "Student t: no current device");
+            std::lock_guard<std::mutex> lk(g_mu);
+            const StaticT* st = nullptr;
+            const qm_status s = static_tables(dev, &st);
+            if (s != QM_OK) return s;
+            *seg_dev = st->seg + i * NSEG;
+            *tail_dev = st->tail + i * kStaticTail;
             return QM_OK;
         }
     *k = -1;
