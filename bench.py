@@ -30,6 +30,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "Φ^{-1} Gsamples/s FP32/FP64 & % roofline; batched p50/p99 latency vs plain"
+FP64_WORKLOAD = ("fp64 normal quantile Phi^-1, n=2^28 doubles per GPU, seed-2 tail-stress mixture "
+                 "(90% k*2^-53, 10% 2^-e*m mirrored)")
 NOMINAL_FP64_TFLOPS = 1.25     # GB300 nominal dense FP64 (profiling recipe table)
 SMS, SCHEDULERS, LANES, MAX_SM_GHZ = 152, 4, 32, 2.07
 ISSUE_PEAK_TINSTR = SMS * SCHEDULERS * LANES * MAX_SM_GHZ / 1e3   # thread-instructions/ns -> T/s
@@ -171,8 +173,8 @@ def run_reference(args, rank, world):
     line = {"metric": METRIC, "value": val, "unit": "Gsamples/s", "n_gpus": 0, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": "fp64 normal quantile, seed-2 tail-stress mixture, per-step sample 2^20 of 2^28",
-                       "n": 1 << 28, "sample": m},
+            "config": {"workload": FP64_WORKLOAD, "n_per_gpu": 1 << 28,
+                       "sample": f"each step evaluates the first 2^20 of the 2^28 elements", "sample_n": m},
             "cpu_baseline": {"value": val, "unit": "Gsamples/s", "cores": threads, "kind": "oracle",
                              "sample": f"2^20 elements of the 2^28 workload per step"},
             "e2e": {"value": val, "unit": "Gsamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -229,13 +231,22 @@ def side_workload(args):
                                                 stream=stream), stream, args.steps, args.warmup)
         m = (mom / n).cpu().tolist()
         del out
+        # FP64 normals from 53-bit Philox integers (fixed-point FP64 evaluation),
+        # 2^30 samples written (8 GiB)
+        n64 = n >> 2
+        out64 = torch.empty(n64, dtype=torch.float64, device=dev)
+        ms_64 = timed(lambda: qm.qm_sample_fused(qm.QM_DIST_NORMAL, 3, 0, out64, out_is_f64=True,
+                                                 stream=stream), stream, args.steps, args.warmup)
+        del out64
         gbs = 4 * n / (ms_w * 1e-3) / 1e9
         line.update(value=n / (ms_w * 1e-3) / 1e9, ms_per_step=ms_w, dtype="f32",
                     config={"workload": f"fused Philox4x32-10 (seed 3) -> fp32 normal, n=2^{n.bit_length()-1}, "
                                         "written (16 GiB) and moments-only", "n": n},
                     roofline={"bound": "alu", "achieved_gbs_written": gbs, "hbm_frac_of_write": gbs / 6780.7},
                     moments={"ms_per_step": ms_m, "gsamples_s": n / (ms_m * 1e-3) / 1e9,
-                             "mean": m[0], "m2": m[1], "m3": m[2], "m4": m[3]})
+                             "mean": m[0], "m2": m[1], "m3": m[2], "m4": m[3]},
+                    fp64={"n": n64, "ms_per_step": ms_64, "gsamples_s": n64 / (ms_64 * 1e-3) / 1e9,
+                          "hbm_frac_of_write": 8 * n64 / (ms_64 * 1e-3) / 1e9 / 6780.7})
     elif args.workload == "hyperbolic":
         # exponential -> hyperbolic recycling (alpha, beta, delta) = (1.3, 0.4, 0.7)
         # over 2^n two-sided exponential base samples resident in HBM
@@ -276,8 +287,9 @@ def side_workload(args):
                     config={"workload": f"Gaussian copula d={d}, equicorrelation 0.5, normal/t margins, "
                                         f"n=2^{n.bit_length() - 1} samples, Philox4x32-10 in registers",
                             "values_per_s": d * n / (ms * 1e-3)},
-                    roofline={"bound": "alu", "note": "FP64: d normals (table) + d(d+1)/2 FMA + t maps "
-                                                      "per sample; 8 d B written per sample",
+                    roofline={"bound": "alu", "note": "FP64: d normals (fixed point, 1 DFMA each) + "
+                                                      "d(d+1)/2 FMA + t maps per sample; 8 d B written "
+                                                      "per sample",
                               "hbm_frac_of_write": 8 * d * n / (ms * 1e-3) / 1e9 / 6780.7})
         c.close()
     elif args.workload == "batch":
@@ -506,8 +518,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic",
-                "config": {"workload": "fp64 normal quantile Phi^-1, n=2^28 doubles per GPU, seed-2 "
-                                       "tail-stress mixture (90% k*2^-53, 10% 2^-e*m mirrored)",
+                "config": {"workload": FP64_WORKLOAD,
                            "n_per_gpu": n, "variant": args.variant, "l2": "inputs larger than L2 (4 GiB)",
                            "deep_tail_elements": n_deep, "subnormal_d_elements": n_sub,
                            "edge_elements": n_edge,

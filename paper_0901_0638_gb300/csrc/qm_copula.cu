@@ -5,7 +5,8 @@
 // fold into one: each coordinate goes straight through the recycling map
 // Q_j = F_j^{-1} o Phi.  One thread draws one d-dimensional sample:
 //     eps_k = Phi^{-1}((m_k + 1/2) 2^-53),  m_k a 53-bit Philox integer
-//             (two per Philox block, as the fused FP64 normal sampler),
+//             (two per Philox block, as the fused FP64 normal sampler;
+//             fixed-point FP64 evaluation, one FP64 FMA),
 //     y = L eps                              (L lower triangular, d <= 16),
 //     x_j = Q_j(y_j)                         (normal: identity; Student t:
 //                                             the Sec. 3 map, any supported nu).
@@ -19,6 +20,7 @@
 
 #include "qm.h"
 #include "qm_device.cuh"
+#include "qm_fx.cuh"
 #include "qm_host.h"
 
 namespace qm {
@@ -34,14 +36,13 @@ struct CopulaDev {
     TSel t[kMaxD];
 };
 
-// normal from two Philox words (53-bit integer, exact reflected grid point)
-__device__ __forceinline__ double normal_from_words(uint32_t hi, uint32_t lo)
+// normal from two Philox words (53-bit integer, exact reflected grid point,
+// the fixed-point FP64 evaluation)
+__device__ __forceinline__ double normal_from_words(const fxt::SegFx* fxT, uint32_t hi, uint32_t lo)
 {
     const uint64_t k = ((uint64_t)(hi >> 11) << 32) | lo;
-    const bool upper = k >= (1ull << 52);
-    const uint64_t j = upper ? ((1ull << 53) - 1 - k) : k;
-    const double d = ((double)j + 0.5) * 1.1102230246251565404e-16;   // exact, >= 2^-54
-    const double m = probit_mag_f64_tbl(d);
+    bool upper;
+    const double m = probit_grid53_fx(fxT, k, upper);
     return upper ? m : -m;
 }
 
@@ -49,7 +50,8 @@ __device__ __forceinline__ double normal_from_words(uint32_t hi, uint32_t lo)
 // D(D+1)/2 products of the lower triangle
 template <int D>
 __global__ void __launch_bounds__(128)
-k_copula(const CopulaDev* __restrict__ cp, PhiloxKeys K, uint64_t blk0, double* out, size_t n)
+k_copula(const CopulaDev* __restrict__ cp, PhiloxKeys K, uint64_t blk0, double* out, size_t n,
+         const fxt::SegFx* fxT)
 {
     __shared__ CopulaDev c;
     {
@@ -67,8 +69,8 @@ k_copula(const CopulaDev* __restrict__ cp, PhiloxKeys K, uint64_t blk0, double* 
 #pragma unroll
         for (int b = 0; b < nb; ++b) {
             const uint4 w = philox_block_keys(K, blk0 + (uint64_t)i * nb + b);
-            const double e0 = normal_from_words(w.x, w.y);
-            const double e1 = normal_from_words(w.z, w.w);
+            const double e0 = normal_from_words(fxT, w.x, w.y);
+            const double e1 = normal_from_words(fxT, w.z, w.w);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int k = 2 * b + h;
@@ -90,12 +92,15 @@ k_copula(const CopulaDev* __restrict__ cp, PhiloxKeys K, uint64_t blk0, double* 
 template <int D>
 qm_status launch_d(const CopulaDev* dev, PhiloxKeys K, uint64_t blk0, double* out, size_t n, cudaStream_t s)
 {
+    qm_status fst;
+    const fxt::SegFx* fxT = (const fxt::SegFx*)fx_table_device(&fst);
+    if (!fxT) return fst;
     int bps = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_copula<D>, 128, 0);
     const size_t cap = (size_t)(sm_count() > 0 ? sm_count() : 1) * (bps > 0 ? bps : 1);
     size_t g = (n + 127) / 128;
     if (g > cap) g = cap;
-    k_copula<D><<<(int)g, 128, 0, s>>>(dev, K, blk0, out, n);
+    k_copula<D><<<(int)g, 128, 0, s>>>(dev, K, blk0, out, n, fxT);
     return check_launch("copula sample");
 }
 

@@ -15,6 +15,9 @@ bool bad_overlap(const void* a, size_t abytes, const void* b, size_t bbytes);
 // FP64 normal quantile, fixed-point segment evaluation (qm_fixed.cu); u and z
 // device arrays of n doubles, in place allowed; stream is a cudaStream_t.
 qm_status launch_f64_fixed(const double* u, double* z, size_t n, void* stream);
+// Device address of the fixed-point FP64 table (fxt::SEG_FX) on the current
+// device, or NULL with *st set.
+const void* fx_table_device(qm_status* st);
 
 // Normal -> Student t tables for nu in [QM_T_NU_MIN, QM_T_NU_MAX] (qm_tdyn.cu):
 // host build (seg: NSEG x 10 coefficients, tail: nu, log kappa, degree, R_k)

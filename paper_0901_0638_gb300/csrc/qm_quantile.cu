@@ -21,6 +21,7 @@
 
 #include "qm.h"
 #include "qm_device.cuh"
+#include "qm_fx.cuh"
 #include "qm_exp_map.cuh"
 #include "qm_host.h"
 #include "qm_tables_deep.h"
@@ -566,33 +567,14 @@ k_fused_normal_f32(PhiloxKeys K, uint64_t blk0, size_t n, float* out, double* pa
 
 // FP64 normal samples: block b gives two samples from 53-bit integers
 // k = (w0 >> 11) 2^32 + w1 and (w2 >> 11) 2^32 + w3, evaluated at the exact
-// reflected point d = (min(k, 2^53-1-k) + 1/2) 2^-53 with the t_2 / warp-vote
-// hybrid (Sec. 7.3).  KIND 0: normal; KIND 2: exponential -> normal with
-// x = -log((k + 1/2) 2^-53).
-__device__ __forceinline__ double half_open53(uint32_t hi, uint32_t lo, bool& upper)
-{
-    const uint64_t k = ((uint64_t)(hi >> 11) << 32) | lo;
-    upper = k >= (1ull << 52);
-    const uint64_t j = upper ? ((1ull << 53) - 1 - k) : k;
-    return ((double)j + 0.5) * 1.1102230246251565404e-16;   // 2^-53, exact
-}
-
-__device__ __forceinline__ double normal_from_d_vote(double d, bool upper, bool valid)
-{
-    const bool t2 = in_t2_domain(d) || !valid;
-    double m;
-    if (__all_sync(0xffffffffu, t2)) {
-        m = probit_mag_t2(t2_coord(d));
-    } else {
-        const double v = -log(2.0 * d);
-        m = probit_mag_exp_main(v);   // d >= 2^-54 here: v <= 36.7 < 42
-    }
-    return upper ? m : -m;
-}
+// reflected point d = (min(k, 2^53-1-k) + 1/2) 2^-53 by the fixed-point FP64
+// evaluation of the Sec. 7.3 segment expansions.  KIND 0: normal; KIND 2:
+// exponential -> normal with x = -log((k + 1/2) 2^-53).
 
 template <int KIND, bool OUT, bool MOM>
 __global__ void __launch_bounds__(256)
-k_fused_f64(PhiloxKeys K, uint64_t blk0, size_t n, double* out, double* partials, TSel tk)
+k_fused_f64(PhiloxKeys K, uint64_t blk0, size_t n, double* out, double* partials, TSel tk,
+            const fxt::SegFx* fxT)
 {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     const size_t nblk = (n + 1) / 2;
@@ -607,17 +589,17 @@ k_fused_f64(PhiloxKeys K, uint64_t blk0, size_t n, double* out, double* partials
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             bool upper;
-            const double d = half_open53(h ? w.z : w.x, h ? w.w : w.y, upper);
+            const uint32_t hi = h ? w.z : w.x, lo = h ? w.w : w.y;
+            const unsigned long long kk = ((unsigned long long)(hi >> 11) << 32) | lo;
+            const double zn = probit_grid53_fx(fxT, kk, upper);   // |Phi^{-1}((k + 1/2) 2^-53)|
             if (KIND == 0) {
-                z[h] = normal_from_d_vote(d, upper, valid);
+                z[h] = upper ? zn : -zn;
             } else if (KIND == 1) {
                 // Student t by recycling the normal sample (Sec. 3 map)
-                const double zn = probit_mag_f64_tbl(d);
                 z[h] = recycle_t_sel(tk, upper ? zn : -zn);
             } else {
                 // Exp(1) sample x = -log(u) recycled by the Sec. 6 map:
                 // Q(x) = Phi^{-1}(1 - u), evaluated from the exact u (no log)
-                const double zn = probit_mag_f64_tbl(d);
                 z[h] = upper ? -zn : zn;
             }
         }
@@ -823,10 +805,13 @@ extern "C" qm_status qm_sample_fused(int target, const qm_params* p, uint64_t ke
         double* o = (double*)out;
         const uint64_t b0 = ctr0 / 4;
         const PhiloxKeys key = philox_keys(key_in);
-#define QM_LAUNCH_F64(KIND)                                                                  \
-    if (o && part) k_fused_f64<KIND, true, true><<<g, B, 0, s>>>(key, b0, n, o, part, tk);   \
-    else if (o) k_fused_f64<KIND, true, false><<<g, B, 0, s>>>(key, b0, n, o, nullptr, tk);  \
-    else k_fused_f64<KIND, false, true><<<g, B, 0, s>>>(key, b0, n, nullptr, part, tk);
+        qm_status fst;
+        const fxt::SegFx* fxT = (const fxt::SegFx*)fx_table_device(&fst);
+        if (!fxT) return fst;
+#define QM_LAUNCH_F64(KIND)                                                                        \
+    if (o && part) k_fused_f64<KIND, true, true><<<g, B, 0, s>>>(key, b0, n, o, part, tk, fxT);   \
+    else if (o) k_fused_f64<KIND, true, false><<<g, B, 0, s>>>(key, b0, n, o, nullptr, tk, fxT);  \
+    else k_fused_f64<KIND, false, true><<<g, B, 0, s>>>(key, b0, n, nullptr, part, tk, fxT);
         if (target == QM_DIST_NORMAL) { QM_LAUNCH_F64(0) }
         else if (target == QM_DIST_STUDENT_T) { QM_LAUNCH_F64(1) }
         else { QM_LAUNCH_F64(2) }

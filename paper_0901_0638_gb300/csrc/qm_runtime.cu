@@ -21,6 +21,7 @@
 
 #include "qm.h"
 #include "qm_device.cuh"
+#include "qm_fx.cuh"
 #include "qm_exp_map.cuh"
 #include "qm_host.h"
 
@@ -40,7 +41,7 @@ struct DevSeg {
 
 template <int EPT, bool ESTRIN>
 __global__ void __launch_bounds__(512)
-k_batch(const DevSeg* __restrict__ segs, int nseg, unsigned long long ntiles)
+k_batch(const DevSeg* __restrict__ segs, int nseg, unsigned long long ntiles, const fxt::SegFx* fxT)
 {
     for (unsigned long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         int lo = 0, hi = nseg - 1;
@@ -62,7 +63,7 @@ k_batch(const DevSeg* __restrict__ segs, int nseg, unsigned long long ntiles)
             double y;
             if (sg.kind == KIND_T) y = recycle_t_sel<ESTRIN>(sg.t, x[k]);
             else if (sg.kind == KIND_EXP) y = exp_to_normal_tbl(x[k]);
-            else y = probit_f64_any(x[k]);
+            else y = probit_fx(fxT, x[k]);
             if (i < sg.n) __stcs(sg.out + i, y);
         }
     }
@@ -70,7 +71,7 @@ k_batch(const DevSeg* __restrict__ segs, int nseg, unsigned long long ntiles)
 
 // One plain launch per segment (the comparison baseline for the batch).
 __global__ void __launch_bounds__(256)
-k_single(const double* __restrict__ in, double* out, size_t n, int kind, TSel t)
+k_single(const double* __restrict__ in, double* out, size_t n, int kind, TSel t, const fxt::SegFx* fxT)
 {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -78,12 +79,12 @@ k_single(const double* __restrict__ in, double* out, size_t n, int kind, TSel t)
         double y;
         if (kind == KIND_T) y = recycle_t_sel<false>(t, x);
         else if (kind == KIND_EXP) y = exp_to_normal_tbl(x);
-        else y = probit_f64_any(x);
+        else y = probit_fx(fxT, x);
         __stcs(out + i, y);
     }
 }
 
-using BatchKernel = void (*)(const DevSeg*, int, unsigned long long);
+using BatchKernel = void (*)(const DevSeg*, int, unsigned long long, const fxt::SegFx*);
 
 static BatchKernel pick_kernel(int ept, int estrin)
 {
@@ -300,9 +301,12 @@ extern "C" qm_status qm_batch_run(qm_batch* b, void* stream)
     if (b->ntiles == 0) return QM_OK;
     if (!b->exec) {
         BatchKernel k = pick_kernel(b->tuning.ept, b->tuning.estrin);
+        qm_status fst;
+        const fxt::SegFx* fxT = (const fxt::SegFx*)fx_table_device(&fst);
+        if (!fxT) return fst;
         if (cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             return fail(QM_ERR_CUDA, "qm_batch_run: stream capture failed to start");
-        k<<<b->grid, b->tuning.block, 0, b->capture>>>(b->dev, b->nseg, b->ntiles);
+        k<<<b->grid, b->tuning.block, 0, b->capture>>>(b->dev, b->nseg, b->ntiles, fxT);
         cudaError_t e = cudaStreamEndCapture(b->capture, &b->graph);
         if (e != cudaSuccess) return fail(QM_ERR_CUDA, "qm_batch_run: capture: %s", cudaGetErrorString(e));
         e = cudaGraphInstantiate(&b->exec, b->graph, 0);
@@ -320,10 +324,13 @@ extern "C" qm_status qm_batch_run_separate(qm_batch* b, void* stream)
 {
     if (!b) return fail(QM_ERR_INVALID, "qm_batch_run_separate: null batch");
     const int sms = sm_count() > 0 ? sm_count() : 1;
+    qm_status fst;
+    const fxt::SegFx* fxT = (const fxt::SegFx*)fx_table_device(&fst);
+    if (!fxT) return fst;
     for (const DevSeg& s : b->host) {
         if (!s.n) continue;
         int g = (int)std::min<size_t>((s.n + 255) / 256, (size_t)sms * 8);
-        k_single<<<g, 256, 0, (cudaStream_t)stream>>>(s.in, s.out, s.n, s.kind, s.t);
+        k_single<<<g, 256, 0, (cudaStream_t)stream>>>(s.in, s.out, s.n, s.kind, s.t, fxT);
     }
     return check_launch("qm_batch_run_separate");
 }

@@ -29,6 +29,7 @@
 
 #include "qm.h"
 #include "qm_device.cuh"
+#include "qm_fx.cuh"
 #include "qm_host.h"
 
 namespace qm {
@@ -63,13 +64,12 @@ __device__ __forceinline__ void serve_f32(const ReqDev& r, unsigned long long pb
     }
 }
 
-__device__ __forceinline__ double serve_f64_one(int kind, const TSel& t, uint32_t hi, uint32_t lo)
+__device__ __forceinline__ double serve_f64_one(const fxt::SegFx* fxT, int kind, const TSel& t, uint32_t hi,
+                                                uint32_t lo)
 {
     const uint64_t k = ((uint64_t)(hi >> 11) << 32) | lo;
-    const bool upper = k >= (1ull << 52);
-    const uint64_t j = upper ? ((1ull << 53) - 1 - k) : k;
-    const double d = ((double)j + 0.5) * 1.1102230246251565404e-16;   // exact
-    const double m = probit_mag_f64_tbl(d);                 // d >= 2^-54: covered
+    bool upper;
+    const double m = probit_grid53_fx(fxT, k, upper);      // |Phi^{-1}((k + 1/2) 2^-53)|
     if (kind == 3) {
         // Exp(1) sample x = -log(u), u = (k + 1/2) 2^-53, recycled to the
         // normal by Q(x) = Phi^{-1}(1 - e^{-x}) = Phi^{-1}(1 - u) (Sec. 6): the
@@ -83,7 +83,7 @@ __device__ __forceinline__ double serve_f64_one(int kind, const TSel& t, uint32_
 }
 
 __global__ void __launch_bounds__(kServeBlock)
-k_serve(const ReqDev* __restrict__ reqs, int nreq, unsigned long long ntiles)
+k_serve(const ReqDev* __restrict__ reqs, int nreq, unsigned long long ntiles, const fxt::SegFx* fxT)
 {
     for (unsigned long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         int lo = 0, hi = nreq - 1;
@@ -104,8 +104,8 @@ k_serve(const ReqDev* __restrict__ reqs, int nreq, unsigned long long ntiles)
             } else {
                 const uint4 w = philox_block(r.key, pb);
                 double* o = static_cast<double*>(r.out);
-                const double z0 = serve_f64_one(r.kind, r.t, w.x, w.y);
-                const double z1 = serve_f64_one(r.kind, r.t, w.z, w.w);
+                const double z0 = serve_f64_one(fxT, r.kind, r.t, w.x, w.y);
+                const double z1 = serve_f64_one(fxT, r.kind, r.t, w.z, w.w);
                 const unsigned long long i0 = pb * 2;
                 if (i0 + 2 <= r.n && ((uintptr_t)(o + i0) % 16 == 0)) {
                     __stcs(reinterpret_cast<double2*>(o + i0), make_double2(z0, z1));
@@ -241,6 +241,8 @@ static void worker_loop(qm_server* s)
     int bps = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_serve, kServeBlock, 0);
     if (bps < 1) bps = 1;
+    qm_status fst;
+    const fxt::SegFx* fxT = (const fxt::SegFx*)fx_table_device(&fst);   // looked up at create
     std::vector<ReqDev> table;
     while (true) {
         bool idle = true;
@@ -329,7 +331,7 @@ static void worker_loop(qm_server* s)
             for (auto& c : batch) c.t_launch = tl;
             if (t0 > 0) {
                 const int grid = (int)std::min<unsigned long long>(t0, (unsigned long long)sms * bps);
-                k_serve<<<grid, kServeBlock, 0, sl.stream>>>(sl.dev, (int)table.size(), t0);
+                k_serve<<<grid, kServeBlock, 0, sl.stream>>>(sl.dev, (int)table.size(), t0, fxT);
             }
             cudaEventRecord(sl.ev, sl.stream);
             if (cudaGetLastError() != cudaSuccess) {
@@ -367,6 +369,10 @@ extern "C" qm_status qm_server_create(const qm_server_config* cfg, qm_server** o
     if (cudaSetDevice(cfg->device) != cudaSuccess) {
         delete s;
         return fail(QM_ERR_CUDA, "qm_server_create: cudaSetDevice(%d) failed", cfg->device);
+    }
+    {
+        qm_status fst;
+        if (!fx_table_device(&fst)) return fst;      // the worker's kernels read this table
     }
     if (!s->arena.init(cfg->mem_budget)) {
         delete s;

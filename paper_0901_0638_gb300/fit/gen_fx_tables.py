@@ -206,13 +206,8 @@ def main():
         f"// Binade e = -1 - E: K = {K_MAIN} for e < {E_MAIN}, K = {K_DEEP} for e = {E_MAIN}..{E_LAST}.\n",
         f"// Index e 2^{K_MAIN} + j (e < {E_MAIN}), {N_MAIN} + (e - {E_MAIN}) 2^{K_DEEP} + j.\n",
         f"// Emulated worst relative error over the checked points: {worst:.3g}.\n",
-        "#pragma once\n#include <stdint.h>\n\nnamespace qm {\nnamespace fxt {\n\n",
-        f"constexpr int K_MAIN = {K_MAIN};\nconstexpr int E_MAIN = {E_MAIN};\n",
-        f"constexpr int K_DEEP = {K_DEEP};\nconstexpr int E_LAST = {E_LAST};\n",
-        f"constexpr int N_MAIN = {N_MAIN};\nconstexpr int N_ALL = {N_ALL};\n\n",
-        "struct alignas(64) SegFx {\n"
-        "    double a0;\n    long long B0, B1, B2;\n    float f3, f4, f5, f6;\n"
-        "    int s0;\n    float csc;\n    int sh;\n    int pad;\n};\n\n",
+        "#pragma once\n#include \"qm_fx.cuh\"   // layout (K_MAIN .. N_ALL, SegFx) and evaluation\n\n",
+        "namespace qm {\nnamespace fxt {\n\n",
         f"__device__ const SegFx SEG_FX[{N_ALL}] = {{\n",
     ]
     for e, j, q, _ in res:
