@@ -368,7 +368,8 @@ def main():
     variants = {"default": qm.QM_VAR_DEFAULT, "fixed": qm.QM_VAR_FIXED, "table": qm.QM_VAR_TABLE,
                 "compact": qm.QM_VAR_COMPACT,
                 "branchfree": qm.QM_VAR_BRANCHFREE, "hybrid_vote": qm.QM_VAR_HYBRID_VOTE,
-                "mixed_halley": qm.QM_VAR_MIXED_HALLEY, "cuda_normcdfinv": qm.QM_VAR_CUDA_LIBM}
+                "mixed_halley": qm.QM_VAR_MIXED_HALLEY, "almost_normal": qm.QM_VAR_ALMOST_NORMAL,
+                "t2_multi": qm.QM_VAR_T2_MULTI, "cuda_normcdfinv": qm.QM_VAR_CUDA_LIBM}
     var = variants[args.variant]
     u = W.mixture_f64(2, n, first=shard_first(rank, n), device=dev)
     z = torch.empty_like(u)
@@ -453,12 +454,33 @@ def main():
             torch.cuda.synchronize(dev)
             t = ev_a.elapsed_time(ev_b) / reps
             extras[f"fp64_{name}"] = {"ms": t, "gsamples_s": n / (t * 1e-3) / 1e9}
+        # the branchy variants on 53-bit uniforms alone (seed 8, no tail
+        # stress): the inputs where the vote and the extra t_2 branch matter
+        del z
+        uu = W.uniform53(8, n, device=dev)
+        zu = torch.empty_like(uu)
+        uni = {}
+        for name in ("fixed", "compact", "hybrid_vote", "t2_multi", "almost_normal"):
+            v = variants[name]
+            qm.qm_normal_quantile_f64(uu, zu, v, stream=stream)
+            torch.cuda.synchronize(dev)
+            ev_a.record(stream)
+            for _ in range(3):
+                qm.qm_normal_quantile_f64(uu, zu, v, stream=stream)
+            ev_b.record(stream)
+            torch.cuda.synchronize(dev)
+            t = ev_a.elapsed_time(ev_b) / 3
+            uni[name] = {"ms": t, "gsamples_s": n / (t * 1e-3) / 1e9}
+        extras["fp64_uniform53_only"] = uni
+        del uu, zu
+        z = torch.empty_like(u)
         # FP32 normal quantile on the 24-bit Philox grid at the same n (HBM bound)
         del z
         _, u32 = W.uniform24(1, n, device=dev)
         z32 = torch.empty_like(u32)
         for name, v in (("table", qm.QM_VAR_TABLE), ("sqrt_form", qm.QM_VAR_SQRT_FORM),
-                        ("paper_form", qm.QM_VAR_BRANCHFREE), ("cuda_normcdfinvf", qm.QM_VAR_CUDA_LIBM)):
+                        ("paper_form", qm.QM_VAR_BRANCHFREE), ("almost_normal", qm.QM_VAR_ALMOST_NORMAL),
+                        ("cuda_normcdfinvf", qm.QM_VAR_CUDA_LIBM)):
             qm.qm_normal_quantile_f32(u32, z32, v, stream=stream)
             torch.cuda.synchronize(dev)
             ev_a.record(stream)

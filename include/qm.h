@@ -78,12 +78,25 @@ typedef enum {
                                 r = m c - 1, |z| = local expansion G(r) of Q(v)
                                 from the recycling ODE (FP64: d >= 2^-65, the
                                 deep tail compacted to the deep rational)       */
-    QM_VAR_FIXED = 8         /* FP64: the same segment expansions (Sec. 2.3,
+    QM_VAR_FIXED = 8,        /* FP64: the same segment expansions (Sec. 2.3,
                                 Sec. 6) in an exact integer offset t from the
                                 segment anchor, evaluated in 64-bit fixed
                                 point with one FP64 FMA, |z| = a0 + t H(t);
                                 every 0 < u < 1 (subnormal u too) takes the
                                 same path.  The FP64 default.                   */
+    QM_VAR_ALMOST_NORMAL = 9, /* FP32 and FP64: the almost-normal /
+                                almost-chi-squared filtering coordinates
+                                (Sec. 5.3): a = -(pi/2) log(4 d (1-d));
+                                a <= 8: |z| = (1 - 2d) P(a); a > 8: |z| = T(sqrt a)
+                                on pieces of the sqrt(a) axis; polynomials
+                                only (no divide).  FP64: one Horner loop over a
+                                per-lane coefficient row (no branch).           */
+    QM_VAR_T2_MULTI = 10     /* FP64: the hybrid with more branches (Sec. 7.5):
+                                t_2 coordinate for v <= 1000 (the Sec. 7.3
+                                rational on v <= 15.5, a second (14,15) t_2
+                                rational on the near tail 15.5 < v <= 1000,
+                                coefficients selected per lane), the rest
+                                compacted per tile onto the exponential form.  */
 } qm_variant;
 
 typedef struct {

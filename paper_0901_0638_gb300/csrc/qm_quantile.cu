@@ -25,6 +25,7 @@
 #include "qm_exp_map.cuh"
 #include "qm_host.h"
 #include "qm_tables_deep.h"
+#include "qm_filter_coeffs.h"
 
 namespace qm {
 
@@ -100,6 +101,111 @@ struct F64Mixed {
     }
 };
 struct F64Libm { __device__ double operator()(double u) const { return normcdfinv(u); } };
+
+// ---------------------------------------------------------------------------
+// Almost-normal / almost-chi-squared filtering coordinates (Sec. 5.3):
+//     a = -(pi/2) log(4 d (1 - d)) = Q_AN(u)^2,  w = sqrt(a) = |Q_AN(u)|,
+//     a <= 8: |z| = (1 - 2d) P(a - a_c);   a > 8: |z| = T_k(w - w_c).
+// 4 d (1 - d) = (2d)(2 - 2d): 2d is exact, 2 - 2d rounds once.
+// ---------------------------------------------------------------------------
+constexpr double kHalfPi = 1.5707963267948966;
+
+// FP64: every piece is a degree-20 polynomial, so one Horner loop runs over
+// the lane's coefficient row (no divergent branch).  d in (0, 1/2].
+__device__ __forceinline__ double probit_mag_an64(double d)
+{
+    const double t4 = __dmul_rn(2.0 * d, __fma_rn(-2.0, d, 2.0));
+    const double a = fmax(-kHalfPi * log(t4), 0.0);
+    const bool centre = a <= filt::AN_A0;
+    const double w = sqrt(a);
+    const int row = centre ? 0
+        : 1 + (w > filt::AN64_WHI[0]) + (w > filt::AN64_WHI[1]) + (w > filt::AN64_WHI[2]);
+    const double* c = filt::AN64[row];
+    const double s = __dadd_rn(centre ? a : w, -__ldg(c));
+    double acc = __ldg(c + filt::AN64_DEG + 1);
+#pragma unroll
+    for (int k = filt::AN64_DEG; k >= 1; --k) acc = __fma_rn(acc, s, __ldg(c + k));
+    const double f = centre ? __fma_rn(-2.0, d, 1.0) : 1.0;
+    return __dmul_rn(f, acc);
+}
+
+struct F64AlmostNormal {
+    __device__ double operator()(double u) const
+    {
+        const double d = reflect_f64(u);
+        const double m = (d > 0.0 && d <= 0.5) ? probit_mag_an64(d) : 0.0;
+        return fix_edges_f64(u, d, m);
+    }
+};
+
+// FP32: centre polynomial with its coefficients as constant operands; the
+// tail (d < 1.7e-3) reads one of two rows.  d in (0, 1/2]; d below 2^-100 is
+// scaled by 2^64 before the MUFU logarithm, which flushes subnormals.
+__device__ __forceinline__ float probit_mag_an32(float d)
+{
+    const bool tiny = d < 7.888609052210118e-31f;                      // 2^-100
+    const float ds = tiny ? d * 1.8446744073709552e19f : d;              // 2^64
+    const float t4 = __fmul_rn(2.0f * ds, __fmaf_rn(-2.0f, d, 2.0f));
+    const float lg = __log2f(t4) - (tiny ? 64.0f : 0.0f);
+    const float a = fmaxf(-1.0887930451518f * lg, 0.0f);                // (pi/2) ln 2
+    if (a <= (float)filt::AN_A0) {
+        const float s = a - filt::AN32_C_OFF;
+        float acc = filt::AN32_C[filt::AN32_DEG];
+#pragma unroll
+        for (int k = filt::AN32_DEG - 1; k >= 0; --k) acc = __fmaf_rn(acc, s, filt::AN32_C[k]);
+        return __fmul_rn(__fmaf_rn(-2.0f, d, 1.0f), acc);
+    }
+    const float w = sqrtf(a);
+    const float* c = filt::AN32_T[w > filt::AN32_WHI0 ? 1 : 0];
+    const float s = w - __ldg(c);
+    float acc = __ldg(c + filt::AN32_DEG + 1);
+#pragma unroll
+    for (int k = filt::AN32_DEG; k >= 1; --k) acc = __fmaf_rn(acc, s, __ldg(c + k));
+    return acc;
+}
+
+struct F32AlmostNormal {
+    __device__ float operator()(float u) const
+    {
+        const bool upper = u >= 0.5f;
+        const float d = upper ? __fadd_rn(1.0f, -u) : u;   // exact for u >= 1/2
+        float mag = (d > 0.0f && d <= 0.5f) ? probit_mag_an32(d) : 0.0f;
+        mag = (d == 0.0f) ? __int_as_float(0x7f800000) : mag;
+        mag = (u >= 0.0f && u <= 1.0f) ? mag : __int_as_float(0x7fffffff);
+        return upper ? mag : -mag;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// t_2 coordinate with more branches (Sec. 7.5): the Sec. 7.3 rational on
+// v <= 15.5 and a second (14,15) rational on the near tail 15.5 < v <= 1000,
+// one evaluation with the coefficients selected per lane.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double probit_mag_t2_two(double v)
+{
+    const bool near = v > 15.5;
+    double p = near ? filt::T2N_P[14] : coef::F64_T2_P[14];
+#pragma unroll
+    for (int k = 13; k >= 0; --k) p = __fma_rn(p, v, near ? filt::T2N_P[k] : coef::F64_T2_P[k]);
+    double q = near ? filt::T2N_Q[15] : coef::F64_T2_Q[15];
+#pragma unroll
+    for (int k = 14; k >= 0; --k) q = __fma_rn(q, v, near ? filt::T2N_Q[k] : coef::F64_T2_Q[k]);
+    return __dmul_rn(v, div_f64(p, q));
+}
+
+__device__ __forceinline__ bool in_t2_multi_domain(double d) { return d > filt::T2N_D_LO; }
+
+// element-wise form (in-place calls): the far tail as a divergent branch
+struct F64T2Multi {
+    __device__ double operator()(double u) const
+    {
+        const double d = reflect_f64(u);
+        double m = 0.0;
+        if (in_t2_multi_domain(d)) m = probit_mag_t2_two(t2_coord(d));
+        else if (d > 0.0) m = probit_mag_f64_exp(d);
+        return fix_edges_f64(u, d, m);
+    }
+};
 
 struct ExpToNormal {
     __device__ double operator()(double x) const { return exp_to_normal_tbl(x); }
@@ -311,6 +417,9 @@ __device__ __forceinline__ void queue_push(bool pred, int* counter, unsigned sho
     if (pred) q[base + __popc(mask & ((1u << lane) - 1u))] = idx;
 }
 
+// MULTI: the in-place branch is the two-piece t_2 form on v <= 1000 (Sec. 7.5)
+// instead of the Sec. 7.3 rational on v <= 15.5.
+template <bool MULTI>
 __global__ void __launch_bounds__(kCompactBlock)
 k_f64_compact(const double* __restrict__ in, double* out, size_t n)
 {
@@ -335,11 +444,12 @@ k_f64_compact(const double* __restrict__ in, double* out, size_t n)
             const double u = a[k];
             const double d = reflect_f64(u);
             const bool edge = !(d > 0.0 && d <= 0.5);       // 0, NaN, out of range
-            const bool t2 = !edge && in_t2_domain(d);
+            const bool t2 = !edge && (MULTI ? in_t2_multi_domain(d) : in_t2_domain(d));
             const bool deep = !edge && !t2 && is_deep(d);
             const bool ex = !edge && !t2 && !deep;
             if (i < n && (t2 || edge)) {
-                const double m = t2 ? probit_mag_t2(t2_coord(d)) : 0.0;
+                const double m = t2 ? (MULTI ? probit_mag_t2_two(t2_coord(d)) : probit_mag_t2(t2_coord(d)))
+                                    : 0.0;
                 __stcs(out + i, fix_edges_f64(u, d, m));
             }
             queue_push(i < n && ex, &cnt[0], q_exp, li);
@@ -668,6 +778,7 @@ extern "C" qm_status qm_normal_quantile_f32(const float* u, float* z, size_t n, 
     case QM_VAR_SQRT_FORM: return launch_map(u, z, n, F32Sqrt(), s, "f32 sqrt form");
     case QM_VAR_BRANCHFREE: return launch_map(u, z, n, F32Paper(), s, "f32 branch-free");
     case QM_VAR_CUDA_LIBM: return launch_map(u, z, n, F32Libm(), s, "f32 normcdfinvf");
+    case QM_VAR_ALMOST_NORMAL: return launch_map(u, z, n, F32AlmostNormal(), s, "f32 almost-normal");
     case QM_VAR_DEFAULT:
     case QM_VAR_TABLE: {
         if ((uintptr_t)u % 16 != 0 || (uintptr_t)z % 16 != 0)
@@ -717,10 +828,21 @@ extern "C" qm_status qm_normal_quantile_f64(const double* u, double* z, size_t n
             return check_launch("f64 hybrid vote (in place)");
         }
         const size_t tiles = (n + kCompactTile - 1) / kCompactTile;
-        const int g = grid_for(k_f64_compact, kCompactBlock, tiles * kCompactBlock);
-        k_f64_compact<<<g, kCompactBlock, 0, s>>>(u, z, n);
+        const int g = grid_for(k_f64_compact<false>, kCompactBlock, tiles * kCompactBlock);
+        k_f64_compact<false><<<g, kCompactBlock, 0, s>>>(u, z, n);
         return check_launch("f64 compact");
     }
+    case QM_VAR_T2_MULTI: {
+        if (u == z) {
+            // the queue re-reads the input after the in-place stores
+            return launch_map(u, z, n, F64T2Multi(), s, "f64 t2 multi (in place)");
+        }
+        const size_t tiles = (n + kCompactTile - 1) / kCompactTile;
+        const int g = grid_for(k_f64_compact<true>, kCompactBlock, tiles * kCompactBlock);
+        k_f64_compact<true><<<g, kCompactBlock, 0, s>>>(u, z, n);
+        return check_launch("f64 t2 multi");
+    }
+    case QM_VAR_ALMOST_NORMAL: return launch_map(u, z, n, F64AlmostNormal(), s, "f64 almost-normal");
     default: return fail(QM_ERR_INVALID, "qm_normal_quantile_f64: variant %d not available in FP64", variant);
     }
 }

@@ -19,10 +19,11 @@ pytestmark = pytest.mark.gpu
 
 DEV = "cuda"
 F32_VARIANTS = {"default": qm.QM_VAR_DEFAULT, "sqrt_form": qm.QM_VAR_SQRT_FORM,
-                "table": qm.QM_VAR_TABLE}
+                "table": qm.QM_VAR_TABLE, "almost_normal": qm.QM_VAR_ALMOST_NORMAL}
 F64_VARIANTS = {"default": qm.QM_VAR_DEFAULT, "branchfree": qm.QM_VAR_BRANCHFREE,
                 "hybrid_vote": qm.QM_VAR_HYBRID_VOTE, "mixed_halley": qm.QM_VAR_MIXED_HALLEY,
-                "compact": qm.QM_VAR_COMPACT, "table": qm.QM_VAR_TABLE, "fixed": qm.QM_VAR_FIXED}
+                "compact": qm.QM_VAR_COMPACT, "table": qm.QM_VAR_TABLE, "fixed": qm.QM_VAR_FIXED,
+                "almost_normal": qm.QM_VAR_ALMOST_NORMAL, "t2_multi": qm.QM_VAR_T2_MULTI}
 
 
 def run_f32(u_host: np.ndarray, variant) -> np.ndarray:
@@ -114,7 +115,7 @@ def test_f32_random_float_bit_patterns(name):
 
 
 @pytest.mark.parametrize("variant", [qm.QM_VAR_DEFAULT, qm.QM_VAR_BRANCHFREE, qm.QM_VAR_SQRT_FORM,
-                                     qm.QM_VAR_TABLE])
+                                     qm.QM_VAR_TABLE, qm.QM_VAR_ALMOST_NORMAL])
 def test_f32_edges(variant):
     u = np.array([0.0, 1.0, 0.5, np.nan, -0.0, -1e-30, 1.0000001, np.inf, -np.inf,
                   1.4e-45, 1.17549435e-38, 1 - 2**-24, 0.5 - 2**-25, 0.5 + 2**-24,
@@ -200,7 +201,7 @@ def test_f64_deep_tail_and_edges():
     u = np.concatenate([np.ldexp(0.75, -e), np.ldexp(0.5000001, -e)[:1070],
                         [0.0, 1.0, 0.5, np.nan, -1e-300, 1.0 + 2**-52, np.inf, 1 - 2**-53,
                          0.5 - 2**-54, 0.5 + 2**-53, 2.8748221264034482e-19,
-                         1.0373472162855378e-3, 1e-300]])
+                         1.0373472162855378e-3, 1e-300, 2.499998125001563e-07]])
     w = oracle.probit(u)
     for name, v in F64_VARIANTS.items():
         z = run_f64(u, v)
@@ -216,7 +217,8 @@ def test_f64_symmetry_bit_exact():
     k = rng.integers(1, 2**52, size=1 << 18, dtype=np.int64)
     u = k.astype(np.float64) * 2.0**-53
     v = (2**53 - k).astype(np.float64) * 2.0**-53
-    for name in ("branchfree", "compact", "hybrid_vote", "mixed_halley", "table", "fixed"):
+    for name in ("branchfree", "compact", "hybrid_vote", "mixed_halley", "table", "fixed",
+                 "almost_normal", "t2_multi"):
         a = run_f64(u, F64_VARIANTS[name])
         b = run_f64(v, F64_VARIANTS[name])
         assert np.array_equal(a, -b), name
@@ -247,6 +249,46 @@ def test_f64_fixed_every_segment():
     assert np.all(rel_err(z[sub], w[sub]) < 1e-12)
     dom = (u >= 1e-300) & (u <= 1 - 2.0**-53)
     print(f"fixed, every segment: max rel {rel_err(z, w)[dom].max():.3g}")
+
+
+def an_piece_edges():
+    """d at the piece boundaries of the almost-normal form (a = 8, w = 5.2,
+    9.2, 16; FP32: w = 5.2) and of the two-piece t_2 form (v = 15.5, 1000),
+    with neighbours a few ulp either side."""
+    a = np.array([8.0, 5.2**2, 9.2**2, 16.0**2])
+    r = np.sqrt(-np.expm1(-2 * a / np.pi))
+    d = np.exp(-2 * a / np.pi) / (2 * (1 + r))
+    d = np.concatenate([d, [1.0373472162855378e-3, 2.499998125001563e-07]])
+    k = np.arange(-4, 5)
+    return (d[:, None] * (1 + k[None, :] * 2.0**-52)).ravel()
+
+
+def test_piece_boundaries():
+    d = an_piece_edges()
+    u = np.concatenate([d, 1 - d])
+    w = oracle.probit(u)
+    for name in ("almost_normal", "t2_multi", "compact", "fixed"):
+        z = run_f64(u, F64_VARIANTS[name])
+        bad = f64_violations(z, w, 4e-15, u=u)
+        assert not bad.any(), (name, u[bad][:5], z[bad][:5], w[bad][:5])
+    u32 = np.concatenate([d, 1 - d]).astype(np.float32)
+    w32 = oracle.probit(u32.astype(np.float64))
+    z32 = run_f32(u32, qm.QM_VAR_ALMOST_NORMAL)
+    assert not f32_violations(z32, w32).any(), max_ulp(z32, w32)
+
+
+def test_f64_uniform_grid_filter_variants():
+    """53-bit uniforms u = k 2^-53 only (no tail stress): the near tail of
+    the two-piece t_2 form is reached by about 0.2% of the elements."""
+    rng = np.random.default_rng(21)
+    k = rng.integers(1, 2**53, size=1 << 21, dtype=np.int64)
+    u = k.astype(np.float64) * 2.0**-53
+    w = oracle.probit(u)
+    for name in ("almost_normal", "t2_multi"):
+        z = run_f64(u, F64_VARIANTS[name])
+        bad = f64_violations(z, w, 4e-15, u=u)
+        print(f"{name}, uniform grid: max rel {rel_err(z, w).max():.3g}")
+        assert not bad.any(), (name, u[bad][:5], z[bad][:5], w[bad][:5])
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 1023, 1025, 65537])
