@@ -86,12 +86,12 @@ typedef enum {
                                 same path.  The FP64 default.                   */
     QM_VAR_ALMOST_NORMAL = 9, /* FP32 and FP64: the almost-normal /
                                 almost-chi-squared filtering coordinates
-                                (Sec. 5.3): a = -(pi/2) log(4 d (1-d));
+                                (Sec. 4.4): a = -(pi/2) log(4 d (1-d));
                                 a <= 8: |z| = (1 - 2d) P(a); a > 8: |z| = T(sqrt a)
                                 on pieces of the sqrt(a) axis; polynomials
                                 only (no divide).  FP64: one Horner loop over a
                                 per-lane coefficient row (no branch).           */
-    QM_VAR_T2_MULTI = 10     /* FP64: the hybrid with more branches (Sec. 7.5):
+    QM_VAR_T2_MULTI = 10     /* FP64: the hybrid with more branches (Sec. 7.4):
                                 t_2 coordinate for v <= 1000 (the Sec. 7.3
                                 rational on v <= 15.5, a second (14,15) t_2
                                 rational on the near tail 15.5 < v <= 1000,

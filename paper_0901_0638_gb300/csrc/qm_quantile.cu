@@ -103,7 +103,7 @@ struct F64Mixed {
 struct F64Libm { __device__ double operator()(double u) const { return normcdfinv(u); } };
 
 // ---------------------------------------------------------------------------
-// Almost-normal / almost-chi-squared filtering coordinates (Sec. 5.3):
+// Almost-normal / almost-chi-squared filtering coordinates (Sec. 4.4):
 //     a = -(pi/2) log(4 d (1 - d)) = Q_AN(u)^2,  w = sqrt(a) = |Q_AN(u)|,
 //     a <= 8: |z| = (1 - 2d) P(a - a_c);   a > 8: |z| = T_k(w - w_c).
 // 4 d (1 - d) = (2d)(2 - 2d): 2d is exact, 2 - 2d rounds once.
@@ -177,7 +177,7 @@ struct F32AlmostNormal {
 };
 
 // ---------------------------------------------------------------------------
-// t_2 coordinate with more branches (Sec. 7.5): the Sec. 7.3 rational on
+// t_2 coordinate with more branches (Sec. 7.4): the Sec. 7.3 rational on
 // v <= 15.5 and a second (14,15) rational on the near tail 15.5 < v <= 1000,
 // one evaluation with the coefficients selected per lane.
 // ---------------------------------------------------------------------------
@@ -417,7 +417,7 @@ __device__ __forceinline__ void queue_push(bool pred, int* counter, unsigned sho
     if (pred) q[base + __popc(mask & ((1u << lane) - 1u))] = idx;
 }
 
-// MULTI: the in-place branch is the two-piece t_2 form on v <= 1000 (Sec. 7.5)
+// MULTI: the in-place branch is the two-piece t_2 form on v <= 1000 (Sec. 7.4)
 // instead of the Sec. 7.3 rational on v <= 15.5.
 template <bool MULTI>
 __global__ void __launch_bounds__(kCompactBlock)

@@ -1,8 +1,8 @@
 """Generate csrc/qm_filter_coeffs.h: the normal quantile through the other
-filtering distributions of Sec. 5.3, and the near-tail t_2 piece of the
-multi-branch hybrid (Sec. 7.5).
+filtering distributions of Sec. 4.4, and the near-tail t_2 piece of the
+multi-branch hybrid (Sec. 7.4).
 
-Almost-normal / almost-chi-squared coordinates (Sec. 5.3).  With
+Almost-normal / almost-chi-squared coordinates (Sec. 4.4).  With
 d = min(u, 1-u) and r = |2u - 1| = 1 - 2d, the almost-chi-squared variate
 (the square of the almost-normal one) is
 
@@ -21,7 +21,7 @@ w - w_c, minimax in relative error (rational.remez with denominator degree
 0).  FP64: degree 20 on every piece (the kernel evaluates all pieces with one
 Horner loop over a per-lane coefficient row); FP32: degree 9.
 
-Near-tail t_2 piece (Sec. 7.5): Psi(v)/v on v in [15.5, 1000] (v the scaled
+Near-tail t_2 piece (Sec. 7.4): Psi(v)/v on v in [15.5, 1000] (v the scaled
 t_2 coordinate), degree (14,15) -- the same form as the Sec. 7.3 centre
 rational, so that the two share one evaluation with per-lane coefficients.
 

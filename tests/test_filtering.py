@@ -1,5 +1,5 @@
-"""The other filtering distributions of Sec. 5.3 and the near-tail t_2 piece
-of Sec. 7.5, on the CPU.
+"""The other filtering distributions of Sec. 4.4 and the near-tail t_2 piece
+of Sec. 7.4, on the CPU.
 
 * The almost-normal law as the paper defines it (density, distribution and
   closed-form quantile) is checked against itself the way the paper's
