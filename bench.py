@@ -493,21 +493,28 @@ def main():
                                       "hbm_frac": 8 * n / (t * 1e-3) / 1e9 / 6780.7}
         del u32, z32
         z = torch.empty_like(u)
-        # end to end through the C ABI with host buffers (pinned), copies timed:
-        # chunks of 2^24 elements pipelined over two streams, so the
-        # host->device copy of one chunk, the kernel on another and the
-        # device->host copy of a third overlap
+        # end to end through the C ABI with host buffers (pinned): the kernel
+        # reads u from and writes z to page-locked host memory over the host
+        # link (unified addressing: the pinned pointer is a device pointer), so
+        # every step moves its 2^28 inputs host -> device and its 2^28 results
+        # device -> host inside the timed region, in one launch.  Beside it, a
+        # copy-engine pipeline (2^24-element chunks over four streams: copy
+        # in, kernel, copy out) on the same buffers.
         hu = u.cpu().pin_memory()
         hz = torch.empty_like(hu).pin_memory()
-        chunk = min(n, 1 << 24)
-        streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
 
         def e2e_step():
+            qm.qm_normal_quantile_f64(hu, hz, var, stream=stream)
+
+        chunk = min(n, 1 << 24)
+        streams = [torch.cuda.Stream(dev) for _ in range(4)]
+
+        def pipe_step():
             cur = torch.cuda.current_stream(dev)
             for st in streams:
                 st.wait_stream(cur)
-            for c0 in range(0, n, chunk):
-                st = streams[(c0 // chunk) % 2]
+            for i, c0 in enumerate(range(0, n, chunk)):
+                st = streams[i % len(streams)]
                 with torch.cuda.stream(st):
                     sl = slice(c0, min(n, c0 + chunk))
                     u[sl].copy_(hu[sl], non_blocking=True)
@@ -516,22 +523,33 @@ def main():
             for st in streams:
                 cur.wait_stream(st)
 
-        for _ in range(2):
-            e2e_step()
+        def time_host(step):
+            for _ in range(2):
+                step()
+            torch.cuda.synchronize(dev)
+            ev_a.record(stream)
+            k2 = max(1, min(args.steps, 5))
+            for _ in range(k2):
+                step()
+            ev_b.record(stream)
+            torch.cuda.synchronize(dev)
+            return ev_a.elapsed_time(ev_b) / k2
+
+        t_pipe = time_host(pipe_step)
+        hz.zero_()
+        t = time_host(e2e_step)
+        idx = torch.arange(0, n, 4099)
+        qm.qm_normal_quantile_f64(u, z, var, stream=stream)
         torch.cuda.synchronize(dev)
-        ev_a.record(stream)
-        k2 = max(1, min(args.steps, 5))
-        for _ in range(k2):
-            e2e_step()
-        ev_b.record(stream)
-        torch.cuda.synchronize(dev)
-        t = ev_a.elapsed_time(ev_b) / k2
-        assert torch.equal(hz[:1024], z[:1024].cpu())
+        assert torch.equal(hz[idx], z[idx.to(dev)].cpu())
         e2e = {"value": n / (t * 1e-3) / 1e9, "unit": "Gsamples/s",
                "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n, "ms_per_step": t,
-               "note": "pinned host buffers; per 2^24-element chunk: copy in, kernel, copy out, "
-                       "chunks alternating over two streams",
-               "gpu_launches_per_step": (n + chunk - 1) // chunk}
+               "note": "pinned host buffers passed to qm_normal_quantile_f64: the kernel streams u from "
+                       "and z to host memory over the host link (zero-copy), one launch per step",
+               "gpu_launches_per_step": 1,
+               "copy_engine_pipeline": {"ms_per_step": t_pipe, "value": n / (t_pipe * 1e-3) / 1e9,
+                                        "note": "2^24-element chunks over four streams: copy in, "
+                                                "kernel, copy out"}}
         del hu, hz
         cpu = cpu_oracle_leg(n)
 

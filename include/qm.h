@@ -105,10 +105,14 @@ typedef struct {
 
 /* ---- normal quantile ------------------------------------------------------
  * z[i] = Phi^{-1}(u[i]) for i < n (Sec. 1, Eq. 1).  FP32 variants: DEFAULT,
- * BRANCHFREE, SQRT_FORM, TABLE, CUDA_LIBM; FP64 variants: DEFAULT, BRANCHFREE,
- * HYBRID_VOTE, MIXED_HALLEY, COMPACT, TABLE, FIXED, CUDA_LIBM (others:
- * QM_ERR_INVALID).
- * u, z: contiguous arrays of n elements (device).                           */
+ * BRANCHFREE, SQRT_FORM, TABLE, ALMOST_NORMAL, CUDA_LIBM; FP64 variants:
+ * DEFAULT, BRANCHFREE, HYBRID_VOTE, MIXED_HALLEY, COMPACT, TABLE, FIXED,
+ * ALMOST_NORMAL, T2_MULTI, CUDA_LIBM (others: QM_ERR_INVALID).
+ * u, z: contiguous arrays of n elements, in device memory or in page-locked
+ * host memory (cudaHostAlloc / cudaHostRegister; with unified addressing its
+ * pointer is a device pointer): the kernel then streams the data over the
+ * host link itself, with no staging copy.  Pageable host memory is not
+ * accepted (the kernel cannot address it).                                  */
 qm_status qm_normal_quantile_f32(const float* u, float* z, size_t n,
                                  int variant, void* stream);
 qm_status qm_normal_quantile_f64(const double* u, double* z, size_t n,

@@ -155,7 +155,7 @@ def _ptr(t):
 def _stream(stream, t=None):
     if stream is None:
         import torch
-        dev = t.device if (t is not None and hasattr(t, "device")) else None
+        dev = t.device if (t is not None and getattr(getattr(t, "device", None), "type", "") == "cuda") else None
         return torch.cuda.current_stream(dev).cuda_stream
     if isinstance(stream, int):
         return stream

@@ -327,6 +327,24 @@ def test_f64_full_size_sampled():
     torch.cuda.empty_cache()
 
 
+def test_pinned_host_buffers():
+    """Page-locked host arrays go straight to the kernels (zero-copy over the
+    host link): same bits as the device path."""
+    u = W.mixture_f64(2, (1 << 20) + 3)
+    hu = u.pin_memory()
+    hz = torch.empty_like(hu).pin_memory()
+    qm.qm_normal_quantile_f64(hu, hz, qm.QM_VAR_DEFAULT)
+    z = run_f64(u.numpy(), qm.QM_VAR_DEFAULT)
+    torch.cuda.synchronize()
+    assert np.array_equal(hz.numpy(), z, equal_nan=True)
+    _, u32 = W.uniform24(1, (1 << 20) + 1)
+    hu32 = u32.pin_memory()
+    hz32 = torch.empty_like(hu32).pin_memory()
+    qm.qm_normal_quantile_f32(hu32, hz32, qm.QM_VAR_DEFAULT)
+    torch.cuda.synchronize()
+    assert np.array_equal(hz32.numpy(), run_f32(u32.numpy(), qm.QM_VAR_DEFAULT), equal_nan=True)
+
+
 def test_f32_beyond_2_pow_31_elements():
     """Index arithmetic past 2^31 elements (8 GiB per array), sampled."""
     n = (1 << 31) + 5
