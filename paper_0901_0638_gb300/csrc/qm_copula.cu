@@ -38,11 +38,11 @@ struct CopulaDev {
 
 // normal from two Philox words (53-bit integer, exact reflected grid point,
 // the fixed-point FP64 evaluation)
-__device__ __forceinline__ double normal_from_words(const fxt::SegFx* fxT, uint32_t hi, uint32_t lo)
+__device__ __forceinline__ double normal_from_words(const fxt::FxTable* fxT, uint32_t hi, uint32_t lo)
 {
     const uint64_t k = ((uint64_t)(hi >> 11) << 32) | lo;
     bool upper;
-    const double m = probit_grid53_fx(fxT, k, upper);
+    const double m = probit_grid53_fx<FX_FP64_LEAN>(fxT, k, upper);
     return upper ? m : -m;
 }
 
@@ -51,7 +51,7 @@ __device__ __forceinline__ double normal_from_words(const fxt::SegFx* fxT, uint3
 template <int D>
 __global__ void __launch_bounds__(128)
 k_copula(const CopulaDev* __restrict__ cp, PhiloxKeys K, uint64_t blk0, double* out, size_t n,
-         const fxt::SegFx* fxT)
+         const fxt::FxTable* fxT)
 {
     __shared__ CopulaDev c;
     {
@@ -93,7 +93,7 @@ template <int D>
 qm_status launch_d(const CopulaDev* dev, PhiloxKeys K, uint64_t blk0, double* out, size_t n, cudaStream_t s)
 {
     qm_status fst;
-    const fxt::SegFx* fxT = (const fxt::SegFx*)fx_table_device(&fst);
+    const fxt::FxTable* fxT = (const fxt::FxTable*)fx_table_device(&fst);
     if (!fxT) return fst;
     int bps = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_copula<D>, 128, 0);

@@ -41,9 +41,9 @@ k_f64_fixed(const double* __restrict__ in, double* out, size_t n)
 #pragma unroll
         for (int k = 0; k < U; ++k)
             if (i + k * stride < nv)
-                __stcs(vout + i + k * stride, make_double2(probit_fx(fxt::SEG_FX, a[k].x), probit_fx(fxt::SEG_FX, a[k].y)));
+                __stcs(vout + i + k * stride, make_double2(probit_fx(&fxt::SEG_FX, a[k].x), probit_fx(&fxt::SEG_FX, a[k].y)));
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) out[n - 1] = probit_fx(fxt::SEG_FX, in[n - 1]);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) out[n - 1] = probit_fx(&fxt::SEG_FX, in[n - 1]);
 }
 
 __global__ void __launch_bounds__(kBlock)
@@ -51,7 +51,7 @@ k_f64_fixed_scalar(const double* in, double* out, size_t n)
 {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-        out[i] = probit_fx(fxt::SEG_FX, in[i]);
+        out[i] = probit_fx(&fxt::SEG_FX, in[i]);
 }
 
 template <class Kern>

@@ -15,9 +15,14 @@
 //     F   = beta_3 + tau (beta_4 + tau (beta_5 + tau beta_6))   (single precision)
 //
 // The Horner steps for beta_0..beta_2 run on signed 64-bit accumulators times
-// tau as an unsigned Q0.64 integer (unsigned mulhi plus a sign correction),
-// the normalisation of x is integer arithmetic, and t_u and H become doubles
-// by bit assembly, so the only FP64 instruction is the final FMA.
+// tau as an unsigned Q0.64 integer (unsigned mulhi plus a sign correction);
+// beta_3..beta_6 are stored pre-scaled to the accumulator's units, so the
+// single-precision chain F enters as one float -> int64 conversion.  The
+// normalisation of x is integer arithmetic, H becomes a double by bit
+// assembly and t_u exactly (two instruction mixes, below), and the final FMA
+// is the one FP64 operation of the method.  A segment is 48 bytes in two
+// arrays (one 256-bit and one 128-bit gather per element; the denser arrays
+// also put more segments in a cache line).
 #pragma once
 #include <stdint.h>
 
@@ -31,14 +36,21 @@ constexpr int E_LAST = 1072;
 constexpr int N_MAIN = 4096;
 constexpr int N_ALL = 36384;
 
-struct alignas(64) SegFx {
+// a0, B0 = beta_0 2^-s0, B1 = beta_1 2^-s0, and B2 = beta_2 2^-s0 in the low
+// 52 bits (sign extended) with s0 in the top 12
+struct alignas(32) SegA {
     double a0;
-    long long B0, B1, B2;
+    long long B0, B1, B2s;
+};
+
+// f_k = beta_k 2^-s0, k = 3..6, rounded to single precision
+struct alignas(16) SegF {
     float f3, f4, f5, f6;
-    int s0;
-    float csc;
-    int sh;
-    int pad;
+};
+
+struct FxTable {
+    SegA a[N_ALL];
+    SegF f[N_ALL];
 };
 
 }  // namespace fxt
@@ -51,6 +63,47 @@ __device__ __forceinline__ void ld256(const void* p, unsigned long long& a, unsi
         : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
 }
 
+// 16 bytes from the read-only path in one 128-bit load
+__device__ __forceinline__ float4 ld128f(const void* p)
+{
+    float4 v;
+    asm("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+    return v;
+}
+
+// float -> int64 rounded to nearest even, by integer operations: the same
+// value as __float2ll_rn for |F| < 2^62 (the hardware conversion to 64 bits
+// issues on the FP64 pipe).
+__device__ __forceinline__ long long f32_to_i64_rn_alu(float F)
+{
+    const unsigned b = __float_as_uint(F);
+    const int ex = (int)((b >> 23) & 0xFFu);
+    const unsigned m = (b & 0x7FFFFFu) | 0x800000u;          // (zero: rounds to 0 below)
+    unsigned long long mag;
+    if (ex >= 150) {
+        mag = (unsigned long long)m << (ex - 150);             // already an integer
+    } else {
+        const int r = min(150 - ex, 25);                       // 1 .. 25
+        const unsigned q = m >> r;
+        const unsigned rem = m & ((1u << r) - 1u);
+        const unsigned half = 1u << (r - 1);
+        mag = q + (unsigned)((rem > half) | ((rem == half) & ((q & 1u) != 0u)));
+    }
+    return (b >> 31) ? -(long long)mag : (long long)mag;
+}
+
+// Instruction mixes with bit-identical results, chosen per kernel by what
+// bounds it (two steps can run on the FP64 pipe or as integer operations):
+//   FX_CVT_HW  -- the float -> int64 conversion by the hardware instruction
+//                 (one FP64-pipe slot) instead of f32_to_i64_rn_alu;
+//   FX_TU_FADD -- t_u as (1 + t_u) - 1, one exact FP64 add, instead of
+//                 normalising Tu with integer operations.
+//   FX_INT_LEAN  = both (the streaming kernel, bound by the integer pipe and
+//                  the L1: three FP64-pipe instructions per element);
+//   FX_FP64_LEAN = neither (kernels bound by the FP64 pipe: the final FMA is
+//                  the only FP64 instruction).
+enum { FX_CVT_HW = 1, FX_TU_FADD = 2, FX_INT_LEAN = 3, FX_FP64_LEAN = 0 };
+
 // floor(a b / 2^64) for signed a and unsigned b
 __device__ __forceinline__ long long mulhi_su(long long a, unsigned long long b)
 {
@@ -60,7 +113,8 @@ __device__ __forceinline__ long long mulhi_su(long long a, unsigned long long b)
 
 // |Phi^{-1}| bits for x = 2d = S 2^(base - 52), 0 < S < 2^53 (any position of
 // the leading bit), from the table T (x = 1, i.e. d = 1/2, gives +0).
-__device__ __forceinline__ unsigned long long probit_mag_fx_sx(const fxt::SegFx* T, unsigned long long S,
+template <int MIX = FX_INT_LEAN>
+__device__ __forceinline__ unsigned long long probit_mag_fx_sx(const fxt::FxTable* T, unsigned long long S,
                                                              int base)
 {
     const int lz = __clzll(S | 1ull) - 11;
@@ -77,20 +131,20 @@ __device__ __forceinline__ unsigned long long probit_mag_fx_sx(const fxt::SegFx*
     const unsigned long long Tu = (1ull << sK) - (Mx & ((1ull << sK) - 1ull));
     const unsigned long long Tau = (Tu << (12 + K)) - (Tu >> sK);   // tau 2^64 (tau = 1 -> 1 - 2^-64)
 
-    const fxt::SegFx* p = T + idx;
-    unsigned long long a0b, B0, B1, B2, f34, f56, s0c, shp;
-    ld256(p, a0b, B0, B1, B2);                                     // a0, B0, B1, B2
-    ld256(reinterpret_cast<const char*>(p) + 32, f34, f56, s0c, shp);   // beta_3..6, s0, 2^c, sh
+    unsigned long long a0b, B0, B1, B2s;
+    ld256(&T->a[idx], a0b, B0, B1, B2s);                           // a0, B0, B1, B2 | s0
+    const float4 f = ld128f(&T->f[idx]);                            // f3..f6
+    const long long B2 = (long long)(B2s << 12) >> 12;
+    const int s0 = (int)((long long)B2s >> 52);
 
     // single-precision tail from the top bits of the offset
     const float tf = __uint_as_float(0x4B000000u | (unsigned)(Tu >> 25)) - 8388608.0f;
     const float tau_f = tf * __uint_as_float((unsigned)(127 + K - 27) << 23);
-    float F = __fmaf_rn(__uint_as_float((unsigned)(f56 >> 32)), tau_f, __uint_as_float((unsigned)f56));
-    F = __fmaf_rn(F, tau_f, __uint_as_float((unsigned)(f34 >> 32)));
-    F = __fmaf_rn(F, tau_f, __uint_as_float((unsigned)f34));
-    const int i3 = __float2int_rn(F * __uint_as_float((unsigned)(s0c >> 32)));
-    long long acc = (long long)((unsigned long long)(long long)i3 << (unsigned)shp);
-    acc = (long long)B2 + mulhi_su(acc, Tau);
+    float F = __fmaf_rn(f.w, tau_f, f.z);
+    F = __fmaf_rn(F, tau_f, f.y);
+    F = __fmaf_rn(F, tau_f, f.x);
+    long long acc = (MIX & FX_CVT_HW) ? __float2ll_rn(F) : f32_to_i64_rn_alu(F);
+    acc = B2 + mulhi_su(acc, Tau);
     acc = (long long)B1 + mulhi_su(acc, Tau);
     acc = (long long)B0 + mulhi_su(acc, Tau);                     // H 2^-s0, in (0, 2^62)
 
@@ -98,12 +152,18 @@ __device__ __forceinline__ unsigned long long probit_mag_fx_sx(const fxt::SegFx*
     const unsigned long long ha = (unsigned long long)acc;
     const int lh = __clzll(ha);
     const unsigned long long hm = ((ha << lh) + 0x400ull) >> 11;
-    const unsigned long long hbits = hm + ((unsigned long long)(1022 + 63 - lh + (int)(unsigned)s0c) << 52);
-    // t_u as a double (exact: 1 <= Tu <= 2^47)
-    const int lt = __clzll(Tu);
-    const unsigned long long tbits = (Tu << (lt - 11)) + ((unsigned long long)(1033 - lt) << 52);
-    const double g = __fma_rn(__longlong_as_double((long long)tbits),
-                              __longlong_as_double((long long)hbits), __longlong_as_double((long long)a0b));
+    const unsigned long long hbits = hm + ((unsigned long long)(1022 + 63 - lh + s0) << 52);
+    // t_u as a double (exact, 1 <= Tu <= 2^47): 1 + t_u has the bits
+    // 0x3FF0... + Tu and taking 1 away again is exact (Sterbenz); or by
+    // normalising Tu and inserting the exponent
+    double tu;
+    if (MIX & FX_TU_FADD) {
+        tu = __dadd_rn(__longlong_as_double((long long)(0x3FF0000000000000ull + Tu)), -1.0);
+    } else {
+        const int lt = __clzll(Tu);
+        tu = __longlong_as_double((long long)((Tu << (lt - 11)) + ((unsigned long long)(1033 - lt) << 52)));
+    }
+    const double g = __fma_rn(tu, __longlong_as_double((long long)hbits), __longlong_as_double((long long)a0b));
     return (e < 0) ? 0ull : (unsigned long long)__double_as_longlong(g);
 }
 
@@ -112,36 +172,39 @@ __device__ __forceinline__ unsigned long long probit_mag_fx_sx(const fxt::SegFx*
 // table index is in range for every bit pattern).  x = 2d = S 2^(base - 52):
 // u >= 1/2 -> S = 2^52 - frac (1 - u exact), u < 1/2 -> S = significand of u
 // (no implicit bit when subnormal).
-__device__ __forceinline__ unsigned long long probit_mag_fx(const fxt::SegFx* T, unsigned long long ub)
+template <int MIX = FX_INT_LEAN>
+__device__ __forceinline__ unsigned long long probit_mag_fx(const fxt::FxTable* T, unsigned long long ub)
 {
     const bool upper = ub >= 0x3FE0000000000000ull;
     const unsigned long long frac = ub & 0x000FFFFFFFFFFFFFull;
     const int eb = (int)(ub >> 52) & 0x7ff;
     const unsigned long long S = upper ? (1ull << 52) - frac : (eb ? (frac | (1ull << 52)) : frac);
     const int base = upper ? 0 : max(eb, 1) - 1022;
-    return probit_mag_fx_sx(T, S, base);
+    return probit_mag_fx_sx<MIX>(T, S, base);
 }
 
 // |Phi^{-1}((k + 1/2) 2^-53)| for a 53-bit integer k on its exact reflected
 // grid point d = (min(k, 2^53-1-k) + 1/2) 2^-53: x = 2d = (2j+1) 2^-53;
 // upper = (k >= 2^52), the sign of z.
-__device__ __forceinline__ double probit_grid53_fx(const fxt::SegFx* T, unsigned long long k, bool& upper)
+template <int MIX = FX_INT_LEAN>
+__device__ __forceinline__ double probit_grid53_fx(const fxt::FxTable* T, unsigned long long k, bool& upper)
 {
     upper = k >= (1ull << 52);
     const unsigned long long j = upper ? ((1ull << 53) - 1 - k) : k;
-    return __longlong_as_double((long long)probit_mag_fx_sx(T, 2 * j + 1, -1));
+    return __longlong_as_double((long long)probit_mag_fx_sx<MIX>(T, 2 * j + 1, -1));
 }
 
 // Phi^{-1}(u) with the IEEE edge values: u = 1/2 -> +0, u = 0 -> -inf,
 // u = 1 -> +inf, NaN or u outside [0, 1] -> NaN.
-__device__ __forceinline__ double probit_fx(const fxt::SegFx* T, double u)
+template <int MIX = FX_INT_LEAN>
+__device__ __forceinline__ double probit_fx(const fxt::FxTable* T, double u)
 {
     const unsigned long long ub = (unsigned long long)__double_as_longlong(u);
     const unsigned hi = (unsigned)(ub >> 32);
-    const unsigned long long mb = probit_mag_fx(T, ub);
+    const unsigned long long mb = probit_mag_fx<MIX>(T, ub);
     const bool valid = hi < 0x3FF00000u && ub != 0ull;                    // 0 < u < 1
     const unsigned sgn = hi < 0x3FE00000u ? 0x80000000u : 0u;              // u < 1/2
-    const unsigned sp = ((ub << 1) == 0ull) ? 0xfff00000u                  // +-0 -> -inf
+    const unsigned sp = (((hi & 0x7fffffffu) | (unsigned)ub) == 0u) ? 0xfff00000u   // +-0 -> -inf
                       : (ub == 0x3FF0000000000000ull ? 0x7ff00000u         // 1 -> +inf
                                                      : 0x7ff80000u);       // NaN
     const unsigned rhi = valid ? ((unsigned)(mb >> 32) | sgn) : sp;

@@ -684,7 +684,7 @@ k_fused_normal_f32(PhiloxKeys K, uint64_t blk0, size_t n, float* out, double* pa
 template <int KIND, bool OUT, bool MOM>
 __global__ void __launch_bounds__(256)
 k_fused_f64(PhiloxKeys K, uint64_t blk0, size_t n, double* out, double* partials, TSel tk,
-            const fxt::SegFx* fxT)
+            const fxt::FxTable* fxT)
 {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     const size_t nblk = (n + 1) / 2;
@@ -701,7 +701,8 @@ k_fused_f64(PhiloxKeys K, uint64_t blk0, size_t n, double* out, double* partials
             bool upper;
             const uint32_t hi = h ? w.z : w.x, lo = h ? w.w : w.y;
             const unsigned long long kk = ((unsigned long long)(hi >> 11) << 32) | lo;
-            const double zn = probit_grid53_fx(fxT, kk, upper);   // |Phi^{-1}((k + 1/2) 2^-53)|
+            // |Phi^{-1}((k + 1/2) 2^-53)|; the Student-t map makes KIND 1 FP64 bound
+            const double zn = probit_grid53_fx<KIND == 1 ? FX_FP64_LEAN : FX_TU_FADD>(fxT, kk, upper);
             if (KIND == 0) {
                 z[h] = upper ? zn : -zn;
             } else if (KIND == 1) {
@@ -928,7 +929,7 @@ extern "C" qm_status qm_sample_fused(int target, const qm_params* p, uint64_t ke
         const uint64_t b0 = ctr0 / 4;
         const PhiloxKeys key = philox_keys(key_in);
         qm_status fst;
-        const fxt::SegFx* fxT = (const fxt::SegFx*)fx_table_device(&fst);
+        const fxt::FxTable* fxT = (const fxt::FxTable*)fx_table_device(&fst);
         if (!fxT) return fst;
 #define QM_LAUNCH_F64(KIND)                                                                        \
     if (o && part) k_fused_f64<KIND, true, true><<<g, B, 0, s>>>(key, b0, n, o, part, tk, fxT);   \

@@ -41,7 +41,7 @@ struct DevSeg {
 
 template <int EPT, bool ESTRIN>
 __global__ void __launch_bounds__(512)
-k_batch(const DevSeg* __restrict__ segs, int nseg, unsigned long long ntiles, const fxt::SegFx* fxT)
+k_batch(const DevSeg* __restrict__ segs, int nseg, unsigned long long ntiles, const fxt::FxTable* fxT)
 {
     for (unsigned long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         int lo = 0, hi = nseg - 1;
@@ -63,7 +63,7 @@ k_batch(const DevSeg* __restrict__ segs, int nseg, unsigned long long ntiles, co
             double y;
             if (sg.kind == KIND_T) y = recycle_t_sel<ESTRIN>(sg.t, x[k]);
             else if (sg.kind == KIND_EXP) y = exp_to_normal_tbl(x[k]);
-            else y = probit_fx(fxT, x[k]);
+            else y = probit_fx<FX_FP64_LEAN>(fxT, x[k]);
             if (i < sg.n) __stcs(sg.out + i, y);
         }
     }
@@ -71,7 +71,7 @@ k_batch(const DevSeg* __restrict__ segs, int nseg, unsigned long long ntiles, co
 
 // One plain launch per segment (the comparison baseline for the batch).
 __global__ void __launch_bounds__(256)
-k_single(const double* __restrict__ in, double* out, size_t n, int kind, TSel t, const fxt::SegFx* fxT)
+k_single(const double* __restrict__ in, double* out, size_t n, int kind, TSel t, const fxt::FxTable* fxT)
 {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -79,12 +79,12 @@ k_single(const double* __restrict__ in, double* out, size_t n, int kind, TSel t,
         double y;
         if (kind == KIND_T) y = recycle_t_sel<false>(t, x);
         else if (kind == KIND_EXP) y = exp_to_normal_tbl(x);
-        else y = probit_fx(fxT, x);
+        else y = probit_fx<FX_FP64_LEAN>(fxT, x);
         __stcs(out + i, y);
     }
 }
 
-using BatchKernel = void (*)(const DevSeg*, int, unsigned long long, const fxt::SegFx*);
+using BatchKernel = void (*)(const DevSeg*, int, unsigned long long, const fxt::FxTable*);
 
 static BatchKernel pick_kernel(int ept, int estrin)
 {
@@ -302,7 +302,7 @@ extern "C" qm_status qm_batch_run(qm_batch* b, void* stream)
     if (!b->exec) {
         BatchKernel k = pick_kernel(b->tuning.ept, b->tuning.estrin);
         qm_status fst;
-        const fxt::SegFx* fxT = (const fxt::SegFx*)fx_table_device(&fst);
+        const fxt::FxTable* fxT = (const fxt::FxTable*)fx_table_device(&fst);
         if (!fxT) return fst;
         if (cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             return fail(QM_ERR_CUDA, "qm_batch_run: stream capture failed to start");
@@ -325,7 +325,7 @@ extern "C" qm_status qm_batch_run_separate(qm_batch* b, void* stream)
     if (!b) return fail(QM_ERR_INVALID, "qm_batch_run_separate: null batch");
     const int sms = sm_count() > 0 ? sm_count() : 1;
     qm_status fst;
-    const fxt::SegFx* fxT = (const fxt::SegFx*)fx_table_device(&fst);
+    const fxt::FxTable* fxT = (const fxt::FxTable*)fx_table_device(&fst);
     if (!fxT) return fst;
     for (const DevSeg& s : b->host) {
         if (!s.n) continue;

@@ -64,12 +64,12 @@ __device__ __forceinline__ void serve_f32(const ReqDev& r, unsigned long long pb
     }
 }
 
-__device__ __forceinline__ double serve_f64_one(const fxt::SegFx* fxT, int kind, const TSel& t, uint32_t hi,
+__device__ __forceinline__ double serve_f64_one(const fxt::FxTable* fxT, int kind, const TSel& t, uint32_t hi,
                                                 uint32_t lo)
 {
     const uint64_t k = ((uint64_t)(hi >> 11) << 32) | lo;
     bool upper;
-    const double m = probit_grid53_fx(fxT, k, upper);      // |Phi^{-1}((k + 1/2) 2^-53)|
+    const double m = probit_grid53_fx<FX_FP64_LEAN>(fxT, k, upper);      // |Phi^{-1}((k + 1/2) 2^-53)|
     if (kind == 3) {
         // Exp(1) sample x = -log(u), u = (k + 1/2) 2^-53, recycled to the
         // normal by Q(x) = Phi^{-1}(1 - e^{-x}) = Phi^{-1}(1 - u) (Sec. 6): the
@@ -83,7 +83,7 @@ __device__ __forceinline__ double serve_f64_one(const fxt::SegFx* fxT, int kind,
 }
 
 __global__ void __launch_bounds__(kServeBlock)
-k_serve(const ReqDev* __restrict__ reqs, int nreq, unsigned long long ntiles, const fxt::SegFx* fxT)
+k_serve(const ReqDev* __restrict__ reqs, int nreq, unsigned long long ntiles, const fxt::FxTable* fxT)
 {
     for (unsigned long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         int lo = 0, hi = nreq - 1;
@@ -242,7 +242,7 @@ static void worker_loop(qm_server* s)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_serve, kServeBlock, 0);
     if (bps < 1) bps = 1;
     qm_status fst;
-    const fxt::SegFx* fxT = (const fxt::SegFx*)fx_table_device(&fst);   // looked up at create
+    const fxt::FxTable* fxT = (const fxt::FxTable*)fx_table_device(&fst);   // looked up at create
     std::vector<ReqDev> table;
     while (true) {
         bool idle = true;

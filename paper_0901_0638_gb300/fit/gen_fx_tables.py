@@ -23,16 +23,20 @@ error); |z| grows away from the end, so H > 0 on every segment:
 On GB300 the FP64 pipe issues about 1/62 of the FP32 rate, so beta_0..beta_2
 are applied by a fixed-point Horner chain on 64-bit integers with tau as an
 unsigned Q0.64 number (acc_k = B_k + mulhi(acc_{k+1}, tau 2^64), every acc in
-units of 2^s0), beta_3..beta_6 by a single-precision chain F entering as
-acc_3 = rn(F 2^c) << sh; then z = fma(t_u, acc_0 2^s0, a_0) is the only
-double-precision operation.
+units of 2^s0), beta_3..beta_6 by a single-precision chain F on the
+coefficients f_k = beta_k 2^-s0 (already in the accumulator's units), entering
+as acc_3 = rn(F) (float -> int64, round to nearest even); then
+z = fma(t_u, acc_0 2^s0, a_0), with t_u = (1 + t_u) - 1 formed exactly by one
+double-precision add.
 
 Binades: e = -1 - E in [0, 64) with K = 6, e in [64, 1072] with K = 5, so
 every double 0 < u < 1 (subnormal u included: x is normalised as an
 integer) falls in a segment.
 
-Entry (64 bytes, two 32-byte halves): a0 (double), B0, B1, B2 (int64) |
-beta_3..beta_6 (float), s0, 2^c (float), sh, pad.
+Entry: two arrays, so that a lane gathers 48 bytes with one 256-bit and one
+128-bit load: A[i] = {a0 (double), B0, B1 (int64), B2 | s0 << 52} (32 bytes;
+B2 in the low 52 bits, sign extended, s0 in the top 12) and
+F[i] = {f3, f4, f5, f6} (float, 16 bytes).
 
 The generator checks every segment by emulating the kernel's integer and
 double-precision steps exactly (single-precision steps to within one
@@ -118,15 +122,11 @@ def quantise(e, j, K, g):
     hmax = sum(abs(x) for x in beta)                              # tau in [0, 1]
     s0 = int(mp.floor(mp.log(hmax, 2))) + 1 - 62                  # |acc| < 2^62
     B = [int(mp.nint(beta[k] / mp.mpf(2) ** s0)) for k in range(NI)]
-    bf = [f32(beta[k]) for k in range(NI, DEG)]
-    fmax = sum(abs(beta[k]) for k in range(NI, DEG))
-    c = 30 - int(mp.ceil(mp.log(fmax, 2)))                        # |F 2^c| <= 2^30
-    sh = -s0 - c
-    if sh < 0:
-        c += sh
-        sh = 0
-    assert 0 <= sh <= 62 and -120 < c < 120, (e, j, c, sh)
-    return {"a0": float(g[0]), "B": B, "bf": bf, "s0": s0, "c": c, "sh": sh}
+    assert abs(B[2]) < 2**51 and -2**11 <= s0 < 2**11, (e, j, B[2], s0)   # B2 | s0 << 52
+    bf = [f32(beta[k] / mp.mpf(2) ** s0) for k in range(NI, DEG)]
+    for x in bf:                                                   # normal floats (or 0)
+        assert x == 0 or 2.0**-126 <= abs(x) < 2.0**62, (e, j, x)
+    return {"a0": float(g[0]), "B": B, "bf": bf, "s0": s0}
 
 
 def emulate(q, K, Tu):
@@ -137,9 +137,8 @@ def emulate(q, K, Tu):
     F = np.float32(q["bf"][-1])
     for cf in reversed(q["bf"][:-1]):
         F = np.float32(float(F) * tf + cf)
-    i3 = int(round(float(np.float32(float(F) * 2.0 ** q["c"]))))
-    assert abs(i3) < 2**31
-    acc = i3 << q["sh"]
+    acc = int(np.rint(float(F)))                                  # float -> int64, nearest even
+    assert abs(acc) < 2**62
     for k in reversed(range(NI)):
         acc = q["B"][k] + ((acc * Tau) >> 64)
         assert abs(acc) < 2**63
@@ -202,20 +201,26 @@ def main():
         "// G(t) = Q(V - log(1 + t/m_c)) from the recycling ODE Q'' + Q' = Q Q'^2,\n",
         "// re-expanded about the segment end and stored for fixed-point evaluation:\n",
         "// G = a0 + t_u H, H = sum beta_k tau^k > 0, tau = (m_end - m) 2^K in (0, 1],\n",
-        "// beta_0..2 as int64 B_k = beta_k 2^-s0, beta_3..6 as float.\n",
+        "// beta_0..2 as int64 B_k = beta_k 2^-s0 (A: a0, B0, B1, B2 | s0 << 52),\n",
+        "// beta_3..6 as float f_k = beta_k 2^-s0 (F).\n",
         f"// Binade e = -1 - E: K = {K_MAIN} for e < {E_MAIN}, K = {K_DEEP} for e = {E_MAIN}..{E_LAST}.\n",
         f"// Index e 2^{K_MAIN} + j (e < {E_MAIN}), {N_MAIN} + (e - {E_MAIN}) 2^{K_DEEP} + j.\n",
         f"// Emulated worst relative error over the checked points: {worst:.3g}.\n",
-        "#pragma once\n#include \"qm_fx.cuh\"   // layout (K_MAIN .. N_ALL, SegFx) and evaluation\n\n",
+        "#pragma once\n#include \"qm_fx.cuh\"   // layout (K_MAIN .. N_ALL, FxTable) and evaluation\n\n",
         "namespace qm {\nnamespace fxt {\n\n",
-        f"__device__ const SegFx SEG_FX[{N_ALL}] = {{\n",
+        "__device__ const FxTable SEG_FX = {\n {\n",
     ]
     for e, j, q, _ in res:
         B = q["B"]
-        lines.append("  {" + hexd(q["a0"]) + "," + ",".join(f"{b}ll" for b in B) + "," +
-                     ",".join(hexf(x) for x in q["bf"]) + f",{q['s0']}," +
-                     hexf(2.0 ** q["c"]) + f",{q['sh']},0}},\n")
-    lines.append("};\n\n}  // namespace fxt\n}  // namespace qm\n")
+        b2s = ((q["s0"] & 0xFFF) << 52) | (B[2] & (2**52 - 1))
+        if b2s >= 2**63:
+            b2s -= 2**64
+        lits = [f"{b}ll" for b in B[:2]] + [f"{b2s}ll" if b2s != -2**63 else "(-0x7fffffffffffffffll - 1)"]
+        lines.append("  {" + hexd(q["a0"]) + "," + ",".join(lits) + "},\n")
+    lines.append(" },\n {\n")
+    for e, j, q, _ in res:
+        lines.append("  {" + ",".join(hexf(x) for x in q["bf"]) + "},\n")
+    lines.append(" }\n};\n\n}  // namespace fxt\n}  // namespace qm\n")
     with open(OUT, "w") as f:
         f.write("".join(lines))
     print("wrote", OUT, file=sys.stderr)

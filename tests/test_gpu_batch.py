@@ -124,3 +124,31 @@ def test_batch_full_size_sampled():
     b.close()
     del ins, outs
     torch.cuda.empty_cache()
+
+
+def test_batch_uniform_segments_match_the_streaming_kernel_bit_for_bit():
+    """Uniform -> normal segments of the batch evaluate the same fixed-point
+    table as the streaming FP64 kernel, with the single-precision tail turned
+    into an integer by integer operations instead of the hardware conversion;
+    both round to nearest even, so the results must be identical.  The inputs
+    crowd the top segment next to u = 1/2, where that tail passes through 0
+    and the conversion rounds, plus the tail-stress mixture."""
+    rng = np.random.default_rng(41)
+    k = np.concatenate([2**52 + rng.integers(-2**46, 2**46, 1 << 18), 2**52 + np.arange(-4096, 4096)])
+    near = k.astype(np.float64) * 2.0**-53
+    mix = W.mixture_f64(43, 1 << 18).numpy()
+    u = torch.from_numpy(np.concatenate([near, mix])).to(DEV)
+    zb = torch.empty_like(u)
+    zs = torch.empty_like(u)
+    zf = torch.empty_like(u)
+    b = qm.Batch([(qm.QM_DIST_UNIFORM, qm.QM_DIST_NORMAL, 0.0, u, zb)])
+    b.run()
+    torch.cuda.synchronize()
+    b.close()
+    b = qm.Batch([(qm.QM_DIST_UNIFORM, qm.QM_DIST_NORMAL, 0.0, u, zs)])
+    b.run_separate()
+    torch.cuda.synchronize()
+    b.close()
+    qm.qm_normal_quantile_f64(u, zf, qm.QM_VAR_FIXED)
+    torch.cuda.synchronize()
+    assert torch.equal(zb, zf) and torch.equal(zs, zf)
