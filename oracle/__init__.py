@@ -15,6 +15,12 @@ What each routine computes, and the passage it restates:
                      through the regularised incomplete beta function.
 * ``recycle_exp`` -- Q(x) = Phi^{-1}(1 - e^{-x}), exponential -> normal
                      (Sec. 2.3 and Sec. 6).
+* ``chi2_from_normal`` -- W = F^{-1}(Phi(z)) for W ~ chi-squared(nu): the
+                     mixing variable of the t copula (Sec. 9), through the
+                     regularised incomplete gamma function (DLMF 8.7.1 series,
+                     8.9.2 continued fraction) solved in log space.
+* ``t_to_normal`` -- G(t) = Phi^{-1}(F_nu(t)), Student t -> normal (the
+                     inverse of the Sec. 3 map), for t-copula margins.
 * ``philox_stream`` -- Philox4x32-10 words (Salmon et al., SC'11).
 * ``hyperbolic.recycle_hyperbolic`` -- Q(v) = F^{-1}(G_0(v)), two-sided
                      exponential -> hyperbolic (Sec. 8.1), by quadrature and
@@ -61,7 +67,8 @@ def lib() -> ctypes.CDLL:
                      "orc_recycle_exp_to_normal"):
             getattr(L, name).restype = d
             getattr(L, name).argtypes = [d]
-        for name in ("orc_t_sf", "orc_recycle_normal_to_t"):
+        for name in ("orc_t_sf", "orc_recycle_normal_to_t", "orc_log_gamma_p", "orc_log_gamma_q",
+                     "orc_chi2_from_normal", "orc_t_to_normal"):
             getattr(L, name).restype = d
             getattr(L, name).argtypes = [d, d]
         L.orc_t_gamma.restype = d
@@ -106,6 +113,20 @@ def recycle_t(nu: float, z, nthreads: int = 0) -> np.ndarray:
 
 def recycle_exp(x, nthreads: int = 0) -> np.ndarray:
     return _vec(lib().orc_recycle_exp_array, x, nthreads=nthreads)
+
+
+def chi2_from_normal(nu: float, z) -> np.ndarray:
+    """W = F_{chi2(nu)}^{-1}(Phi(z)) element by element."""
+    f = lib().orc_chi2_from_normal
+    z = _f64(z)
+    return np.array([f(nu, float(v)) for v in z.ravel()]).reshape(z.shape)
+
+
+def t_to_normal(nu: float, t) -> np.ndarray:
+    """G(t) = Phi^{-1}(F_nu(t)) element by element."""
+    f = lib().orc_t_to_normal
+    t = _f64(t)
+    return np.array([f(nu, float(v)) for v in t.ravel()]).reshape(t.shape)
 
 
 def scalar(name: str):

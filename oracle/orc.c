@@ -354,6 +354,115 @@ double orc_recycle_exp_to_normal(double x)
 }
 
 /* ------------------------------------------------------------------------
+ * Chi-squared and the t -> normal map, for the t copula (Sec. 9).
+ * ---------------------------------------------------------------------- */
+
+/* log P(a, x) and log Q(a, x), the regularised incomplete gamma functions,
+ * with x = e^s given by its logarithm (so x may lie far below the double
+ * range).  Series, DLMF 8.7.1:
+ *   P(a,x) = x^a e^{-x} / Gamma(a+1) * sum_{n>=0} x^n / ((a+1)...(a+n)),
+ * for x < a + 1; otherwise the continued fraction of DLMF 8.9.2,
+ *   Q(a,x) = x^a e^{-x} / Gamma(a) * 1/(x+1-a- 1(1-a)/(x+3-a- 2(2-a)/(...))),
+ * by the modified Lentz method.  Each returns the log of its own function;
+ * the complement is taken in log space.                                    */
+static double log_gamma_p_series(double a, double s)
+{
+    const double x = exp(s);
+    double term = 1.0, sum = 1.0;
+    for (int n = 1; n < 100000; ++n) {
+        term *= x / (a + n);
+        sum += term;
+        if (term < 1e-18 * sum) break;
+    }
+    return a * s - x - lgamma(a + 1.0) + log(sum);
+}
+
+static double log_gamma_q_cf(double a, double s)
+{
+    const double x = exp(s), tiny = 1e-300;
+    double b = x + 1.0 - a;
+    double C = 1.0 / tiny, D = 1.0 / b, f = D;
+    for (int n = 1; n < 100000; ++n) {
+        const double an = -n * (n - a);
+        b += 2.0;
+        D = an * D + b;
+        if (fabs(D) < tiny) D = tiny;
+        C = b + an / C;
+        if (fabs(C) < tiny) C = tiny;
+        D = 1.0 / D;
+        const double delta = C * D;
+        f *= delta;
+        if (fabs(delta - 1.0) < 1e-17) break;
+    }
+    return a * s - x - lgamma(a) + log(f);
+}
+
+double orc_log_gamma_p(double a, double s)
+{
+    if (exp(s) < a + 1.0) return log_gamma_p_series(a, s);
+    return log1p(-exp(log_gamma_q_cf(a, s)));
+}
+
+double orc_log_gamma_q(double a, double s)
+{
+    if (exp(s) < a + 1.0) return log1p(-exp(log_gamma_p_series(a, s)));
+    return log_gamma_q_cf(a, s);
+}
+
+/* W = F^{-1}(Phi(z)) for W ~ chi-squared with nu degrees of freedom
+ * (Gamma(nu/2) in x = W/2).  z <= 0 solves log P(nu/2, x) = log Phi(z),
+ * z > 0 solves log Q(nu/2, x) = log(1 - Phi(z)), for s = log x by bisection
+ * with Newton steps; both sides are relative-accurate far into the tails.
+ * d log P / ds = x f(x) / P and d log Q / ds = -x f(x) / Q, with
+ * x f(x) = x^a e^{-x} / Gamma(a).                                          */
+double orc_chi2_from_normal(double nu, double z)
+{
+    if (isnan(z) || !(nu > 0.0)) return NAN;
+    if (z == -INFINITY) return 0.0;
+    if (z == INFINITY) return INFINITY;
+    const double a = 0.5 * nu;
+    const int lower = z <= 0.0;
+    const double target = lower ? orc_log_norm_sf(-z) : orc_log_norm_sf(z);
+    double lo = -3000.0, hi = 12.0;
+    /* start: the leading term of the side being solved */
+    double s = lower ? (target + lgamma(a + 1.0)) / a : log(a + 4.0 * z * z + 1.0);
+    if (!(s > lo && s < hi)) s = 0.5 * (lo + hi);
+    for (int it = 0; it < 400; ++it) {
+        const double lp = lower ? orc_log_gamma_p(a, s) : orc_log_gamma_q(a, s);
+        const double g = lower ? lp - target : target - lp;   /* increasing in s */
+        if (g == 0.0) break;
+        if (g > 0.0) hi = s; else lo = s;
+        const double dlog = exp(a * s - exp(s) - lgamma(a) - lp);   /* |d lp / ds| */
+        double sn = s - g / dlog;
+        if (!(sn > lo && sn < hi)) sn = 0.5 * (lo + hi);
+        if (fabs(sn - s) <= 1e-16 * fmax(1.0, fabs(s)) || hi - lo <= 1e-16 * fmax(1.0, fabs(hi))) {
+            s = sn;
+            break;
+        }
+        s = sn;
+    }
+    return 2.0 * exp(s);
+}
+
+/* G(t) = Phi^{-1}(F_nu(t)), the Student t -> normal map (the inverse of
+ * orc_recycle_normal_to_t).  Odd in t.  With p = P(T > |t|):
+ * p < 1/4: tail form -Phi^{-1}(p) from log p;
+ * otherwise the centre form: 2 F(|t|) - 1 = I_y(1/2, nu/2), y = t^2/(nu+t^2),
+ * and |G| solves erf(|G|/sqrt2) = that.  Domain: P(T > |t|) a normal double
+ * (|G| below about 37.5).                                                  */
+double orc_t_to_normal(double nu, double t)
+{
+    if (isnan(t) || !(nu > 0.0)) return NAN;
+    if (t == 0.0) return t;
+    if (isinf(t)) return t;
+    const double at = fabs(t), sg = copysign(1.0, t);
+    const double p = orc_t_sf(nu, at);
+    if (p < 0.25) return sg * orc_probit_tail_log(log(p));
+    const double y = at * at / (nu + at * at);
+    return sg * orc_probit_centre(orc_ibeta(0.5, 0.5 * nu, y));
+}
+
+/* ------------------------------------------------------------------------
  * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  One round maps the
  * counter (c0, c1, c2, c3) with round key (k0, k1) to
  *   (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)),

@@ -47,6 +47,12 @@ double orc_t_sf(double nu, double t);                /* P(T_nu > t)          */
 double orc_t_gamma(double nu);                       /* Q'(0), Sec. 3.1      */
 double orc_recycle_normal_to_t(double nu, double z); /* F_nu^{-1}(Phi(z))    */
 
+/* ---- t copula (Sec. 9): chi-squared mixing variable, t -> normal ------- */
+double orc_log_gamma_p(double a, double s);   /* log P(a, e^s), regularised    */
+double orc_log_gamma_q(double a, double s);   /* log Q(a, e^s) = log(1 - P)    */
+double orc_chi2_from_normal(double nu, double z); /* F_chi2(nu)^{-1}(Phi(z))   */
+double orc_t_to_normal(double nu, double t);      /* Phi^{-1}(F_nu(t))         */
+
 /* ---- exponential background (Sec. 2.3, Sec. 6) ------------------------ */
 double orc_recycle_exp_to_normal(double x);          /* Phi^{-1}(1 - e^{-x}) */
 
