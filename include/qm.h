@@ -273,6 +273,37 @@ qm_status qm_copula_sample(const qm_copula* c, uint64_t key, uint64_t ctr0, doub
                            void* stream);
 qm_status qm_copula_destroy(qm_copula* c);
 
+/* ---- t copula (Sec. 9) ------------------------------------------------------
+ * x_j = F_j^{-1}(F_nu(T_j)), T = (L eps) / sigma * sqrt(nu / W): eps iid
+ * normal, W ~ chi-squared(nu) shared by the coordinates of a sample, sigma_j
+ * the row norms of L (so that L L^T may be a covariance; the copula is that of
+ * its correlation).  The paper's folding (Sec. 9): W comes from one more
+ * grid normal through the normal -> chi-squared recycling map, and each
+ * coordinate goes straight to its margin: a Student-t margin with the
+ * copula's nu is T_j itself, a normal margin is G(T_j) = Phi^{-1}(F_nu(T_j))
+ * (the Student t -> normal recycling map), a Student-t margin with another
+ * mu is the normal -> t_mu map after G.  Both maps are tables built on the
+ * host from their recycling ODEs at the first use of a nu (cached per device
+ * until exit).  Sample i uses the Philox blocks ctr0/4 + i ceil((d+1)/2) + b:
+ * its first 53-bit normal is W's, the next d are eps.
+ * qm_tcopula_create: as qm_copula_create plus nu in [QM_T_NU_MIN, QM_T_NU_MAX]
+ * (QM_ERR_UNSUPPORTED outside); the handle is sampled and destroyed by
+ * qm_copula_sample / qm_copula_destroy.
+ * qm_tcopula_table_build (host only, no GPU): the two tables for nu --
+ * chi_seg: QM_TC_NZ x 10 coefficients of log W(z) about the centres
+ * -QM_TC_Z_MAX + (j + 1/2)/QM_TC_HZ_INV; g_seg: (QM_TC_NA + *nb) x 10
+ * (room for QM_TC_NA + QM_TC_NB_MAX) coefficients of G: rows j < QM_TC_NA in
+ * t about 0 (j = 0) or (j + 1/2)/QM_TC_HT_INV, rows QM_TC_NA + i in y = log t
+ * about ln 2 + (i + 1/2)/QM_TC_HT_INV.                                         */
+#define QM_TC_Z_MAX 8.5
+#define QM_TC_HZ_INV 16
+#define QM_TC_NZ 272
+#define QM_TC_HT_INV 32
+#define QM_TC_NA 64
+#define QM_TC_NB_MAX 2048
+qm_status qm_tcopula_create(int d, double nu, const double* chol, const qm_margin* margins, qm_copula** out);
+qm_status qm_tcopula_table_build(double nu, double* chi_seg, double* g_seg, int* nb);
+
 /* ---- ragged batches ---------------------------------------------------------
  * A batch is a table of independent recycling jobs evaluated by ONE
  * persistent launch over a device-resident segment table, replayed as a CUDA

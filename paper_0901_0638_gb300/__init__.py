@@ -93,6 +93,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "qm_hyp_destroy": [vp],
         "qm_hyp_table_build": [d, d, d, vp, vp, vp, vp],
         "qm_copula_create": [i, vp, vp, vp],
+        "qm_tcopula_create": [i, d, vp, vp, vp],
+        "qm_tcopula_table_build": [d, vp, vp, vp],
         "qm_copula_sample": [vp, u64, u64, vp, sz, vp],
         "qm_copula_destroy": [vp],
         "qm_sample_moments_noalloc": [u64, u64, sz, vp, vp],
@@ -228,6 +230,23 @@ def qm_t_table_build(nu: float):
     return seg, tail
 
 
+QM_TC_Z_MAX, QM_TC_HZ_INV, QM_TC_NZ, QM_TC_HT_INV, QM_TC_NA, QM_TC_NB_MAX = 8.5, 16, 272, 32, 64, 2048
+
+
+def qm_tcopula_table_build(nu: float):
+    """Host-built t-copula tables (no GPU): (chi, g) -- chi[j, k] coefficient k
+    of log W(z) about -QM_TC_Z_MAX + (j + 1/2)/QM_TC_HZ_INV; g[j, k] of
+    G(t) = Phi^{-1}(F_nu(t)) about 0 (j = 0) or (j + 1/2)/QM_TC_HT_INV for
+    j < QM_TC_NA, in y = log t about ln 2 + (j - QM_TC_NA + 1/2)/QM_TC_HT_INV
+    above."""
+    import numpy as np
+    chi = np.zeros((QM_TC_NZ, 10), dtype=np.float64)
+    g = np.zeros((QM_TC_NA + QM_TC_NB_MAX, 10), dtype=np.float64)
+    nb = ctypes.c_int(0)
+    _check(load().qm_tcopula_table_build(float(nu), chi.ctypes.data, g.ctypes.data, ctypes.byref(nb)))
+    return chi, g[: QM_TC_NA + nb.value]
+
+
 QM_HYP_E_MIN, QM_HYP_MAX_BINADES = -30, 64
 
 
@@ -287,18 +306,22 @@ class qm_margin(ctypes.Structure):
 
 
 class Copula:
-    """Gaussian copula with recycled marginals (qm_copula_*): chol is a d x d
+    """Gaussian copula (qm_copula_create) or, with nu, t copula
+    (qm_tcopula_create) with recycled marginals: chol is a d x d
     lower-triangular Cholesky factor (host array), margins a list of
     (kind, nu) with kind QM_DIST_NORMAL or QM_DIST_STUDENT_T."""
 
-    def __init__(self, chol, margins):
+    def __init__(self, chol, margins, nu=None):
         import numpy as np
         L = np.ascontiguousarray(np.asarray(chol, dtype=np.float64))
         d = L.shape[0]
-        arr = (qm_margin * d)(*[qm_margin(int(k), float(nu or 0.0)) for k, nu in margins])
+        arr = (qm_margin * d)(*[qm_margin(int(k), float(m_nu or 0.0)) for k, m_nu in margins])
         h = ctypes.c_void_p()
-        _check(load().qm_copula_create(d, L.ctypes.data, arr, ctypes.byref(h)))
-        self._h, self.d = h, d
+        if nu is None:
+            _check(load().qm_copula_create(d, L.ctypes.data, arr, ctypes.byref(h)))
+        else:
+            _check(load().qm_tcopula_create(d, float(nu), L.ctypes.data, arr, ctypes.byref(h)))
+        self._h, self.d, self.nu = h, d, nu
 
     def sample(self, key: int, ctr0: int, out, n: int, stream=None):
         _check(load().qm_copula_sample(self._h, key, ctr0, _ptr(out), n, _stream(stream, out)))

@@ -12,6 +12,13 @@
 //                                             the Sec. 3 map, any supported nu).
 // Sample i uses the Philox blocks ctr0/4 + i ceil(d/2) + 0 .. ceil(d/2)-1.
 // Output is column-major, x[j n + i], so the stores of a warp coalesce.
+//
+// The t copula (same handle): one more grid normal per sample gives the
+// chi-squared mixing variable through its recycling map, W = exp(L(z)),
+// T_j = y_j / sigma_j sqrt(nu / W), and each T_j goes to its margin: itself
+// (Student t with the copula's nu), G(T_j) (normal; the Student t -> normal
+// map) or the normal -> t_mu map after G.  The two maps are the host-built
+// tables of qm_tcop_tables.cu.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -28,13 +35,57 @@ namespace {
 
 constexpr int kMaxD = QM_COPULA_MAX_DIM;
 
+enum { MARGIN_NORMAL = 0, MARGIN_T = 1, MARGIN_SAME_T = 2 };
+
 struct CopulaDev {
     int d;
-    int pad;
+    int tcop;                             // 0: Gaussian copula, 1: t copula
     double L[kMaxD * (kMaxD + 1) / 2];   // packed rows of the lower triangle
-    int kind[kMaxD];                      // QM_DIST_NORMAL or QM_DIST_STUDENT_T
+    int kind[kMaxD];                      // MARGIN_*
     TSel t[kMaxD];
+    // t copula
+    double inv_sigma[kMaxD];              // 1 / row norms of L
+    double half_log_nu;
+    const double* chi;                    // log W(z) segments (QM_TC_NZ x 10)
+    const double* g;                      // G segments ((QM_TC_NA + nb) x 10)
+    int nb;
+    int pad;
 };
+
+__device__ __forceinline__ double seg10(const double* __restrict__ c, double s)
+{
+    double r = __ldg(c + 9);
+#pragma unroll
+    for (int k = 8; k >= 0; --k) r = __fma_rn(r, s, __ldg(c + k));
+    return r;
+}
+
+// log W for the normal score z (|z| <= 8.3 on the 53-bit grid)
+__device__ __forceinline__ double tc_log_w(const double* __restrict__ chi, double z)
+{
+    int j = (int)floor((z + QM_TC_Z_MAX) * QM_TC_HZ_INV);
+    j = min(max(j, 0), QM_TC_NZ - 1);
+    const double s = z - (-QM_TC_Z_MAX + (j + 0.5) * (1.0 / QM_TC_HZ_INV));
+    return seg10(chi + 10 * j, s);
+}
+
+// G(t) = Phi^{-1}(F_nu(t)): segments in |t| below 2, in log|t| above
+__device__ __forceinline__ double tc_g(const double* __restrict__ g, int nb, double t)
+{
+    const double a = fabs(t);
+    int row;
+    double s;
+    if (a < 2.0) {
+        row = min((int)(a * QM_TC_HT_INV), QM_TC_NA - 1);
+        s = a - (row == 0 ? 0.0 : (row + 0.5) * (1.0 / QM_TC_HT_INV));
+    } else {
+        const double y = log(a);
+        const int i = min(max((int)((y - 0.69314718055994530942) * QM_TC_HT_INV), 0), nb - 1);
+        s = y - (0.69314718055994530942 + (i + 0.5) * (1.0 / QM_TC_HT_INV));
+        row = QM_TC_NA + i;
+    }
+    return copysign(seg10(g + 10 * row, s), t);
+}
 
 // normal from two Philox words (53-bit integer, exact reflected grid point,
 // the fixed-point FP64 evaluation)
@@ -83,40 +134,94 @@ k_copula(const CopulaDev* __restrict__ cp, PhiloxKeys K, uint64_t blk0, double* 
 #pragma unroll
         for (int j = 0; j < D; ++j) {
             double x = y[j];
-            if (c.kind[j] == QM_DIST_STUDENT_T) x = recycle_t_call(c.t[j], x);
+            if (c.kind[j] == MARGIN_T) x = recycle_t_call(c.t[j], x);
+            __stcs(out + (size_t)j * n + i, x);
+        }
+    }
+}
+
+// t copula: sample i draws ceil((D+1)/2) Philox blocks; normal 0 is the
+// mixing variable's score, normals 1..D are eps
+template <int D>
+__global__ void __launch_bounds__(128)
+k_tcopula(const CopulaDev* __restrict__ cp, PhiloxKeys K, uint64_t blk0, double* out, size_t n,
+          const fxt::FxTable* fxT)
+{
+    __shared__ CopulaDev c;
+    {
+        const int* src = reinterpret_cast<const int*>(cp);
+        int* dst = reinterpret_cast<int*>(&c);
+        for (int i = threadIdx.x; i < (int)(sizeof(CopulaDev) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    constexpr int nb = (D + 2) / 2;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        double y[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) y[j] = 0.0;
+        double zw = 0.0;
+#pragma unroll
+        for (int b = 0; b < nb; ++b) {
+            const uint4 w = philox_block_keys(K, blk0 + (uint64_t)i * nb + b);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int q = 2 * b + h;               // normal index in the sample
+                if (q > D) break;
+                const double e = h ? normal_from_words(fxT, w.z, w.w) : normal_from_words(fxT, w.x, w.y);
+                if (q == 0) {
+                    zw = e;
+                } else {
+                    const int k = q - 1;
+#pragma unroll
+                    for (int j = k; j < D; ++j) y[j] = __fma_rn(c.L[j * (j + 1) / 2 + k], e, y[j]);
+                }
+            }
+        }
+        const double S = exp(c.half_log_nu - 0.5 * tc_log_w(c.chi, zw));    // sqrt(nu / W)
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            const double T = y[j] * c.inv_sigma[j] * S;
+            double x = T;
+            if (c.kind[j] != MARGIN_SAME_T) {
+                x = tc_g(c.g, c.nb, T);
+                if (c.kind[j] == MARGIN_T) x = recycle_t_call(c.t[j], x);
+            }
             __stcs(out + (size_t)j * n + i, x);
         }
     }
 }
 
 template <int D>
-qm_status launch_d(const CopulaDev* dev, PhiloxKeys K, uint64_t blk0, double* out, size_t n, cudaStream_t s)
+qm_status launch_d(const CopulaDev* dev, bool tcop, PhiloxKeys K, uint64_t blk0, double* out, size_t n,
+                   cudaStream_t s)
 {
     qm_status fst;
     const fxt::FxTable* fxT = (const fxt::FxTable*)fx_table_device(&fst);
     if (!fxT) return fst;
     int bps = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_copula<D>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, tcop ? k_tcopula<D> : k_copula<D>, 128, 0);
     const size_t cap = (size_t)(sm_count() > 0 ? sm_count() : 1) * (bps > 0 ? bps : 1);
     size_t g = (n + 127) / 128;
     if (g > cap) g = cap;
-    k_copula<D><<<(int)g, 128, 0, s>>>(dev, K, blk0, out, n, fxT);
+    if (tcop) k_tcopula<D><<<(int)g, 128, 0, s>>>(dev, K, blk0, out, n, fxT);
+    else k_copula<D><<<(int)g, 128, 0, s>>>(dev, K, blk0, out, n, fxT);
     return check_launch("copula sample");
 }
 
 template <int... Ds>
-qm_status launch_dispatch(int d, const CopulaDev* dev, PhiloxKeys K, uint64_t blk0, double* out, size_t n,
-                          cudaStream_t s, std::integer_sequence<int, Ds...>)
+qm_status launch_dispatch(int d, const CopulaDev* dev, bool tcop, PhiloxKeys K, uint64_t blk0, double* out,
+                          size_t n, cudaStream_t s, std::integer_sequence<int, Ds...>)
 {
     qm_status st = QM_ERR_INVALID;
-    ((d == Ds + 1 ? (st = launch_d<Ds + 1>(dev, K, blk0, out, n, s), 0) : 0), ...);
+    ((d == Ds + 1 ? (st = launch_d<Ds + 1>(dev, tcop, K, blk0, out, n, s), 0) : 0), ...);
     return st;
 }
 
-qm_status launch_copula(int d, const CopulaDev* dev, PhiloxKeys K, uint64_t blk0, double* out, size_t n,
-                        cudaStream_t s)
+qm_status launch_copula(int d, const CopulaDev* dev, bool tcop, PhiloxKeys K, uint64_t blk0, double* out,
+                        size_t n, cudaStream_t s)
 {
-    return launch_dispatch(d, dev, K, blk0, out, n, s, std::make_integer_sequence<int, kMaxD>{});
+    return launch_dispatch(d, dev, tcop, K, blk0, out, n, s, std::make_integer_sequence<int, kMaxD>{});
 }
 
 }  // namespace
@@ -129,46 +234,91 @@ struct qm_copula {
     CopulaDev* dev;
 };
 
-extern "C" qm_status qm_copula_create(int d, const double* chol, const qm_margin* margins, qm_copula** out)
+namespace {
+
+// validation and the parts common to both copulas; tcop_nu > 0 for the t copula
+qm_status fill_copula(int d, const double* chol, const qm_margin* margins, double tcop_nu, qm_copula& c,
+                      const char* who)
 {
-    if (!out || !chol || !margins) return fail(QM_ERR_INVALID, "qm_copula_create: null argument");
-    *out = nullptr;
-    if (d < 1 || d > kMaxD) return fail(QM_ERR_INVALID, "qm_copula_create: d = %d outside [1, %d]", d, kMaxD);
-    qm_copula c{};
+    if (!chol || !margins) return fail(QM_ERR_INVALID, "%s: null argument", who);
+    if (d < 1 || d > kMaxD) return fail(QM_ERR_INVALID, "%s: d = %d outside [1, %d]", who, d, kMaxD);
     c.host.d = d;
+    c.host.tcop = tcop_nu > 0.0;
     for (int j = 0; j < d; ++j) {
+        double ss = 0.0;
         for (int k = 0; k < d; ++k) {
             const double v = chol[j * d + k];
-            if (!std::isfinite(v)) return fail(QM_ERR_INVALID, "qm_copula_create: L[%d][%d] not finite", j, k);
+            if (!std::isfinite(v)) return fail(QM_ERR_INVALID, "%s: L[%d][%d] not finite", who, j, k);
             if (k > j && v != 0.0)
-                return fail(QM_ERR_INVALID, "qm_copula_create: L must be lower triangular (L[%d][%d] = %g)", j, k, v);
-            if (k <= j) c.host.L[j * (j + 1) / 2 + k] = v;
+                return fail(QM_ERR_INVALID, "%s: L must be lower triangular (L[%d][%d] = %g)", who, j, k, v);
+            if (k <= j) {
+                c.host.L[j * (j + 1) / 2 + k] = v;
+                ss += v * v;
+            }
         }
-        if (!(chol[j * d + j] > 0.0))
-            return fail(QM_ERR_INVALID, "qm_copula_create: L[%d][%d] must be > 0", j, j);
+        if (!(chol[j * d + j] > 0.0)) return fail(QM_ERR_INVALID, "%s: L[%d][%d] must be > 0", who, j, j);
+        c.host.inv_sigma[j] = 1.0 / std::sqrt(ss);
         const qm_margin& m = margins[j];
-        c.host.kind[j] = m.kind;
         c.host.t[j] = TSel{0, 0, nullptr, nullptr};
         if (m.kind == QM_DIST_STUDENT_T) {
+            if (tcop_nu > 0.0 && m.nu == tcop_nu) {
+                c.host.kind[j] = MARGIN_SAME_T;
+                continue;
+            }
+            c.host.kind[j] = MARGIN_T;
             const void* seg = nullptr;
             const double* tail = nullptr;
             const qm_status st = t_select(m.nu, &c.host.t[j].k, &seg, &tail);
             if (st != QM_OK) return st;
             c.host.t[j].seg = (const ttbl::SegT*)seg;
             c.host.t[j].tail = tail;
-        } else if (m.kind != QM_DIST_NORMAL) {
-            return fail(QM_ERR_UNSUPPORTED, "qm_copula_create: margin %d: kind %d not supported "
-                        "(normal or Student t)", j, m.kind);
+        } else if (m.kind == QM_DIST_NORMAL) {
+            c.host.kind[j] = MARGIN_NORMAL;
+        } else {
+            return fail(QM_ERR_UNSUPPORTED, "%s: margin %d: kind %d not supported (normal or Student t)", who, j,
+                        m.kind);
         }
     }
-    if (cudaMalloc(&c.dev, sizeof(CopulaDev)) != cudaSuccess)
-        return fail(QM_ERR_NOMEM, "qm_copula_create: allocation failed");
+    return QM_OK;
+}
+
+qm_status upload(qm_copula& c, qm_copula** out, const char* who)
+{
+    if (cudaMalloc(&c.dev, sizeof(CopulaDev)) != cudaSuccess) return fail(QM_ERR_NOMEM, "%s: allocation failed", who);
     if (cudaMemcpy(c.dev, &c.host, sizeof(CopulaDev), cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaFree(c.dev);
-        return fail(QM_ERR_CUDA, "qm_copula_create: upload failed");
+        return fail(QM_ERR_CUDA, "%s: upload failed", who);
     }
     *out = new qm_copula(c);
     return QM_OK;
+}
+
+}  // namespace
+
+extern "C" qm_status qm_copula_create(int d, const double* chol, const qm_margin* margins, qm_copula** out)
+{
+    if (!out) return fail(QM_ERR_INVALID, "qm_copula_create: null argument");
+    *out = nullptr;
+    qm_copula c{};
+    const qm_status st = fill_copula(d, chol, margins, 0.0, c, "qm_copula_create");
+    if (st != QM_OK) return st;
+    return upload(c, out, "qm_copula_create");
+}
+
+extern "C" qm_status qm_tcopula_create(int d, double nu, const double* chol, const qm_margin* margins,
+                                       qm_copula** out)
+{
+    if (!out) return fail(QM_ERR_INVALID, "qm_tcopula_create: null argument");
+    *out = nullptr;
+    if (!(nu >= QM_T_NU_MIN && nu <= QM_T_NU_MAX))
+        return fail(QM_ERR_UNSUPPORTED, "qm_tcopula_create: nu = %g outside [%g, %g]", nu, QM_T_NU_MIN, QM_T_NU_MAX);
+    qm_copula c{};
+    qm_status st = fill_copula(d, chol, margins, nu, c, "qm_tcopula_create");
+    if (st != QM_OK) return st;
+    c.host.half_log_nu = 0.5 * std::log(nu);
+    st = tcop_table_device(nu, &c.host.chi, &c.host.g, &c.host.nb);
+    if (st != QM_OK) return st;
+    return upload(c, out, "qm_tcopula_create");
 }
 
 extern "C" qm_status qm_copula_sample(const qm_copula* c, uint64_t key, uint64_t ctr0, double* out, size_t n,
@@ -178,7 +328,8 @@ extern "C" qm_status qm_copula_sample(const qm_copula* c, uint64_t key, uint64_t
     if (ctr0 % 4 != 0) return fail(QM_ERR_INVALID, "qm_copula_sample: ctr0 must be a multiple of 4");
     if (n == 0) return QM_OK;
     if (!out) return fail(QM_ERR_INVALID, "qm_copula_sample: null output");
-    return launch_copula(c->host.d, c->dev, philox_keys(key), ctr0 / 4, out, n, (cudaStream_t)stream);
+    return launch_copula(c->host.d, c->dev, c->host.tcop != 0, philox_keys(key), ctr0 / 4, out, n,
+                         (cudaStream_t)stream);
 }
 
 extern "C" qm_status qm_copula_destroy(qm_copula* c)

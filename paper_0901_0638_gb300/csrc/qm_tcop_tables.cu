@@ -1,0 +1,441 @@
+// qm_tcop_tables.cu -- host-built recycling tables of the t copula (Sec. 9).
+//
+// A t copula with nu degrees of freedom and correlation R draws
+// T = (L eps) sqrt(nu / W), eps iid normal, W ~ chi-squared(nu), and maps each
+// coordinate to its margin.  The paper notes that the trip through the unit
+// hypercube folds into one recycling map per coordinate; two maps make that
+// possible here, each tabulated per nu from its recycling ODE (Sec. 9 form,
+// Q'' + H_0 Q' = H_1(Q) Q'^2, H_i = -(log f_i)'):
+//
+//   mixing variable  W(z) = F_chi2^{-1}(Phi(z))  (normal base, H_0 = z;
+//                    chi-squared target, H_1(w) = -(k-1)/w + 1/2, k = nu/2):
+//                    W W'' = -z W W' - (k-1) W'^2 + W W'^2 / 2,
+//                    stored as L = log W, segments of width 1/16 on
+//                    z in [-8.5, 8.5] (every 53-bit grid normal);
+//   t -> normal      G(t) = Phi^{-1}(F_nu(t))  (Student-t base,
+//                    H_0 = (nu+1) t / (nu + t^2); normal target, H_1 = G):
+//                    (nu + t^2) G'' = -(nu+1) t G' + (nu + t^2) G G'^2,
+//                    segments of width 1/32 on t in [0, 2) (segment 0 the odd
+//                    series about 0), then in y = log t, where the ODE reads
+//                    (nu + e^{2y}) G_yy = nu (1 - e^{2y}) G_y + (nu + e^{2y}) G G_y^2,
+//                    with segments of width 1/32 up to the largest |T| the
+//                    sampler can produce for this nu.
+//
+// Each segment's expansion is computed at its centre c from the value and the
+// slope there (Q(c) by inverting the special function in long double, Q'(c)
+// = f_0 / f_1), the higher Taylor coefficients by the ODE's recurrence, so
+// there is no integration and no error growth in either tail; every segment
+// is checked against direct values at both of its ends.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "qm.h"
+#include "qm_host.h"
+
+namespace qm {
+namespace {
+
+using LD = long double;
+constexpr LD kPi = 3.14159265358979323846264338327950288L;
+constexpr LD kLnSqrt2Pi = 0.91893853320467274178032973640561764L;
+constexpr LD kLn2 = 0.69314718055994530941723212145817657L;
+constexpr int DI = 18;   // working degree of the local series
+constexpr int DO = 9;    // stored degree
+
+// ---- special functions, long double -------------------------------------
+
+// log of Phi(z) and of 1 - Phi(z)
+LD log_ncdf(LD z) { return std::log(0.5L * std::erfc(-z / std::sqrt(2.0L))); }
+LD log_nsf(LD z) { return std::log(0.5L * std::erfc(z / std::sqrt(2.0L))); }
+
+// log P(a, e^lx) by the power series of the lower incomplete gamma function
+LD log_p_series(LD a, LD lx)
+{
+    const LD x = std::exp(lx);
+    LD t = 1.0L, sum = 1.0L;
+    for (int n = 1; n < 200000 && t > 1e-22L * sum; ++n) {
+        t *= x / (a + n);
+        sum += t;
+    }
+    return a * lx - x - std::lgamma(a + 1.0L) + std::log(sum);
+}
+
+// log Q(a, e^lx) by Legendre's continued fraction of the upper function,
+// evaluated with the modified Lentz recurrence
+LD log_q_fraction(LD a, LD lx)
+{
+    const LD x = std::exp(lx), tiny = 1e-4000L;
+    LD bn = x + 1.0L - a, c = 1.0L / tiny, d = 1.0L / bn, h = d;
+    for (int n = 1; n < 200000; ++n) {
+        const LD an = n * (a - n);
+        bn += 2.0L;
+        d = bn + an * d;
+        c = bn + an / c;
+        if (std::fabs(d) < tiny) d = tiny;
+        if (std::fabs(c) < tiny) c = tiny;
+        d = 1.0L / d;
+        const LD f = c * d;
+        h *= f;
+        if (std::fabs(f - 1.0L) < 1e-21L) break;
+    }
+    return a * lx - x - std::lgamma(a) + std::log(h);
+}
+
+LD log_gp(LD a, LD lx) { return std::exp(lx) < a + 1 ? log_p_series(a, lx) : std::log1p(-std::exp(log_q_fraction(a, lx))); }
+LD log_gq(LD a, LD lx) { return std::exp(lx) < a + 1 ? std::log1p(-std::exp(log_p_series(a, lx))) : log_q_fraction(a, lx); }
+
+// s = log(W/2) with P(W <= w) = Phi(z), W ~ chi-squared(2a)
+LD chi2_log_half(LD a, LD z)
+{
+    const bool lower = z <= 0;
+    const LD target = lower ? log_ncdf(z) : log_nsf(z);
+    LD lo = -20000.0L, hi = 30.0L;
+    LD s = lower ? (target + std::lgamma(a + 1.0L)) / a : std::log(a + z * z + 2 * z * std::sqrt(a) + 1);
+    if (!(s > lo && s < hi)) s = 0.5L * (lo + hi);
+    for (int it = 0; it < 500; ++it) {
+        const LD lp = lower ? log_gp(a, s) : log_gq(a, s);
+        const LD g = lower ? lp - target : target - lp;           // increasing in s
+        if (g == 0) break;
+        (g > 0 ? hi : lo) = s;
+        const LD slope = std::exp(a * s - std::exp(s) - std::lgamma(a) - lp);
+        LD sn = s - g / slope;
+        if (!(sn > lo && sn < hi)) sn = 0.5L * (lo + hi);
+        const bool done = std::fabs(sn - s) <= 1e-19L * std::fmax(1.0L, std::fabs(s));
+        s = sn;
+        if (done) break;
+    }
+    return s;
+}
+
+// I_x(a, b) by the continued fraction of DLMF 8.17.22 (x below its mean
+// (a+1)/(a+b+2)); returns log I_x
+LD log_ibeta_cf(LD a, LD b, LD x)
+{
+    const LD tiny = 1e-4000L;
+    LD c = 1.0L, d = 1.0L - (a + b) * x / (a + 1.0L);
+    if (std::fabs(d) < tiny) d = tiny;
+    d = 1.0L / d;
+    LD h = d;
+    for (int m = 1; m < 200000; ++m) {
+        const LD m2 = 2.0L * m;
+        LD num = m * (b - m) * x / ((a + m2 - 1) * (a + m2));
+        d = 1.0L + num * d;
+        c = 1.0L + num / c;
+        if (std::fabs(d) < tiny) d = tiny;
+        if (std::fabs(c) < tiny) c = tiny;
+        d = 1.0L / d;
+        h *= d * c;
+        num = -(a + m) * (a + b + m) * x / ((a + m2) * (a + m2 + 1));
+        d = 1.0L + num * d;
+        c = 1.0L + num / c;
+        if (std::fabs(d) < tiny) d = tiny;
+        if (std::fabs(c) < tiny) c = tiny;
+        d = 1.0L / d;
+        const LD f = d * c;
+        h *= f;
+        if (std::fabs(f - 1.0L) < 1e-21L) break;
+    }
+    const LD lbeta = std::lgamma(a) + std::lgamma(b) - std::lgamma(a + b);
+    return a * std::log(x) + b * std::log1p(-x) - lbeta - std::log(a) + std::log(h);
+}
+
+// g >= 0 with log(1 - Phi(g)) = lp (tail form), or erf(g/sqrt2) = q (centre)
+LD probit_tail_log(LD lp)
+{
+    LD g = std::sqrt(std::fmax(-2 * lp - std::log(-4 * kPi * lp), 0.25L)), lo = 0.0L, hi = 40.0L;
+    for (int it = 0; it < 300; ++it) {
+        const LD f = log_nsf(g) - lp;                                  // decreasing in g
+        (f > 0 ? lo : hi) = g;
+        const LD dl = -std::exp(-g * g / 2 - kLnSqrt2Pi - log_nsf(g));   // d/dg log(1 - Phi)
+        LD gn = g - f / dl;
+        if (!(gn > lo && gn < hi)) gn = 0.5L * (lo + hi);
+        const bool done = std::fabs(gn - g) <= 1e-20L * std::fmax(1.0L, g);
+        g = gn;
+        if (done) break;
+    }
+    return g;
+}
+
+LD probit_centre(LD q)
+{
+    LD g = 1.2533141373155002512L * q, lo = 0.0L, hi = 12.0L;   // sqrt(pi/2) q
+    for (int it = 0; it < 300; ++it) {
+        const LD f = std::erf(g / std::sqrt(2.0L)) - q;
+        (f > 0 ? hi : lo) = g;
+        const LD df = 2.0L * std::exp(-g * g / 2 - kLnSqrt2Pi);
+        LD gn = g - f / df;
+        if (!(gn > lo && gn < hi)) gn = 0.5L * (lo + hi);
+        const bool done = std::fabs(gn - g) <= 1e-20L * std::fmax(1e-300L, g);
+        g = gn;
+        if (done) break;
+    }
+    return g;
+}
+
+// G(t) = Phi^{-1}(F_nu(t)) for t > 0
+LD t_to_normal(LD nu, LD t)
+{
+    const LD a = nu / 2;
+    const LD x = nu / (nu + t * t);                      // P(T > t) = I_x(a, 1/2) / 2
+    if (x < (a + 1) / (a + 2.5L)) {                     // below the mean of I_x(a, 1/2)
+        const LD lp = log_ibeta_cf(a, 0.5L, x) - kLn2;
+        if (lp < std::log(0.25L)) return probit_tail_log(lp);
+        return probit_centre(-std::expm1(lp + kLn2));    // 2 F(t) - 1 = 1 - 2p
+    }
+    const LD y = t * t / (nu + t * t);                   // 2 F(t) - 1 = I_y(1/2, a)
+    return probit_centre(std::exp(log_ibeta_cf(0.5L, a, y)));
+}
+
+// ---- series ---------------------------------------------------------------
+
+using Ser = std::vector<LD>;
+
+Ser smul(const Ser& p, const Ser& q)
+{
+    Ser r(p.size(), 0.0L);
+    for (size_t i = 0; i < p.size(); ++i)
+        for (size_t k = 0; i + k < p.size(); ++k) r[i + k] += p[i] * q[k];
+    return r;
+}
+
+Ser sderiv(const Ser& p)
+{
+    Ser r(p.size(), 0.0L);
+    for (size_t k = 0; k + 1 < p.size(); ++k) r[k] = (k + 1) * p[k + 1];
+    return r;
+}
+
+// W W'' = -(c+s) W W' - (k-1) W'^2 + W W'^2 / 2, W(c) = w0, W'(c) = w1
+Ser taylor_chi2(LD k, LD c, LD w0, LD w1)
+{
+    Ser b(DI + 1, 0.0L);
+    b[0] = w0;
+    b[1] = w1;
+    for (int n = 0; n + 2 <= DI; ++n) {
+        const Ser d1 = sderiv(b);
+        Ser d2 = sderiv(d1);
+        d2[n] = 0.0L;                                   // (m+2)(m+1) b_{m+2}, m = n unknown
+        const Ser P = smul(b, d1), Q2 = smul(d1, d1), R = smul(b, Q2), WW = smul(b, d2);
+        const LD rhs = -c * P[n] - (n >= 1 ? P[n - 1] : 0.0L) - (k - 1) * Q2[n] + 0.5L * R[n];
+        b[n + 2] = (rhs - WW[n]) / (b[0] * (n + 2) * (n + 1));
+    }
+    return b;
+}
+
+// log of a series with b_0 > 0
+Ser slog(const Ser& b)
+{
+    Ser f(b.size(), 0.0L), a(b.size(), 0.0L);
+    for (size_t k = 1; k < b.size(); ++k) a[k] = b[k] / b[0];
+    f[0] = std::log(b[0]);
+    for (size_t k = 1; k < b.size(); ++k) {             // (1 + a) f' = a'
+        LD acc = k * a[k];
+        for (size_t i = 1; i < k; ++i) acc -= a[i] * (k - i) * f[k - i];
+        f[k] = acc / k;
+    }
+    return f;
+}
+
+// (nu + t^2) G'' = -(nu+1) t G' + (nu + t^2) G G'^2 about t = c
+Ser taylor_g_t(LD nu, LD c, LD g0, LD g1)
+{
+    Ser b(DI + 1, 0.0L), A(DI + 1, 0.0L), T(DI + 1, 0.0L);
+    A[0] = nu + c * c;
+    A[1] = 2 * c;
+    A[2] = 1.0L;
+    T[0] = c;
+    T[1] = 1.0L;
+    b[0] = g0;
+    b[1] = g1;
+    for (int n = 0; n + 2 <= DI; ++n) {
+        const Ser d1 = sderiv(b);
+        Ser d2 = sderiv(d1);
+        d2[n] = 0.0L;
+        const Ser Ad2 = smul(A, d2), Td1 = smul(T, d1), GQ = smul(b, smul(d1, d1)), AGQ = smul(A, GQ);
+        const LD rhs = -(nu + 1) * Td1[n] + AGQ[n];
+        b[n + 2] = (rhs - Ad2[n]) / (A[0] * (n + 2) * (n + 1));
+    }
+    return b;
+}
+
+// in y = log t about y = c: dividing the ODE by e^{2c},
+// (nu e^{-2c} + e^{2s}) G'' = nu (e^{-2c} - e^{2s}) G' + (nu e^{-2c} + e^{2s}) G G'^2
+Ser taylor_g_y(LD nu, LD c, LD g0, LD g1)
+{
+    Ser b(DI + 1, 0.0L), E(DI + 1, 0.0L), B(DI + 1, 0.0L), C(DI + 1, 0.0L);
+    const LD em = nu * std::exp(-2 * c);
+    LD f = 1.0L;
+    for (int m = 0; m <= DI; ++m) {
+        E[m] = f;                                       // e^{2s} = sum (2s)^m / m!
+        f *= 2.0L / (m + 1);
+    }
+    for (int m = 0; m <= DI; ++m) {
+        B[m] = E[m] + (m == 0 ? em : 0.0L);
+        C[m] = -nu * E[m] + (m == 0 ? em : 0.0L);
+    }
+    b[0] = g0;
+    b[1] = g1;
+    for (int n = 0; n + 2 <= DI; ++n) {
+        const Ser d1 = sderiv(b);
+        Ser d2 = sderiv(d1);
+        d2[n] = 0.0L;
+        const Ser Bd2 = smul(B, d2), Cd1 = smul(C, d1), BGQ = smul(B, smul(b, smul(d1, d1)));
+        const LD rhs = Cd1[n] + BGQ[n];
+        b[n + 2] = (rhs - Bd2[n]) / (B[0] * (n + 2) * (n + 1));
+    }
+    return b;
+}
+
+LD hornerl(const Ser& b, int D, LD s)
+{
+    LD r = b[D];
+    for (int k = D - 1; k >= 0; --k) r = r * s + b[k];
+    return r;
+}
+
+}  // namespace
+
+// Tables for nu in host memory (layout in qm.h, qm_tcopula_table_build).
+qm_status tcop_table_build(double nu_d, double* chi_seg, double* g_seg, int* nb_out)
+{
+    if (!(nu_d >= QM_T_NU_MIN && nu_d <= QM_T_NU_MAX))
+        return fail(QM_ERR_UNSUPPORTED, "t copula: nu = %g outside [%g, %g]", nu_d, QM_T_NU_MIN, QM_T_NU_MAX);
+    const LD nu = nu_d, k = nu / 2;
+    const LD lgk = std::lgamma(k);
+
+    // ---- mixing variable: L = log W on z in [-Z, Z], width 1/16 ----------
+    const LD hz = 1.0L / QM_TC_HZ_INV;
+    auto logw = [&](LD z) { return kLn2 + chi2_log_half(k, z); };
+    LD worst = 0.0L;
+    for (int j = 0; j < QM_TC_NZ; ++j) {
+        const LD c = -(LD)QM_TC_Z_MAX + (j + 0.5L) * hz;
+        const LD lw = logw(c), w0 = std::exp(lw);
+        // W' = phi(c) / f(W), log f(w) = (k-1) log w - w/2 - k ln 2 - lgamma(k)
+        const LD lf = (k - 1) * lw - w0 / 2 - k * kLn2 - lgk;
+        const LD w1 = std::exp(-c * c / 2 - kLnSqrt2Pi - lf);
+        const Ser L = slog(taylor_chi2(k, c, w0, w1));
+        if (!std::isfinite(L[DI]))
+            return fail(QM_ERR_INVALID, "t copula: chi-squared series overflow for nu = %g", nu_d);
+        for (int e = -1; e <= 1; e += 2) {
+            const LD err = std::fabs(hornerl(L, DO, e * hz / 2) - logw(c + e * hz / 2));
+            worst = std::fmax(worst, err);
+        }
+        for (int q = 0; q <= DO; ++q) chi_seg[(DO + 1) * j + q] = (double)L[q];
+    }
+    if (!(worst < 1e-13L))
+        return fail(QM_ERR_INVALID, "t copula: chi-squared table check failed for nu = %g (%Lg)", nu_d, worst);
+
+    // largest |T| the sampler can produce: |y_j| / sigma_j <= |eps| <= 8.3 sqrt(16)
+    // times S = sqrt(nu / W) at the smallest grid normal
+    const LD smax = std::exp(0.5L * (std::log(nu) - logw(-8.3L)));
+    const LD ymax = std::log(8.3L * 4.0L * smax) + 0.5L;
+    const LD ht = 1.0L / QM_TC_HT_INV, ln2 = kLn2;
+    int nb = (int)std::ceil((ymax - ln2) * QM_TC_HT_INV);
+    if (nb < 1) nb = 1;
+    if (nb > QM_TC_NB_MAX)
+        return fail(QM_ERR_UNSUPPORTED, "t copula: nu = %g needs %d log-segments (max %d)", nu_d, nb, QM_TC_NB_MAX);
+
+    // ---- t -> normal: t in [0, 2), then y = log t --------------------------
+    const LD lft0 = std::lgamma((nu + 1) / 2) - lgk - 0.5L * std::log(nu * kPi);   // log f_nu(0)
+    auto logft = [&](LD t) { return lft0 - (nu + 1) / 2 * std::log1p(t * t / nu); };
+    worst = 0.0L;
+    for (int j = 0; j < QM_TC_NA + nb; ++j) {
+        Ser b;
+        LD lo, hi;
+        if (j < QM_TC_NA) {
+            const LD c = j == 0 ? 0.0L : (j + 0.5L) * ht;
+            const LD g0 = j == 0 ? 0.0L : t_to_normal(nu, c);
+            const LD g1 = std::exp(logft(c) + g0 * g0 / 2 + kLnSqrt2Pi);             // f_nu / phi(G)
+            b = taylor_g_t(nu, c, g0, g1);
+            lo = j * ht - c;
+            hi = (j + 1) * ht - c;
+            for (LD s : {lo, hi}) {
+                if (c + s == 0) continue;
+                const LD ref = t_to_normal(nu, c + s);
+                worst = std::fmax(worst, std::fabs(hornerl(b, DO, s) / ref - 1));
+            }
+        } else {
+            const int i = j - QM_TC_NA;
+            const LD c = ln2 + (i + 0.5L) * ht;
+            const LD t = std::exp(c), g0 = t_to_normal(nu, t);
+            const LD g1 = t * std::exp(logft(t) + g0 * g0 / 2 + kLnSqrt2Pi);         // dG/dy = t G'
+            b = taylor_g_y(nu, c, g0, g1);
+            for (LD s : {-ht / 2, ht / 2}) {
+                const LD ref = t_to_normal(nu, std::exp(c + s));
+                worst = std::fmax(worst, std::fabs(hornerl(b, DO, s) / ref - 1));
+            }
+        }
+        if (!std::isfinite(b[DI]))
+            return fail(QM_ERR_INVALID, "t copula: t -> normal series overflow for nu = %g", nu_d);
+        for (int q = 0; q <= DO; ++q) g_seg[(DO + 1) * j + q] = (double)b[q];
+    }
+    if (!(worst < 1e-13L))
+        return fail(QM_ERR_INVALID, "t copula: t -> normal table check failed for nu = %g (%Lg)", nu_d, worst);
+    *nb_out = nb;
+    return QM_OK;
+}
+
+namespace {
+
+struct TcEntry {
+    int device;
+    double nu;
+    double* chi;   // device, QM_TC_NZ x 10
+    double* g;     // device, (QM_TC_NA + nb) x 10
+    int nb;
+};
+
+std::mutex g_tc_mu;
+std::vector<TcEntry> g_tc_cache;
+constexpr size_t kTcMax = 256;
+
+}  // namespace
+
+// Device tables for nu on the current device, built and uploaded at first use
+// (kept until the process exits).
+qm_status tcop_table_device(double nu, const double** chi, const double** g, int* nb)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(QM_ERR_CUDA, "t copula: no current device");
+    std::lock_guard<std::mutex> lk(g_tc_mu);
+    for (const TcEntry& e : g_tc_cache)
+        if (e.device == dev && e.nu == nu) {
+            *chi = e.chi;
+            *g = e.g;
+            *nb = e.nb;
+            return QM_OK;
+        }
+    if (g_tc_cache.size() >= kTcMax) return fail(QM_ERR_NOMEM, "t copula: more than %zu distinct nu in use", kTcMax);
+    std::vector<double> hc(10 * QM_TC_NZ), hg(10 * (QM_TC_NA + QM_TC_NB_MAX));
+    int n = 0;
+    const qm_status st = tcop_table_build(nu, hc.data(), hg.data(), &n);
+    if (st != QM_OK) return st;
+    TcEntry e{dev, nu, nullptr, nullptr, n};
+    const size_t gbytes = sizeof(double) * 10 * (QM_TC_NA + n);
+    if (cudaMalloc(&e.chi, sizeof(double) * hc.size()) != cudaSuccess || cudaMalloc(&e.g, gbytes) != cudaSuccess) {
+        if (e.chi) cudaFree(e.chi);
+        return fail(QM_ERR_NOMEM, "t copula: table allocation failed");
+    }
+    if (cudaMemcpy(e.chi, hc.data(), sizeof(double) * hc.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(e.g, hg.data(), gbytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(e.chi);
+        cudaFree(e.g);
+        return fail(QM_ERR_CUDA, "t copula: table upload failed");
+    }
+    g_tc_cache.push_back(e);
+    *chi = e.chi;
+    *g = e.g;
+    *nb = e.nb;
+    return QM_OK;
+}
+
+}  // namespace qm
+
+extern "C" qm_status qm_tcopula_table_build(double nu, double* chi_seg, double* g_seg, int* nb)
+{
+    if (!chi_seg || !g_seg || !nb) return qm::fail(QM_ERR_INVALID, "qm_tcopula_table_build: null argument");
+    return qm::tcop_table_build(nu, chi_seg, g_seg, nb);
+}
