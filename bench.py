@@ -52,7 +52,7 @@ def parse():
     p.add_argument("--variant", default="default")
     p.add_argument("--no-extras", action="store_true", help="skip variant/e2e/cpu legs")
     p.add_argument("--workload", default="fp64", choices=["fp64", "fp32", "batch", "serve", "fused",
-                                                          "hyperbolic", "copula"],
+                                                          "hyperbolic", "copula", "tcopula"],
                    help="fp64: the headline line; fp32/batch/serve: the other hot-path kernels "
                         "(for profiling and context)")
     p.add_argument("--serve-seconds", type=float, default=2.0)
@@ -268,9 +268,10 @@ def side_workload(args):
                                                       "segment tables; 16 B/element",
                               "hbm_frac": 16 * n / (ms * 1e-3) / 1e9 / 6780.7})
         h.close()
-    elif args.workload == "copula":
-        # Gaussian copula, d = 8, equicorrelation 0.5, margins alternating
-        # normal / Student t (nu = 4, 2.7 run-time table, 30), 2^n samples
+    elif args.workload in ("copula", "tcopula"):
+        # Gaussian copula (or t copula with nu = 4), d = 8, equicorrelation
+        # 0.5, margins alternating normal / Student t (nu = 4, 2.7 run-time
+        # table, 30), 2^n samples
         import numpy as np
         n = 1 << (args.n_log2 if args.n_log2 != 28 else 24)
         d = 8
@@ -279,12 +280,14 @@ def side_workload(args):
         margins = [(qm.QM_DIST_NORMAL, 0.0), (qm.QM_DIST_STUDENT_T, 4.0), (qm.QM_DIST_NORMAL, 0.0),
                    (qm.QM_DIST_STUDENT_T, 2.7)] * 2
         margins[-1] = (qm.QM_DIST_STUDENT_T, 30.0)
-        c = qm.Copula(L, margins)
+        tnu = 4.0 if args.workload == "tcopula" else None
+        c = qm.Copula(L, margins, nu=tnu)
         out = torch.empty(d * n, dtype=torch.float64, device=dev)
         ms = timed(lambda: c.sample(11, 0, out, n, stream=stream), stream, args.steps, args.warmup)
         line.update(value=n / (ms * 1e-3) / 1e9, unit="Gsamples/s (d-dimensional)", ms_per_step=ms,
                     dtype="f64",
-                    config={"workload": f"Gaussian copula d={d}, equicorrelation 0.5, normal/t margins, "
+                    config={"workload": ("t copula nu=4" if tnu else "Gaussian copula") +
+                                        f" d={d}, equicorrelation 0.5, normal/t margins, "
                                         f"n=2^{n.bit_length() - 1} samples, Philox4x32-10 in registers",
                             "values_per_s": d * n / (ms * 1e-3)},
                     roofline={"bound": "alu", "note": "FP64: d normals (fixed point, 1 DFMA each) + "
