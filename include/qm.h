@@ -289,20 +289,24 @@ qm_status qm_copula_destroy(qm_copula* c);
  * qm_tcopula_create: as qm_copula_create plus nu in [QM_T_NU_MIN, QM_T_NU_MAX]
  * (QM_ERR_UNSUPPORTED outside); the handle is sampled and destroyed by
  * qm_copula_sample / qm_copula_destroy.
- * qm_tcopula_table_build (host only, no GPU): the two tables for nu --
- * chi_seg: QM_TC_NZ x 10 coefficients of log W(z) about the centres
- * -QM_TC_Z_MAX + (j + 1/2)/QM_TC_HZ_INV; g_seg: (QM_TC_NA + *nb) x 10
- * (room for QM_TC_NA + QM_TC_NB_MAX) coefficients of G: rows j < QM_TC_NA in
- * t about 0 (j = 0) or (j + 1/2)/QM_TC_HT_INV, rows QM_TC_NA + i in y = log t
- * about ln 2 + (i + 1/2)/QM_TC_HT_INV.                                         */
+ * qm_tcopula_table_build (host only, no GPU): the two tables for nu, rows of
+ * QM_TC_ROW doubles (coefficients 0..9, then one more value) --
+ * chi_seg: QM_TC_NZ rows, log W(z) about the centre c_j = -QM_TC_Z_MAX +
+ * (j + 1/2)/QM_TC_HZ_INV (stored as the row's last value);
+ * g_seg: room for 1 + QM_TC_G_NE_MAX 2^QM_TC_G_K rows, *ne binades used:
+ * row 0 is G(t) about t = 0 (for |t| < 2^QM_TC_G_EMIN); row
+ * 1 + e 2^K + j covers |t| = 2^E m, E = QM_TC_G_EMIN + e, m in
+ * [1 + j 2^-K, 1 + (j+1) 2^-K), as a series in r = m / m_c - 1,
+ * m_c = 1 + (j + 1/2) 2^-K, with 1 / m_c as the row's last value.          */
 #define QM_TC_Z_MAX 8.5
 #define QM_TC_HZ_INV 16
 #define QM_TC_NZ 272
-#define QM_TC_HT_INV 32
-#define QM_TC_NA 64
-#define QM_TC_NB_MAX 2048
+#define QM_TC_ROW 11
+#define QM_TC_G_EMIN (-5)
+#define QM_TC_G_K 5
+#define QM_TC_G_NE_MAX 128
 qm_status qm_tcopula_create(int d, double nu, const double* chol, const qm_margin* margins, qm_copula** out);
-qm_status qm_tcopula_table_build(double nu, double* chi_seg, double* g_seg, int* nb);
+qm_status qm_tcopula_table_build(double nu, double* chi_seg, double* g_seg, int* ne);
 
 /* ---- ragged batches ---------------------------------------------------------
  * A batch is a table of independent recycling jobs evaluated by ONE

@@ -230,21 +230,22 @@ def qm_t_table_build(nu: float):
     return seg, tail
 
 
-QM_TC_Z_MAX, QM_TC_HZ_INV, QM_TC_NZ, QM_TC_HT_INV, QM_TC_NA, QM_TC_NB_MAX = 8.5, 16, 272, 32, 64, 2048
+QM_TC_Z_MAX, QM_TC_HZ_INV, QM_TC_NZ, QM_TC_ROW = 8.5, 16, 272, 11
+QM_TC_G_EMIN, QM_TC_G_K, QM_TC_G_NE_MAX = -5, 5, 128
 
 
 def qm_tcopula_table_build(nu: float):
-    """Host-built t-copula tables (no GPU): (chi, g) -- chi[j, k] coefficient k
-    of log W(z) about -QM_TC_Z_MAX + (j + 1/2)/QM_TC_HZ_INV; g[j, k] of
-    G(t) = Phi^{-1}(F_nu(t)) about 0 (j = 0) or (j + 1/2)/QM_TC_HT_INV for
-    j < QM_TC_NA, in y = log t about ln 2 + (j - QM_TC_NA + 1/2)/QM_TC_HT_INV
-    above."""
+    """Host-built t-copula tables (no GPU): (chi, g), rows of QM_TC_ROW --
+    chi[j, :10] the coefficients of log W(z) about chi[j, 10]; g[0, :10] those
+    of G(t) = Phi^{-1}(F_nu(t)) about 0, g[1 + e 2^K + j, :10] those of G in
+    r = m / m_c - 1 on |t| = 2^(QM_TC_G_EMIN + e) m, with 1 / m_c in
+    g[., 10]."""
     import numpy as np
-    chi = np.zeros((QM_TC_NZ, 10), dtype=np.float64)
-    g = np.zeros((QM_TC_NA + QM_TC_NB_MAX, 10), dtype=np.float64)
-    nb = ctypes.c_int(0)
-    _check(load().qm_tcopula_table_build(float(nu), chi.ctypes.data, g.ctypes.data, ctypes.byref(nb)))
-    return chi, g[: QM_TC_NA + nb.value]
+    chi = np.zeros((QM_TC_NZ, QM_TC_ROW), dtype=np.float64)
+    g = np.zeros((1 + QM_TC_G_NE_MAX * (1 << QM_TC_G_K), QM_TC_ROW), dtype=np.float64)
+    ne = ctypes.c_int(0)
+    _check(load().qm_tcopula_table_build(float(nu), chi.ctypes.data, g.ctypes.data, ctypes.byref(ne)))
+    return chi, g[: 1 + ne.value * (1 << QM_TC_G_K)]
 
 
 QM_HYP_E_MIN, QM_HYP_MAX_BINADES = -30, 64

@@ -46,9 +46,9 @@ struct CopulaDev {
     // t copula
     double inv_sigma[kMaxD];              // 1 / row norms of L
     double half_log_nu;
-    const double* chi;                    // log W(z) segments (QM_TC_NZ x 10)
-    const double* g;                      // G segments ((QM_TC_NA + nb) x 10)
-    int nb;
+    const double* chi;                    // log W(z) rows (QM_TC_NZ)
+    const double* g;                      // G rows (1 + ne 2^QM_TC_G_K)
+    int ne;
     int pad;
 };
 
@@ -63,28 +63,28 @@ __device__ __forceinline__ double seg10(const double* __restrict__ c, double s)
 // log W for the normal score z (|z| <= 8.3 on the 53-bit grid)
 __device__ __forceinline__ double tc_log_w(const double* __restrict__ chi, double z)
 {
-    int j = (int)floor((z + QM_TC_Z_MAX) * QM_TC_HZ_INV);
+    int j = (int)(__fma_rn(z, (double)QM_TC_HZ_INV, QM_TC_Z_MAX * QM_TC_HZ_INV));
     j = min(max(j, 0), QM_TC_NZ - 1);
-    const double s = z - (-QM_TC_Z_MAX + (j + 0.5) * (1.0 / QM_TC_HZ_INV));
-    return seg10(chi + 10 * j, s);
+    const double* row = chi + QM_TC_ROW * j;
+    return seg10(row, z - __ldg(row + 10));
 }
 
-// G(t) = Phi^{-1}(F_nu(t)): segments in |t| below 2, in log|t| above
-__device__ __forceinline__ double tc_g(const double* __restrict__ g, int nb, double t)
+// G(t) = Phi^{-1}(F_nu(t)), no logarithm: |t| = 2^E m selects the row by E
+// and the top QM_TC_G_K bits of m, r = m / m_c - 1 is one FMA; below
+// 2^QM_TC_G_EMIN row 0 is the series about 0 in |t| itself
+__device__ __forceinline__ double tc_g(const double* __restrict__ g, int ne, double t)
 {
     const double a = fabs(t);
-    int row;
-    double s;
-    if (a < 2.0) {
-        row = min((int)(a * QM_TC_HT_INV), QM_TC_NA - 1);
-        s = a - (row == 0 ? 0.0 : (row + 0.5) * (1.0 / QM_TC_HT_INV));
-    } else {
-        const double y = log(a);
-        const int i = min(max((int)((y - 0.69314718055994530942) * QM_TC_HT_INV), 0), nb - 1);
-        s = y - (0.69314718055994530942 + (i + 0.5) * (1.0 / QM_TC_HT_INV));
-        row = QM_TC_NA + i;
-    }
-    return copysign(seg10(g + 10 * row, s), t);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+    const int E = (int)(b >> 52) - 1023;
+    const bool small = E < QM_TC_G_EMIN;
+    const int e = min(E - QM_TC_G_EMIN, ne - 1);
+    const int j = (int)(b >> (52 - QM_TC_G_K)) & ((1 << QM_TC_G_K) - 1);
+    const int row = small ? 0 : 1 + (e << QM_TC_G_K) + j;
+    const double* rp = g + QM_TC_ROW * row;
+    const double m = __longlong_as_double((long long)((b & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull));
+    const double v = small ? a : __fma_rn(m, __ldg(rp + 10), -1.0);
+    return copysign(seg10(rp, v), t);
 }
 
 // normal from two Philox words (53-bit integer, exact reflected grid point,
@@ -184,7 +184,7 @@ k_tcopula(const CopulaDev* __restrict__ cp, PhiloxKeys K, uint64_t blk0, double*
             const double T = y[j] * c.inv_sigma[j] * S;
             double x = T;
             if (c.kind[j] != MARGIN_SAME_T) {
-                x = tc_g(c.g, c.nb, T);
+                x = tc_g(c.g, c.ne, T);
                 if (c.kind[j] == MARGIN_T) x = recycle_t_call(c.t[j], x);
             }
             __stcs(out + (size_t)j * n + i, x);
@@ -316,7 +316,7 @@ extern "C" qm_status qm_tcopula_create(int d, double nu, const double* chol, con
     qm_status st = fill_copula(d, chol, margins, nu, c, "qm_tcopula_create");
     if (st != QM_OK) return st;
     c.host.half_log_nu = 0.5 * std::log(nu);
-    st = tcop_table_device(nu, &c.host.chi, &c.host.g, &c.host.nb);
+    st = tcop_table_device(nu, &c.host.chi, &c.host.g, &c.host.ne);
     if (st != QM_OK) return st;
     return upload(c, out, "qm_tcopula_create");
 }

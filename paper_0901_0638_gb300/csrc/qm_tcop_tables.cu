@@ -14,12 +14,17 @@
 //                    z in [-8.5, 8.5] (every 53-bit grid normal);
 //   t -> normal      G(t) = Phi^{-1}(F_nu(t))  (Student-t base,
 //                    H_0 = (nu+1) t / (nu + t^2); normal target, H_1 = G):
-//                    (nu + t^2) G'' = -(nu+1) t G' + (nu + t^2) G G'^2,
-//                    segments of width 1/32 on t in [0, 2) (segment 0 the odd
-//                    series about 0), then in y = log t, where the ODE reads
+//                    (nu + t^2) G'' = -(nu+1) t G' + (nu + t^2) G G'^2;
+//                    row 0 is its odd series about 0 for |t| < 2^-5 (the
+//                    series converges for |t| < sqrt(nu)); above, |t| =
+//                    2^E m, m in [1, 2), is split by its exponent and the top
+//                    5 bits of m into segments of relative width 1/32, and
+//                    each row holds G as a series in r = m / m_c - 1 about
+//                    the segment centre m_c: the ODE in y = log t,
 //                    (nu + e^{2y}) G_yy = nu (1 - e^{2y}) G_y + (nu + e^{2y}) G G_y^2,
-//                    with segments of width 1/32 up to the largest |T| the
-//                    sampler can produce for this nu.
+//                    gives G's series in y, composed with y = y_c + log(1 + r).
+//                    The device thus needs no logarithm: exponent and mantissa
+//                    bits select the row, one FMA forms r.
 //
 // Each segment's expansion is computed at its centre c from the value and the
 // slope there (Q(c) by inverting the special function in long double, Q'(c)
@@ -44,6 +49,8 @@ constexpr LD kLnSqrt2Pi = 0.91893853320467274178032973640561764L;
 constexpr LD kLn2 = 0.69314718055994530941723212145817657L;
 constexpr int DI = 18;   // working degree of the local series
 constexpr int DO = 9;    // stored degree
+constexpr int RW = 11;   // doubles per row: DO + 1 coefficients, then the centre
+                         // (log W rows) or 1 / m_c (G rows)
 
 // ---- special functions, long double -------------------------------------
 
@@ -289,6 +296,19 @@ Ser taylor_g_y(LD nu, LD c, LD g0, LD g1)
     return b;
 }
 
+// G's series in r from its series in y about y_c: y - y_c = log(1 + r)
+Ser compose_log1p(const Ser& gy)
+{
+    Ser L(DI + 1, 0.0L), P(DI + 1, 0.0L), out(DI + 1, 0.0L);
+    for (int k = 1; k <= DI; ++k) L[k] = ((k & 1) ? 1.0L : -1.0L) / k;     // log(1 + r)
+    P[0] = 1.0L;                                                           // L^0
+    for (int k = 0; k <= DI; ++k) {
+        for (int i = 0; i <= DI; ++i) out[i] += gy[k] * P[i];
+        P = smul(P, L);
+    }
+    return out;
+}
+
 LD hornerl(const Ser& b, int D, LD s)
 {
     LD r = b[D];
@@ -299,7 +319,7 @@ LD hornerl(const Ser& b, int D, LD s)
 }  // namespace
 
 // Tables for nu in host memory (layout in qm.h, qm_tcopula_table_build).
-qm_status tcop_table_build(double nu_d, double* chi_seg, double* g_seg, int* nb_out)
+qm_status tcop_table_build(double nu_d, double* chi_seg, double* g_seg, int* ne_out)
 {
     if (!(nu_d >= QM_T_NU_MIN && nu_d <= QM_T_NU_MAX))
         return fail(QM_ERR_UNSUPPORTED, "t copula: nu = %g outside [%g, %g]", nu_d, QM_T_NU_MIN, QM_T_NU_MAX);
@@ -323,7 +343,8 @@ qm_status tcop_table_build(double nu_d, double* chi_seg, double* g_seg, int* nb_
             const LD err = std::fabs(hornerl(L, DO, e * hz / 2) - logw(c + e * hz / 2));
             worst = std::fmax(worst, err);
         }
-        for (int q = 0; q <= DO; ++q) chi_seg[(DO + 1) * j + q] = (double)L[q];
+        for (int q = 0; q <= DO; ++q) chi_seg[RW * j + q] = (double)L[q];
+        chi_seg[RW * j + DO + 1] = (double)c;
     }
     if (!(worst < 1e-13L))
         return fail(QM_ERR_INVALID, "t copula: chi-squared table check failed for nu = %g (%Lg)", nu_d, worst);
@@ -331,50 +352,45 @@ qm_status tcop_table_build(double nu_d, double* chi_seg, double* g_seg, int* nb_
     // largest |T| the sampler can produce: |y_j| / sigma_j <= |eps| <= 8.3 sqrt(16)
     // times S = sqrt(nu / W) at the smallest grid normal
     const LD smax = std::exp(0.5L * (std::log(nu) - logw(-8.3L)));
-    const LD ymax = std::log(8.3L * 4.0L * smax) + 0.5L;
-    const LD ht = 1.0L / QM_TC_HT_INV, ln2 = kLn2;
-    int nb = (int)std::ceil((ymax - ln2) * QM_TC_HT_INV);
-    if (nb < 1) nb = 1;
-    if (nb > QM_TC_NB_MAX)
-        return fail(QM_ERR_UNSUPPORTED, "t copula: nu = %g needs %d log-segments (max %d)", nu_d, nb, QM_TC_NB_MAX);
+    const int emax = (int)std::floor(std::log2(8.3L * 4.0L * smax)) + 1;        // last binade, inclusive
+    const int ne = emax - QM_TC_G_EMIN + 1;
+    if (ne > QM_TC_G_NE_MAX)
+        return fail(QM_ERR_UNSUPPORTED, "t copula: nu = %g needs %d binades (max %d)", nu_d, ne, QM_TC_G_NE_MAX);
 
-    // ---- t -> normal: t in [0, 2), then y = log t --------------------------
+    // ---- t -> normal: row 0 about t = 0, then 32 segments per binade -------
     const LD lft0 = std::lgamma((nu + 1) / 2) - lgk - 0.5L * std::log(nu * kPi);   // log f_nu(0)
     auto logft = [&](LD t) { return lft0 - (nu + 1) / 2 * std::log1p(t * t / nu); };
+    const int nseg = 1 << QM_TC_G_K;
     worst = 0.0L;
-    for (int j = 0; j < QM_TC_NA + nb; ++j) {
-        Ser b;
-        LD lo, hi;
-        if (j < QM_TC_NA) {
-            const LD c = j == 0 ? 0.0L : (j + 0.5L) * ht;
-            const LD g0 = j == 0 ? 0.0L : t_to_normal(nu, c);
-            const LD g1 = std::exp(logft(c) + g0 * g0 / 2 + kLnSqrt2Pi);             // f_nu / phi(G)
-            b = taylor_g_t(nu, c, g0, g1);
-            lo = j * ht - c;
-            hi = (j + 1) * ht - c;
-            for (LD s : {lo, hi}) {
-                if (c + s == 0) continue;
-                const LD ref = t_to_normal(nu, c + s);
-                worst = std::fmax(worst, std::fabs(hornerl(b, DO, s) / ref - 1));
-            }
-        } else {
-            const int i = j - QM_TC_NA;
-            const LD c = ln2 + (i + 0.5L) * ht;
-            const LD t = std::exp(c), g0 = t_to_normal(nu, t);
+    {
+        const Ser b = taylor_g_t(nu, 0.0L, 0.0L, std::exp(lft0 + kLnSqrt2Pi));  // G'(0) = f_nu(0) / phi(0)
+        for (LD t : {std::ldexp(1.0L, QM_TC_G_EMIN), std::ldexp(0.75L, QM_TC_G_EMIN), 1e-3L})
+            worst = std::fmax(worst, std::fabs(hornerl(b, DO, t) / t_to_normal(nu, t) - 1));
+        for (int q = 0; q <= DO; ++q) g_seg[q] = (double)b[q];
+        g_seg[DO + 1] = 0.0;
+    }
+    for (int e = 0; e < ne; ++e) {
+        const int E = QM_TC_G_EMIN + e;
+        for (int j = 0; j < nseg; ++j) {
+            const LD mc = 1.0L + (j + 0.5L) / nseg;
+            const LD yc = E * kLn2 + std::log(mc);
+            const LD t = std::exp(yc), g0 = t_to_normal(nu, t);
             const LD g1 = t * std::exp(logft(t) + g0 * g0 / 2 + kLnSqrt2Pi);         // dG/dy = t G'
-            b = taylor_g_y(nu, c, g0, g1);
-            for (LD s : {-ht / 2, ht / 2}) {
-                const LD ref = t_to_normal(nu, std::exp(c + s));
-                worst = std::fmax(worst, std::fabs(hornerl(b, DO, s) / ref - 1));
+            const Ser b = compose_log1p(taylor_g_y(nu, yc, g0, g1));
+            if (!std::isfinite(b[DI]))
+                return fail(QM_ERR_INVALID, "t copula: t -> normal series overflow for nu = %g", nu_d);
+            for (LD m : {1.0L + (LD)j / nseg, 1.0L + (j + 1.0L) / nseg}) {
+                const LD ref = t_to_normal(nu, std::ldexp(m, E));
+                worst = std::fmax(worst, std::fabs(hornerl(b, DO, m / mc - 1) / ref - 1));
             }
+            double* row = g_seg + RW * (1 + e * nseg + j);
+            for (int q = 0; q <= DO; ++q) row[q] = (double)b[q];
+            row[DO + 1] = (double)(1.0L / mc);
         }
-        if (!std::isfinite(b[DI]))
-            return fail(QM_ERR_INVALID, "t copula: t -> normal series overflow for nu = %g", nu_d);
-        for (int q = 0; q <= DO; ++q) g_seg[(DO + 1) * j + q] = (double)b[q];
     }
     if (!(worst < 1e-13L))
         return fail(QM_ERR_INVALID, "t copula: t -> normal table check failed for nu = %g (%Lg)", nu_d, worst);
-    *nb_out = nb;
+    *ne_out = ne;
     return QM_OK;
 }
 
@@ -383,9 +399,9 @@ namespace {
 struct TcEntry {
     int device;
     double nu;
-    double* chi;   // device, QM_TC_NZ x 10
-    double* g;     // device, (QM_TC_NA + nb) x 10
-    int nb;
+    double* chi;   // device, QM_TC_NZ rows
+    double* g;     // device, 1 + ne 2^QM_TC_G_K rows
+    int ne;
 };
 
 std::mutex g_tc_mu;
@@ -396,7 +412,7 @@ constexpr size_t kTcMax = 256;
 
 // Device tables for nu on the current device, built and uploaded at first use
 // (kept until the process exits).
-qm_status tcop_table_device(double nu, const double** chi, const double** g, int* nb)
+qm_status tcop_table_device(double nu, const double** chi, const double** g, int* ne)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return fail(QM_ERR_CUDA, "t copula: no current device");
@@ -405,16 +421,16 @@ qm_status tcop_table_device(double nu, const double** chi, const double** g, int
         if (e.device == dev && e.nu == nu) {
             *chi = e.chi;
             *g = e.g;
-            *nb = e.nb;
+            *ne = e.ne;
             return QM_OK;
         }
     if (g_tc_cache.size() >= kTcMax) return fail(QM_ERR_NOMEM, "t copula: more than %zu distinct nu in use", kTcMax);
-    std::vector<double> hc(10 * QM_TC_NZ), hg(10 * (QM_TC_NA + QM_TC_NB_MAX));
+    std::vector<double> hc(RW * QM_TC_NZ), hg(RW * (1 + QM_TC_G_NE_MAX * (1 << QM_TC_G_K)));
     int n = 0;
     const qm_status st = tcop_table_build(nu, hc.data(), hg.data(), &n);
     if (st != QM_OK) return st;
     TcEntry e{dev, nu, nullptr, nullptr, n};
-    const size_t gbytes = sizeof(double) * 10 * (QM_TC_NA + n);
+    const size_t gbytes = sizeof(double) * RW * (1 + n * (1 << QM_TC_G_K));
     if (cudaMalloc(&e.chi, sizeof(double) * hc.size()) != cudaSuccess || cudaMalloc(&e.g, gbytes) != cudaSuccess) {
         if (e.chi) cudaFree(e.chi);
         return fail(QM_ERR_NOMEM, "t copula: table allocation failed");
@@ -428,14 +444,14 @@ qm_status tcop_table_device(double nu, const double** chi, const double** g, int
     g_tc_cache.push_back(e);
     *chi = e.chi;
     *g = e.g;
-    *nb = e.nb;
+    *ne = e.ne;
     return QM_OK;
 }
 
 }  // namespace qm
 
-extern "C" qm_status qm_tcopula_table_build(double nu, double* chi_seg, double* g_seg, int* nb)
+extern "C" qm_status qm_tcopula_table_build(double nu, double* chi_seg, double* g_seg, int* ne)
 {
-    if (!chi_seg || !g_seg || !nb) return qm::fail(QM_ERR_INVALID, "qm_tcopula_table_build: null argument");
-    return qm::tcop_table_build(nu, chi_seg, g_seg, nb);
+    if (!chi_seg || !g_seg || !ne) return qm::fail(QM_ERR_INVALID, "qm_tcopula_table_build: null argument");
+    return qm::tcop_table_build(nu, chi_seg, g_seg, ne);
 }

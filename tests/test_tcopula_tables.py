@@ -19,32 +19,32 @@ NUS = [0.75, 1.0, 2.0, 3.3, 4.0, 30.0, 100.0]
 
 
 def eval_log_w(chi, z):
-    j = np.clip(np.floor((z + qm.QM_TC_Z_MAX) * qm.QM_TC_HZ_INV).astype(int), 0, qm.QM_TC_NZ - 1)
-    s = z - (-qm.QM_TC_Z_MAX + (j + 0.5) / qm.QM_TC_HZ_INV)
-    c = chi[j]
-    acc = c[:, 9].copy()
+    j = np.clip(np.trunc(z * qm.QM_TC_HZ_INV + qm.QM_TC_Z_MAX * qm.QM_TC_HZ_INV).astype(int), 0, qm.QM_TC_NZ - 1)
+    row = chi[j]
+    s = z - row[:, 10]
+    acc = row[:, 9].copy()
     for k in range(8, -1, -1):
-        acc = acc * s + c[:, k]
+        acc = acc * s + row[:, k]
     return acc
 
 
 def eval_g(g, t):
-    nb = g.shape[0] - qm.QM_TC_NA
+    """The device's evaluation: exponent and top mantissa bits select the row
+    (row 0 below 2^QM_TC_G_EMIN), r = m / m_c - 1 with 1/m_c from the row."""
+    ne = (g.shape[0] - 1) >> qm.QM_TC_G_K
     a = np.abs(t)
-    small = a < 2.0
-    row = np.empty(a.shape, dtype=int)
-    s = np.empty_like(a)
-    j = np.minimum((a[small] * qm.QM_TC_HT_INV).astype(int), qm.QM_TC_NA - 1)
-    row[small] = j
-    s[small] = a[small] - np.where(j == 0, 0.0, (j + 0.5) / qm.QM_TC_HT_INV)
-    y = np.log(a[~small])
-    i = np.clip(((y - math.log(2)) * qm.QM_TC_HT_INV).astype(int), 0, nb - 1)
-    row[~small] = qm.QM_TC_NA + i
-    s[~small] = y - (math.log(2) + (i + 0.5) / qm.QM_TC_HT_INV)
-    c = g[row]
-    acc = c[:, 9].copy()
+    m, E = np.frexp(a)                           # a = m 2^E, m in [0.5, 1)
+    E = np.where(a == 0, -1075, E - 1)
+    m = m * 2.0                                  # m in [1, 2)
+    small = E < qm.QM_TC_G_EMIN
+    e = np.minimum(E - qm.QM_TC_G_EMIN, ne - 1)
+    j = np.floor((m - 1.0) * (1 << qm.QM_TC_G_K)).astype(int)
+    row = np.where(small, 0, 1 + (e << qm.QM_TC_G_K) + j)
+    rp = g[row]
+    v = np.where(small, a, m * rp[:, 10] - 1.0)
+    acc = rp[:, 9].copy()
     for k in range(8, -1, -1):
-        acc = acc * s + c[:, k]
+        acc = acc * v + rp[:, k]
     return np.copysign(acc, t)
 
 
@@ -62,14 +62,15 @@ def test_mixing_table_against_the_oracle(nu):
 @pytest.mark.parametrize("nu", NUS)
 def test_t_to_normal_table_against_the_oracle(nu):
     chi, g = qm.qm_tcopula_table_build(nu)
-    nb = g.shape[0] - qm.QM_TC_NA
-    tmax = math.exp(math.log(2) + nb / qm.QM_TC_HT_INV)
+    ne = (g.shape[0] - 1) >> qm.QM_TC_G_K
+    tmax = 2.0 ** (qm.QM_TC_G_EMIN + ne)
     # the largest |T| of the sampler: 8.3 * 4 * sqrt(nu / W(-8.3)) (< tmax)
     smax = math.sqrt(nu / oracle.chi2_from_normal(nu, np.array([-8.3]))[0])
     assert 33.2 * smax < tmax
     rng = np.random.default_rng(int(nu * 10))
-    t = np.concatenate([rng.uniform(0, 2, 2000), np.exp(rng.uniform(math.log(2), math.log(33.2 * smax), 3000)),
-                        np.linspace(0, 2.2, 300), [1e-12, 1e-6, 2.0, 33.2 * smax]])
+    t = np.concatenate([rng.uniform(0, 2, 2000), np.exp(rng.uniform(math.log(1e-3), math.log(33.2 * smax), 3000)),
+                        np.linspace(0, 2.2, 300), [1e-12, 1e-6, 2.0**-5, 2.0**-5 * (1 - 2**-52), 2.0, 33.2 * smax],
+                        2.0 ** np.arange(-5, int(math.log2(33.2 * smax)))])
     t = np.concatenate([t, -t[::7]])
     got = eval_g(g, t)
     ref = oracle.t_to_normal(nu, t)
