@@ -29,12 +29,9 @@
 namespace qm {
 namespace fxt {
 
-constexpr int K_MAIN = 6;
-constexpr int E_MAIN = 64;
-constexpr int K_DEEP = 5;
-constexpr int E_LAST = 1072;
-constexpr int N_MAIN = 4096;
-constexpr int N_ALL = 36384;
+constexpr int K = 6;           // 64 segments in every binade
+constexpr int E_LAST = 1072;   // binades e = -1 - E = 0 .. 1072 (x down to 2^-1073)
+constexpr int N_ALL = (E_LAST + 1) << K;
 
 // a0, B0 = beta_0 2^-s0, B1 = beta_1 2^-s0, and B2 = beta_2 2^-s0 in the low
 // 52 bits (sign extended) with s0 in the top 12
@@ -117,19 +114,19 @@ template <int MIX = FX_INT_LEAN>
 __device__ __forceinline__ unsigned long long probit_mag_fx_sx(const fxt::FxTable* T, unsigned long long S,
                                                              int base)
 {
+    constexpr int K = fxt::K, sK = 52 - K;
     const int lz = __clzll(S | 1ull) - 11;
     const unsigned long long Mx = S << lz;                      // 2^52 <= Mx < 2^53
     const int e = -1 - (base - lz);                             // binade: x in [2^-e-1, 2^-e)
     const int ec = min(max(e, 0), fxt::E_LAST);
-    const bool mainb = ec < fxt::E_MAIN;
-    const int K = mainb ? fxt::K_MAIN : fxt::K_DEEP;
-    const int sK = 52 - K;
     const unsigned j = (unsigned)(Mx >> sK) & ((1u << K) - 1u);
-    const int idx = mainb ? (ec << fxt::K_MAIN) + (int)j
-                          : fxt::N_MAIN + ((ec - fxt::E_MAIN) << fxt::K_DEEP) + (int)j;
+    const int idx = (ec << K) + (int)j;
     // offset back from the segment end: Tu in [1, 2^sK]
     const unsigned long long Tu = (1ull << sK) - (Mx & ((1ull << sK) - 1ull));
-    const unsigned long long Tau = (Tu << (12 + K)) - (Tu >> sK);   // tau 2^64 (tau = 1 -> 1 - 2^-64)
+    // tau 2^64, with tau = 1 (Tu = 2^sK) mapped to 2^64 - 1; written without a
+    // shift that overflows 64 bits
+    const unsigned long long top = Tu >> sK;                        // 1 iff tau = 1
+    const unsigned long long Tau = ((Tu - top) << (12 + K)) | (0ull - top);
 
     unsigned long long a0b, B0, B1, B2s;
     ld256(&T->a[idx], a0b, B0, B1, B2s);                           // a0, B0, B1, B2 | s0

@@ -29,9 +29,9 @@ as acc_3 = rn(F) (float -> int64, round to nearest even); then
 z = fma(t_u, acc_0 2^s0, a_0), with t_u = (1 + t_u) - 1 formed exactly by one
 double-precision add.
 
-Binades: e = -1 - E in [0, 64) with K = 6, e in [64, 1072] with K = 5, so
-every double 0 < u < 1 (subnormal u included: x is normalised as an
-integer) falls in a segment.
+Binades: e = -1 - E in [0, 1072], 64 segments each (K = 6), so every
+double 0 < u < 1 (subnormal u included: x is normalised as an integer)
+falls in a segment.
 
 Entry: two arrays, so that a lane gathers 48 bytes with one 256-bit and one
 128-bit load: A[i] = {a0 (double), B0, B1 (int64), B2 | s0 << 52} (32 bytes;
@@ -64,7 +64,8 @@ OUT = os.path.join(os.path.dirname(HERE), "csrc", "qm_fx_tables.h")
 DEG = 7                 # a_0..a_7
 NI = 3                  # beta_0..beta_2 in fixed point
 K_MAIN, E_MAIN = 6, 64  # binade index e = -1 - E in [0, 64): K = 6
-K_DEEP, E_LAST = 5, 1072  # e in [64, 1072]: K = 5 (x down to 2^-1073)
+K_DEEP, E_LAST = 6, 1072  # e in [64, 1072]: K = 6 too (x down to 2^-1073); one K
+                          # everywhere makes every shift of the kernel a constant
 N_MAIN = E_MAIN << K_MAIN
 N_ALL = N_MAIN + ((E_LAST - E_MAIN + 1) << K_DEEP)
 
@@ -203,10 +204,9 @@ def main():
         "// G = a0 + t_u H, H = sum beta_k tau^k > 0, tau = (m_end - m) 2^K in (0, 1],\n",
         "// beta_0..2 as int64 B_k = beta_k 2^-s0 (A: a0, B0, B1, B2 | s0 << 52),\n",
         "// beta_3..6 as float f_k = beta_k 2^-s0 (F).\n",
-        f"// Binade e = -1 - E: K = {K_MAIN} for e < {E_MAIN}, K = {K_DEEP} for e = {E_MAIN}..{E_LAST}.\n",
-        f"// Index e 2^{K_MAIN} + j (e < {E_MAIN}), {N_MAIN} + (e - {E_MAIN}) 2^{K_DEEP} + j.\n",
+        f"// Binade e = -1 - E = 0..{E_LAST}, {2**K_MAIN} segments each; index e 2^{K_MAIN} + j.\n",
         f"// Emulated worst relative error over the checked points: {worst:.3g}.\n",
-        "#pragma once\n#include \"qm_fx.cuh\"   // layout (K_MAIN .. N_ALL, FxTable) and evaluation\n\n",
+        "#pragma once\n#include \"qm_fx.cuh\"   // layout (K, E_LAST, N_ALL, FxTable) and evaluation\n\n",
         "namespace qm {\nnamespace fxt {\n\n",
         "__device__ const FxTable SEG_FX = {\n {\n",
     ]

@@ -226,11 +226,11 @@ def test_f64_symmetry_bit_exact():
 
 def test_f64_fixed_every_segment():
     """Every segment of the fixed-point table (x = 2d = M 2^(E-52), binades
-    E = -1..-1073, 64 or 32 segments each) at its start, start + 1 ulp,
+    E = -1..-1073, 64 segments each) at its start, start + 1 ulp,
     centre and last point, for u = d and, where 1 - d is exact, u = 1 - d."""
     ms, es = [], []
     for e in range(0, 1073):
-        K = 6 if e < 64 else 5
+        K = 6
         j = np.arange(2**K, dtype=np.int64)
         lo = 2**52 + j * 2**(52 - K)
         for off in (0, 1, 2**(51 - K), 2**(52 - K) - 1):
