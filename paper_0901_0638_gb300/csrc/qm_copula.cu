@@ -37,6 +37,8 @@ constexpr int kMaxD = QM_COPULA_MAX_DIM;
 
 enum { MARGIN_NORMAL = 0, MARGIN_T = 1, MARGIN_SAME_T = 2 };
 
+static_assert(sizeof(ttbl::SegT) == 64, "t-copula rows share the Student-t segment layout");
+
 struct CopulaDev {
     int d;
     int tcop;                             // 0: Gaussian copula, 1: t copula
@@ -46,45 +48,37 @@ struct CopulaDev {
     // t copula
     double inv_sigma[kMaxD];              // 1 / row norms of L
     double half_log_nu;
-    const double* chi;                    // log W(z) rows (QM_TC_NZ)
-    const double* g;                      // G rows (1 + ne 2^QM_TC_G_K)
+    const ttbl::SegT* chi;                // log W(z) rows (QM_TC_NZ)
+    const double* chi_c;                  //   and their centres
+    const ttbl::SegT* g;                  // G rows (1 + ne 2^QM_TC_G_K)
+    const double* g_c;                    //   and their 1 / m_c (row 0: unused)
     int ne;
     int pad;
 };
 
-__device__ __forceinline__ double seg10(const double* __restrict__ c, double s)
-{
-    double r = __ldg(c + 9);
-#pragma unroll
-    for (int k = 8; k >= 0; --k) r = __fma_rn(r, s, __ldg(c + k));
-    return r;
-}
-
 // log W for the normal score z (|z| <= 8.3 on the 53-bit grid)
-__device__ __forceinline__ double tc_log_w(const double* __restrict__ chi, double z)
+__device__ __forceinline__ double tc_log_w(const CopulaDev& c, double z)
 {
     int j = (int)(__fma_rn(z, (double)QM_TC_HZ_INV, QM_TC_Z_MAX * QM_TC_HZ_INV));
     j = min(max(j, 0), QM_TC_NZ - 1);
-    const double* row = chi + QM_TC_ROW * j;
-    return seg10(row, z - __ldg(row + 10));
+    return seg_poly(c.chi[j], z - __ldg(c.chi_c + j));
 }
 
 // G(t) = Phi^{-1}(F_nu(t)), no logarithm: |t| = 2^E m selects the row by E
 // and the top QM_TC_G_K bits of m, r = m / m_c - 1 is one FMA; below
 // 2^QM_TC_G_EMIN row 0 is the series about 0 in |t| itself
-__device__ __forceinline__ double tc_g(const double* __restrict__ g, int ne, double t)
+__device__ __forceinline__ double tc_g(const CopulaDev& c, double t)
 {
     const double a = fabs(t);
     const unsigned long long b = (unsigned long long)__double_as_longlong(a);
     const int E = (int)(b >> 52) - 1023;
     const bool small = E < QM_TC_G_EMIN;
-    const int e = min(E - QM_TC_G_EMIN, ne - 1);
+    const int e = min(E - QM_TC_G_EMIN, c.ne - 1);
     const int j = (int)(b >> (52 - QM_TC_G_K)) & ((1 << QM_TC_G_K) - 1);
     const int row = small ? 0 : 1 + (e << QM_TC_G_K) + j;
-    const double* rp = g + QM_TC_ROW * row;
     const double m = __longlong_as_double((long long)((b & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull));
-    const double v = small ? a : __fma_rn(m, __ldg(rp + 10), -1.0);
-    return copysign(seg10(rp, v), t);
+    const double v = small ? a : __fma_rn(m, __ldg(c.g_c + row), -1.0);
+    return copysign(seg_poly(c.g[row], v), t);
 }
 
 // normal from two Philox words (53-bit integer, exact reflected grid point,
@@ -178,13 +172,13 @@ k_tcopula(const CopulaDev* __restrict__ cp, PhiloxKeys K, uint64_t blk0, double*
                 }
             }
         }
-        const double S = exp(c.half_log_nu - 0.5 * tc_log_w(c.chi, zw));    // sqrt(nu / W)
+        const double S = exp(c.half_log_nu - 0.5 * tc_log_w(c, zw));       // sqrt(nu / W)
 #pragma unroll
         for (int j = 0; j < D; ++j) {
             const double T = y[j] * c.inv_sigma[j] * S;
             double x = T;
             if (c.kind[j] != MARGIN_SAME_T) {
-                x = tc_g(c.g, c.ne, T);
+                x = tc_g(c, T);
                 if (c.kind[j] == MARGIN_T) x = recycle_t_call(c.t[j], x);
             }
             __stcs(out + (size_t)j * n + i, x);
@@ -316,8 +310,14 @@ extern "C" qm_status qm_tcopula_create(int d, double nu, const double* chol, con
     qm_status st = fill_copula(d, chol, margins, nu, c, "qm_tcopula_create");
     if (st != QM_OK) return st;
     c.host.half_log_nu = 0.5 * std::log(nu);
-    st = tcop_table_device(nu, &c.host.chi, &c.host.g, &c.host.ne);
+    const void* chi = nullptr;
+    const void* g = nullptr;
+    st = tcop_table_device(nu, &chi, &g, &c.host.ne);
     if (st != QM_OK) return st;
+    c.host.chi = static_cast<const ttbl::SegT*>(chi);
+    c.host.chi_c = reinterpret_cast<const double*>(c.host.chi + QM_TC_NZ);
+    c.host.g = static_cast<const ttbl::SegT*>(g);
+    c.host.g_c = reinterpret_cast<const double*>(c.host.g + 1 + (c.host.ne << QM_TC_G_K));
     return upload(c, out, "qm_tcopula_create");
 }
 

@@ -396,11 +396,21 @@ qm_status tcop_table_build(double nu_d, double* chi_seg, double* g_seg, int* ne_
 
 namespace {
 
+// Device row: coefficients 0..4 in double, 5..9 in single precision (their
+// rounding stays below 2e-15 relative on every row), the layout of the
+// Student-t segments, so the same mixed evaluation serves both.
+struct PackedRow {
+    double a[5];
+    float b[5];
+    float pad;
+};
+static_assert(sizeof(PackedRow) == 64, "packed row layout");
+
 struct TcEntry {
     int device;
     double nu;
-    double* chi;   // device, QM_TC_NZ rows
-    double* g;     // device, 1 + ne 2^QM_TC_G_K rows
+    void* chi;     // device: QM_TC_NZ packed rows, then QM_TC_NZ centres
+    void* g;       // device: 1 + ne 2^QM_TC_G_K packed rows, then as many 1 / m_c
     int ne;
 };
 
@@ -408,11 +418,28 @@ std::mutex g_tc_mu;
 std::vector<TcEntry> g_tc_cache;
 constexpr size_t kTcMax = 256;
 
+// host rows of RW doubles -> packed rows followed by the rows' last values
+std::vector<unsigned char> pack_rows(const double* rows, int n)
+{
+    std::vector<unsigned char> buf((sizeof(PackedRow) + sizeof(double)) * (size_t)n);
+    PackedRow* pr = reinterpret_cast<PackedRow*>(buf.data());
+    double* last = reinterpret_cast<double*>(buf.data() + sizeof(PackedRow) * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        const double* r = rows + (size_t)RW * i;
+        for (int k = 0; k < 5; ++k) pr[i].a[k] = r[k];
+        for (int k = 0; k < 5; ++k) pr[i].b[k] = (float)r[5 + k];
+        pr[i].pad = 0.0f;
+        last[i] = r[DO + 1];
+    }
+    return buf;
+}
+
 }  // namespace
 
 // Device tables for nu on the current device, built and uploaded at first use
-// (kept until the process exits).
-qm_status tcop_table_device(double nu, const double** chi, const double** g, int* ne)
+// (kept until the process exits): packed rows, then the rows' centres (log W)
+// or 1 / m_c (G).
+qm_status tcop_table_device(double nu, const void** chi, const void** g, int* ne)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return fail(QM_ERR_CUDA, "t copula: no current device");
@@ -429,14 +456,15 @@ qm_status tcop_table_device(double nu, const double** chi, const double** g, int
     int n = 0;
     const qm_status st = tcop_table_build(nu, hc.data(), hg.data(), &n);
     if (st != QM_OK) return st;
+    const std::vector<unsigned char> pc = pack_rows(hc.data(), QM_TC_NZ);
+    const std::vector<unsigned char> pg = pack_rows(hg.data(), 1 + n * (1 << QM_TC_G_K));
     TcEntry e{dev, nu, nullptr, nullptr, n};
-    const size_t gbytes = sizeof(double) * RW * (1 + n * (1 << QM_TC_G_K));
-    if (cudaMalloc(&e.chi, sizeof(double) * hc.size()) != cudaSuccess || cudaMalloc(&e.g, gbytes) != cudaSuccess) {
+    if (cudaMalloc(&e.chi, pc.size()) != cudaSuccess || cudaMalloc(&e.g, pg.size()) != cudaSuccess) {
         if (e.chi) cudaFree(e.chi);
         return fail(QM_ERR_NOMEM, "t copula: table allocation failed");
     }
-    if (cudaMemcpy(e.chi, hc.data(), sizeof(double) * hc.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(e.g, hg.data(), gbytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (cudaMemcpy(e.chi, pc.data(), pc.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(e.g, pg.data(), pg.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaFree(e.chi);
         cudaFree(e.g);
         return fail(QM_ERR_CUDA, "t copula: table upload failed");
