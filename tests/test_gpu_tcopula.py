@@ -112,3 +112,38 @@ def test_tcopula_argument_errors():
     with pytest.raises(qm.QMError) as e:
         qm.Copula(np.eye(2), [(qm.QM_DIST_EXPONENTIAL, 0.0)] * 2, nu=4.0)
     assert e.value.status == qm.QM_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("d,n", [(1, 1), (1, 257), (16, 3), (16, 1025), (7, 130)])
+def test_copulas_dimensions_and_ragged_counts(d, n):
+    """The degenerate dimension 1 and the maximum 16, ragged sample counts,
+    a nonzero counter base: both copulas element by element, and nothing
+    written past the d n outputs."""
+    rng = np.random.default_rng(d * 1000 + n)
+    A = rng.normal(size=(d, d))
+    L = np.linalg.cholesky(A @ A.T + d * np.eye(d))
+    kinds = [(qm.QM_DIST_NORMAL, 0.0), (qm.QM_DIST_STUDENT_T, 3.0), (qm.QM_DIST_STUDENT_T, 5.5)]
+    margins = [kinds[j % 3] for j in range(d)]
+    key, ctr0 = 77, 4 * 12345
+    for nu in (None, 3.0):
+        c = qm.Copula(L, margins, nu=nu)
+        out = torch.full((d * n + 8,), 7.0, dtype=torch.float64, device=DEV)
+        c.sample(key, ctr0, out, n)
+        torch.cuda.synchronize()
+        c.close()
+        o = out.cpu().numpy()
+        assert np.all(o[d * n:] == 7.0)
+        x = o[: d * n].reshape(d, n).T
+        if nu is None:
+            e = grid_normals(key, ctr0, n, d)
+            y = e @ L.T
+            ref = np.stack([oracle.recycle_t(mu, y[:, j]) if k == qm.QM_DIST_STUDENT_T else y[:, j]
+                            for j, (k, mu) in enumerate(margins)], axis=1)
+            scale = np.abs(e) @ np.abs(L).T
+            T = y
+        else:
+            ref, T, scale = reference(L, margins, nu, key, ctr0, n)
+        for j in range(d):
+            gain = np.abs(ref[:, j] / np.where(T[:, j] == 0, 1, T[:, j]))
+            tol = 1e-12 * np.abs(ref[:, j]) + 1e-15 * scale[:, j] * np.maximum(gain, 1.0)
+            assert np.all(np.abs(x[:, j] - ref[:, j]) <= tol), (nu, j)
