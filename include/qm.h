@@ -256,9 +256,10 @@ qm_status qm_hyp_table_build(double alpha, double beta, double delta, double* se
  * Student t with nu_j (QM_DIST_STUDENT_T; tabulated or run-time tables as in
  * qm_recycle).
  * qm_copula_create: chol = host d x d row-major lower-triangular Cholesky
- * factor with positive diagonal (1 <= d <= QM_COPULA_MAX_DIM), margins = host
- * array of d; copies both to the device (one cudaMalloc, owned by the
- * handle).  Errors: bad d, non-finite or non-lower-triangular L, L[j][j] <= 0:
+ * factor with positive diagonal (1 <= d <= QM_COPULA_MAX_DIM) of a
+ * correlation or covariance matrix (rows are divided by their norms: the
+ * copula is that of the correlation), margins = host array of d; copies both
+ * to the device (one cudaMalloc, owned by the handle).  Errors: bad d, non-finite or non-lower-triangular L, L[j][j] <= 0:
  * QM_ERR_INVALID; other margin kinds or out-of-range nu: QM_ERR_UNSUPPORTED.
  * qm_copula_sample: out = device double[d n], column-major (x_j of sample i
  * at out[j n + i]); ctr0 a multiple of 4.                                    */
@@ -276,8 +277,7 @@ qm_status qm_copula_destroy(qm_copula* c);
 /* ---- t copula (Sec. 9) ------------------------------------------------------
  * x_j = F_j^{-1}(F_nu(T_j)), T = (L eps) / sigma * sqrt(nu / W): eps iid
  * normal, W ~ chi-squared(nu) shared by the coordinates of a sample, sigma_j
- * the row norms of L (so that L L^T may be a covariance; the copula is that of
- * its correlation).  The paper's folding (Sec. 9): W comes from one more
+ * the row norms of L (as for qm_copula_create).  The paper's folding (Sec. 9): W comes from one more
  * grid normal through the normal -> chi-squared recycling map, and each
  * coordinate goes straight to its margin: a Student-t margin with the
  * copula's nu is T_j itself, a normal margin is G(T_j) = Phi^{-1}(F_nu(T_j))

@@ -7,7 +7,8 @@
 //     eps_k = Phi^{-1}((m_k + 1/2) 2^-53),  m_k a 53-bit Philox integer
 //             (two per Philox block, as the fused FP64 normal sampler;
 //             fixed-point FP64 evaluation, one FP64 FMA),
-//     y = L eps                              (L lower triangular, d <= 16),
+//     y = L eps / sigma                      (L lower triangular, d <= 16,
+//                                             sigma_j its row norms),
 //     x_j = Q_j(y_j)                         (normal: identity; Student t:
 //                                             the Sec. 3 map, any supported nu).
 // Sample i uses the Philox blocks ctr0/4 + i ceil(d/2) + 0 .. ceil(d/2)-1.
@@ -42,11 +43,11 @@ static_assert(sizeof(ttbl::SegT) == 64, "t-copula rows share the Student-t segme
 struct CopulaDev {
     int d;
     int tcop;                             // 0: Gaussian copula, 1: t copula
-    double L[kMaxD * (kMaxD + 1) / 2];   // packed rows of the lower triangle
+    double L[kMaxD * (kMaxD + 1) / 2];   // packed rows of the lower triangle, each
+                                          // divided by its norm (L L^T -> correlation)
     int kind[kMaxD];                      // MARGIN_*
     TSel t[kMaxD];
     // t copula
-    double inv_sigma[kMaxD];              // 1 / row norms of L
     double half_log_nu;
     const ttbl::SegT* chi;                // log W(z) rows (QM_TC_NZ)
     const double* chi_c;                  //   and their centres
@@ -175,7 +176,7 @@ k_tcopula(const CopulaDev* __restrict__ cp, PhiloxKeys K, uint64_t blk0, double*
         const double S = exp(c.half_log_nu - 0.5 * tc_log_w(c, zw));       // sqrt(nu / W)
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            const double T = y[j] * c.inv_sigma[j] * S;
+            const double T = y[j] * S;
             double x = T;
             if (c.kind[j] != MARGIN_SAME_T) {
                 x = tc_g(c, T);
@@ -251,7 +252,8 @@ qm_status fill_copula(int d, const double* chol, const qm_margin* margins, doubl
             }
         }
         if (!(chol[j * d + j] > 0.0)) return fail(QM_ERR_INVALID, "%s: L[%d][%d] must be > 0", who, j, j);
-        c.host.inv_sigma[j] = 1.0 / std::sqrt(ss);
+        const double inv_sigma = 1.0 / std::sqrt(ss);         // the copula of L L^T is its correlation's
+        for (int k = 0; k <= j; ++k) c.host.L[j * (j + 1) / 2 + k] *= inv_sigma;
         const qm_margin& m = margins[j];
         c.host.t[j] = TSel{0, 0, nullptr, nullptr};
         if (m.kind == QM_DIST_STUDENT_T) {

@@ -23,11 +23,12 @@ def reference(L, margins, key, ctr0, n):
     dd = (np.where(upper, 2**53 - 1 - m, m).astype(np.float64) + 0.5) * 2.0**-53
     eps = oracle.probit(dd.ravel()).reshape(dd.shape)
     eps = np.where(upper, -eps, eps)
-    y = eps @ L.T
+    sigma = np.sqrt((L * L).sum(axis=1))            # rows normalised: the copula of the correlation
+    y = eps @ L.T / sigma
     x = np.empty_like(y)
     for j, (kind, nu) in enumerate(margins):
         x[:, j] = oracle.recycle_t(nu, y[:, j]) if kind == qm.QM_DIST_STUDENT_T else y[:, j]
-    scale = np.abs(eps) @ np.abs(L).T
+    scale = np.abs(eps) @ np.abs(L).T / sigma
     return x, y, scale
 
 

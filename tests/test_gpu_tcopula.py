@@ -136,10 +136,11 @@ def test_copulas_dimensions_and_ragged_counts(d, n):
         x = o[: d * n].reshape(d, n).T
         if nu is None:
             e = grid_normals(key, ctr0, n, d)
-            y = e @ L.T
+            sigma = np.sqrt((L * L).sum(axis=1))
+            y = e @ L.T / sigma
             ref = np.stack([oracle.recycle_t(mu, y[:, j]) if k == qm.QM_DIST_STUDENT_T else y[:, j]
                             for j, (k, mu) in enumerate(margins)], axis=1)
-            scale = np.abs(e) @ np.abs(L).T
+            scale = np.abs(e) @ np.abs(L).T / sigma
             T = y
         else:
             ref, T, scale = reference(L, margins, nu, key, ctr0, n)
