@@ -170,7 +170,8 @@ def run_reference(args, rank, world):
         times.append(time.perf_counter() - t0)
     t = sum(times) / len(times)
     val = m / t / 1e9
-    line = {"metric": METRIC, "value": val, "unit": "Gsamples/s", "n_gpus": 0, "steps": args.steps,
+    line = {"metric": METRIC, "value": val, "unit": "Gsamples/s", "n_gpus": args.gpus, "device": "cpu (host cores)",
+            "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": FP64_WORKLOAD, "n_per_gpu": 1 << 28,
