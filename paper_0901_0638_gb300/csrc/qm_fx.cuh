@@ -14,10 +14,12 @@
 //     |z| = a0 + t_u H,   H = beta_0 + tau (beta_1 + tau (beta_2 + tau F)) > 0,
 //     F   = beta_3 + tau (beta_4 + tau (beta_5 + tau beta_6))   (single precision)
 //
-// The Horner steps for beta_0..beta_2 run on signed 64-bit accumulators times
-// tau as an unsigned Q0.64 integer (unsigned mulhi plus a sign correction);
-// beta_3..beta_6 are stored pre-scaled to the accumulator's units, so the
-// single-precision chain F enters as one float -> int64 conversion.  The
+// The Horner steps for beta_0 and beta_1 run on signed 64-bit accumulators
+// times tau as an unsigned Q0.64 integer (unsigned mulhi plus a sign
+// correction); beta_3..beta_6 are stored pre-scaled to the accumulator's
+// units, and the single-precision chain F enters the beta_2 step as
+// B2 + rn(F tau), F tau formed in single precision from an exact two-float
+// split of tau.  The
 // normalisation of x is integer arithmetic, H becomes a double by bit
 // assembly and t_u exactly (two instruction mixes, below), and the final FMA
 // is the one FP64 operation of the method.  A segment is 48 bytes in two
@@ -140,8 +142,14 @@ __device__ __forceinline__ unsigned long long probit_mag_fx_sx(const fxt::FxTabl
     float F = __fmaf_rn(f.w, tau_f, f.z);
     F = __fmaf_rn(F, tau_f, f.y);
     F = __fmaf_rn(F, tau_f, f.x);
-    long long acc = (MIX & FX_CVT_HW) ? __float2ll_rn(F) : f32_to_i64_rn_alu(F);
-    acc = B2 + mulhi_su(acc, Tau);
+    // innermost step in single precision: tau = Tu 2^-46 = th 2^-23 + tl 2^-46
+    // exactly (both halves are integers below 2^23, or th = 2^23 at tau = 1),
+    // F tau = fl(fl(F 2^-23 th) + F 2^-46 tl); acc = B2 + rn(F tau)
+    const float th = __uint_as_float(0x4B000000u | (unsigned)(Tu >> 23)) - 8388608.0f;
+    const float tl = __uint_as_float(0x4B000000u | ((unsigned)Tu & 0x7FFFFFu)) - 8388608.0f;
+    const float f23 = F * 1.1920928955078125e-07f;                 // 2^-23, exact
+    const float G = __fmaf_rn(f23 * 1.1920928955078125e-07f, tl, __fmul_rn(f23, th));
+    long long acc = B2 + ((MIX & FX_CVT_HW) ? __float2ll_rn(G) : f32_to_i64_rn_alu(G));
     acc = (long long)B1 + mulhi_su(acc, Tau);
     acc = (long long)B0 + mulhi_su(acc, Tau);                     // H 2^-s0, in (0, 2^62)
 

@@ -24,8 +24,10 @@ On GB300 the FP64 pipe issues about 1/62 of the FP32 rate, so beta_0..beta_2
 are applied by a fixed-point Horner chain on 64-bit integers with tau as an
 unsigned Q0.64 number (acc_k = B_k + mulhi(acc_{k+1}, tau 2^64), every acc in
 units of 2^s0), beta_3..beta_6 by a single-precision chain F on the
-coefficients f_k = beta_k 2^-s0 (already in the accumulator's units), entering
-as acc_3 = rn(F) (float -> int64, round to nearest even); then
+coefficients f_k = beta_k 2^-s0 (already in the accumulator's units), which
+enters as acc_2 = B_2 + rn(F tau): F tau is formed in single precision from
+the exact split tau = th 2^-23 + tl 2^-46 of the integer offset (one
+multiply and one FMA) and converted to int64 rounding to nearest even; then
 z = fma(t_u, acc_0 2^s0, a_0), with t_u = (1 + t_u) - 1 formed exactly by one
 double-precision add.
 
@@ -138,9 +140,15 @@ def emulate(q, K, Tu):
     F = np.float32(q["bf"][-1])
     for cf in reversed(q["bf"][:-1]):
         F = np.float32(float(F) * tf + cf)
-    acc = int(np.rint(float(F)))                                  # float -> int64, nearest even
-    assert abs(acc) < 2**62
-    for k in reversed(range(NI)):
+    # innermost step in single precision: tau = Tu 2^-46 = th 2^-23 + tl 2^-46
+    # exactly; G = fl(fl(F 2^-23 th) + F 2^-46 tl) (a multiply, then one FMA)
+    th, tl = float(Tu >> 23), float(Tu & 0x7FFFFF)
+    f23 = float(F) * 2.0 ** -23
+    p = np.float32(f23 * th)
+    G = np.float32(float(Fraction(f23 * 2.0 ** -23) * Fraction(tl) + Fraction(float(p))))
+    acc = q["B"][NI - 1] + int(np.rint(float(G)))                 # float -> int64, nearest even
+    assert abs(acc) < 2**63
+    for k in reversed(range(NI - 1)):
         acc = q["B"][k] + ((acc * Tau) >> 64)
         assert abs(acc) < 2**63
     assert 0 < acc < 2**62
