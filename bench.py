@@ -38,8 +38,8 @@ ISSUE_PEAK_TINSTR = SMS * SCHEDULERS * LANES * MAX_SM_GHZ / 1e3   # thread-instr
 # k_f64_fixed: thread-instructions issued per element and DRAM bytes per
 # element, from the ncu capture of the 2^24-element case of this workload
 # (profiles/k_f64_fixed_fp64_mixture.md); re-measured whenever the kernel changes
-FIXED_INSTR_PER_ELEM = 150.5
-FIXED_DRAM_BYTES_PER_ELEM = (137.285e6 + 88.615e6) / 2**24   # writes still in L2 at exit not counted
+FIXED_INSTR_PER_ELEM = 148.5
+FIXED_DRAM_BYTES_PER_ELEM = (137.287e6 + 88.145e6) / 2**24   # writes still in L2 at exit not counted
 
 
 def parse():
