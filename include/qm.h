@@ -313,10 +313,12 @@ qm_status qm_tcopula_table_build(double nu, double* chi_seg, double* g_seg, int*
  * persistent launch over a device-resident segment table, replayed as a CUDA
  * graph.  Each segment is cut into tiles of block x ept elements that never
  * span two segments, so the target is uniform within a block.
- * Segment pairs: (NORMAL, STUDENT_T) with nu tabulated, (EXPONENTIAL,
- * NORMAL), (UNIFORM, NORMAL); in/out device arrays of n doubles.
+ * Segment pairs: (NORMAL, STUDENT_T) with nu in [QM_T_NU_MIN, QM_T_NU_MAX]
+ * (tabulated nu from the offline tables, others from tables built on the host
+ * at first use), (EXPONENTIAL, NORMAL), (UNIFORM, NORMAL); in/out device
+ * arrays of n doubles.
  * qm_batch_create validates everything before any launch: unsupported pairs
- * or out-of-set nu, null pointers, in/out partial overlap and overlapping
+ * or out-of-range nu, null pointers, in/out partial overlap and overlapping
  * outputs of two segments are rejected (QM_ERR_INVALID / QM_ERR_UNSUPPORTED).
  * Tuning: block in {128, 256, 512}, ept in {1, 2, 4}, estrin in {0, 1}
  * (Estrin instead of Horner for the Student-t segment polynomial; the two
