@@ -358,7 +358,8 @@ qm_status qm_batch_destroy(qm_batch* b);
  * A request asks for n samples of one target from its own Philox key
  * (counters from 0): QM_REQ_NORMAL_F32 (24-bit grid, TABLE form),
  * QM_REQ_NORMAL_F64 (53-bit grid), QM_REQ_STUDENT_T (the FP64 normal
- * recycled by the Sec. 3 map, nu tabulated), QM_REQ_EXP_NORMAL (Exp(1)
+ * recycled by the Sec. 3 map, nu in [QM_T_NU_MIN, QM_T_NU_MAX]; an
+ * untabulated nu has its tables built at submit), QM_REQ_EXP_NORMAL (Exp(1)
  * samples x = -log u recycled by the Sec. 6 map, evaluated from the exact u
  * as in qm_sample_fused).  Sample i of a request is the same value whether
  * it is computed alone or inside any batch.
