@@ -40,6 +40,8 @@ ISSUE_PEAK_TINSTR = SMS * SCHEDULERS * LANES * MAX_SM_GHZ / 1e3   # thread-instr
 # (profiles/k_f64_fixed_fp64_mixture.md); re-measured whenever the kernel changes
 FIXED_INSTR_PER_ELEM = 148.5
 FIXED_DRAM_BYTES_PER_ELEM = (137.287e6 + 88.145e6) / 2**24   # writes still in L2 at exit not counted
+# k_f32_table DRAM read + write bytes of one 2^26-element launch (ncu), per element
+F32_DRAM_BYTES_PER_ELEM = (268.489e6 + 217.546e6) / 2**26
 
 
 def parse():
@@ -218,8 +220,12 @@ def side_workload(args):
         line.update(value=n / (ms * 1e-3) / 1e9, ms_per_step=ms, dtype="f32",
                     config={"workload": f"fp32 normal quantile, n=2^{args.n_log2} floats, "
                                         "u=fl32((k+1/2)2^-24), k = top 24 bits of Philox seed 1"},
-                    roofline={"bound": "hbm", "achieved": gbs, "peak": 6780.7, "unit": "GB/s",
-                              "frac": gbs / 6780.7, "traffic": None})
+                    roofline={"bound": "hbm", "kernel": "k_f32_table", "achieved": gbs, "peak": 6780.7,
+                              "unit": "GB/s", "frac": gbs / 6780.7,
+                              "traffic": F32_DRAM_BYTES_PER_ELEM * n,
+                              "traffic_note": "DRAM bytes per launch, per-element figure of the 2^26 "
+                                              "capture x n (algorithmic: 8 B/element; writes still in "
+                                              "L2 at exit not counted)"})
     elif args.workload == "fused":
         # Philox4x32-10 (seed 3) -> FP32 normal for 2^32 samples: written (16 GiB)
         # and, separately, reduced on the device to the first four moments

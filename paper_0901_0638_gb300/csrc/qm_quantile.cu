@@ -305,51 +305,62 @@ static qm_status launch_map(const T* in, T* out, size_t n, F f, cudaStream_t s, 
 
 // ===========================================================================
 // FP32 TABLE map: one check per float4 for the rare edge inputs (0, 1, 1/2,
-// subnormal, out of range, NaN); the common case runs the short table path
-// on all four lanes of the vector with no per-element branch.
+// tiny or out of range, NaN); the common case runs the short table path on
+// all four lanes of the vector with no per-element branch.  The kernel is
+// bound by the L1 (the streaming traffic plus one 16-byte table gather per
+// element), so the common path is kept to as few instructions as possible:
+// x = 2d = min(2u, 2 - 2u) (Sec. 6.1; 2 - 2u is exact for u >= 1/2 and
+// above 1 otherwise), the range check on x (normal and below 1, which also
+// excludes u = 1/2, u = 1, u <= 0, u > 1 and NaN), and the sign of
+// u - 1/2 applied to |z| by one logic operation.
 // ===========================================================================
-__device__ __forceinline__ bool f32_common(float u)
+__device__ __forceinline__ float f32_x(float u)
 {
-    const uint32_t ub = __float_as_uint(u);
-    return (ub - 0x00800000u < 0x3f800000u - 0x00800000u) && ub != 0x3f000000u;
+    return fminf(2.0f * u, __fmaf_rn(-2.0f, u, 2.0f));
 }
 
-__device__ __forceinline__ float f32_fast(float u)
+__device__ __forceinline__ bool f32_x_common(float x)
 {
-    const uint32_t ub = __float_as_uint(u);
-    const bool upper = ub > 0x3f000000u;
-    const float x = upper ? __fmaf_rn(-2.0f, u, 2.0f) : 2.0f * u;
-    const float g = tbl32_core(x);
-    return __uint_as_float(__float_as_uint(g) ^ (upper ? 0u : 0x80000000u));
+    return __float_as_uint(x) - 0x00800000u < 0x3f800000u - 0x00800000u;
 }
 
+// -g for u < 1/2, +g for u > 1/2 (g = |z|)
+__device__ __forceinline__ float f32_signed(float g, float u)
+{
+    const uint32_t q = __float_as_uint(__fadd_rn(u, -0.5f));
+    return __uint_as_float(__float_as_uint(g) ^ (q & 0x80000000u));
+}
+
+__device__ __forceinline__ float4 f32_table4(float4 v)
+{
+    const float4 x = make_float4(f32_x(v.x), f32_x(v.y), f32_x(v.z), f32_x(v.w));
+    if (f32_x_common(x.x) && f32_x_common(x.y) && f32_x_common(x.z) && f32_x_common(x.w))
+        return make_float4(f32_signed(tbl32_core(x.x), v.x), f32_signed(tbl32_core(x.y), v.y),
+                           f32_signed(tbl32_core(x.z), v.z), f32_signed(tbl32_core(x.w), v.w));
+    return make_float4(probit_f32_tbl(v.x), probit_f32_tbl(v.y), probit_f32_tbl(v.z),
+                       probit_f32_tbl(v.w));
+}
+
+// U float4 loads in flight per thread; the main loop runs over whole groups
+// of U without bounds checks, then a remainder loop, then the scalar tail.
+// Four blocks of 256 per SM (64 registers) measured faster than six.
 template <int U>
-__global__ void __launch_bounds__(256, 6)
+__global__ void __launch_bounds__(256, 4)
 k_f32_table(const float* __restrict__ in, float* out, size_t n)
 {
     const size_t nv = n / 4;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     const float4* vin = reinterpret_cast<const float4*>(in);
     float4* vout = reinterpret_cast<float4*>(out);
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride * U) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + (U - 1) * stride < nv; i += stride * U) {
         float4 a[U];
 #pragma unroll
-        for (int k = 0; k < U; ++k)
-            if (i + k * stride < nv) a[k] = __ldcs(vin + i + k * stride);
+        for (int k = 0; k < U; ++k) a[k] = __ldcs(vin + i + k * stride);
 #pragma unroll
-        for (int k = 0; k < U; ++k) {
-            if (i + k * stride >= nv) continue;
-            const float4 v = a[k];
-            float4 z;
-            if (f32_common(v.x) && f32_common(v.y) && f32_common(v.z) && f32_common(v.w)) {
-                z = make_float4(f32_fast(v.x), f32_fast(v.y), f32_fast(v.z), f32_fast(v.w));
-            } else {
-                z = make_float4(probit_f32_tbl(v.x), probit_f32_tbl(v.y), probit_f32_tbl(v.z),
-                                probit_f32_tbl(v.w));
-            }
-            __stcs(vout + i + k * stride, z);
-        }
+        for (int k = 0; k < U; ++k) __stcs(vout + i + k * stride, f32_table4(a[k]));
     }
+    for (; i < nv; i += stride) __stcs(vout + i, f32_table4(__ldcs(vin + i)));
     const size_t tail = nv * 4;
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n - tail) out[tail + t] = probit_f32_tbl(in[tail + t]);
@@ -784,8 +795,8 @@ extern "C" qm_status qm_normal_quantile_f32(const float* u, float* z, size_t n, 
     case QM_VAR_TABLE: {
         if ((uintptr_t)u % 16 != 0 || (uintptr_t)z % 16 != 0)
             return launch_map(u, z, n, F32Table(), s, "f32 table (unaligned)");
-        const int g = grid_for(k_f32_table<2>, 256, (n / 4 + 1) / 2 + 1);
-        k_f32_table<2><<<g, 256, 0, s>>>(u, z, n);
+        const int g = grid_for(k_f32_table<4>, 256, (n / 4 + 3) / 4 + 1);
+        k_f32_table<4><<<g, 256, 0, s>>>(u, z, n);
         return check_launch("f32 table");
     }
     default: return fail(QM_ERR_INVALID, "qm_normal_quantile_f32: variant %d not available in FP32", variant);
