@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--n-log2", type=int, default=28, help="elements per rank = 2^n")
     p.add_argument("--variant", default="default")
     p.add_argument("--no-extras", action="store_true", help="skip variant/e2e/cpu legs")
+    p.add_argument("--cpu-threads", type=int, default=0,
+                   help="host threads of the oracle in --impl reference (0: all cores)")
     p.add_argument("--workload", default="fp64", choices=["fp64", "fp32", "batch", "serve", "fused",
                                                           "hyperbolic", "copula", "tcopula"],
                    help="fp64: the headline line; fp32/batch/serve: the other hot-path kernels "
@@ -155,31 +157,90 @@ def cpu_oracle_leg(n_total: int, budget_s: float = 12.0):
             "sample": f"first {m} elements of the seed-2 mixture (of 2^28), {dt:.1f} s"}
 
 
+def reference_sample(args, nt):
+    """The oracle's work for one step of the reference arm: a bounded sample
+    of the workload `args.workload`, from the same generators as the device
+    path.  Returns (fn, elements per call, config, dtype)."""
+    import numpy as np
+    import oracle
+    from paper_0901_0638_gb300 import workloads as W
+    if args.workload == "fp64":
+        m = 1 << 20
+        u = W.mixture_f64(2, m).numpy()
+        cfg = {"workload": FP64_WORKLOAD, "n_per_gpu": 1 << 28,
+               "sample": "each step evaluates the first 2^20 of the 2^28 elements", "sample_n": m}
+        return (lambda: oracle.probit(u, nt)), m, cfg, "f64"
+    if args.workload == "fp32":
+        n = 1 << args.n_log2
+        m = min(n, 1 << 20)
+        _, u32 = W.uniform24(1, m)
+        u = u32.double().numpy()
+        cfg = {"workload": f"fp32 normal quantile, n=2^{args.n_log2} floats, u=fl32((k+1/2)2^-24), "
+                           "k = top 24 bits of Philox seed 1",
+               "sample": f"each step evaluates the first {m} of the {n} elements in FP64", "sample_n": m}
+        return (lambda: oracle.probit(u, nt)), m, cfg, "f64"
+    if args.workload == "batch":
+        lens, targets = W.ragged_segments(4, 256, hi=args.batch_hi)
+        segs = []
+        for j, (nj, tg) in enumerate(zip(lens, targets)):
+            mj = min(int(nj), 4096)
+            if tg == 8:
+                segs.append((None, W.exponential(4, mj, 0, j + 1).numpy()))
+            else:
+                segs.append((W.NU_SET[tg], W.normal_box_muller(4, mj, 0, j + 1).numpy()))
+        m = sum(x.size for _, x in segs)
+
+        def fn():
+            for nu, x in segs:
+                if nu is None:
+                    oracle.recycle_exp(x, nt)
+                else:
+                    oracle.recycle_t(nu, x, nt)
+        cfg = {"workload": "ragged recycling batch: 256 segments, lengths log-uniform [2^10, 2^24] "
+                           "(seed 4), normal->t_nu for nu in {1,2,3,4,5,8,10,30} and exp->normal",
+               "sample": "stratified: the first min(len, 4096) elements of every segment", "sample_n": m}
+        return fn, m, cfg, "f64"
+    if args.workload == "fused":
+        chunks, w = 256, 4096
+
+        def fn():
+            for c in range(chunks):
+                k = oracle.philox_stream(3, c << 24, w) >> 8
+                oracle.probit((k.astype(np.float64) + 0.5) * 2.0 ** -24, nt)
+        cfg = {"workload": "fused Philox4x32-10 (seed 3) -> fp32 normal, n=2^32",
+               "sample": "256 chunks of 4096 samples at stride 2^24 (2^20 of the 2^32), Philox and "
+                         "quantile both in the oracle", "sample_n": chunks * w}
+        return fn, chunks * w, cfg, "f64"
+    return None, 0, None, None
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
     import oracle
-    from paper_0901_0638_gb300 import workloads as W
-    threads = oracle.threads_used(0)
-    m = 1 << 20  # bounded per-step sample of the workload
-    u = W.mixture_f64(2, m).numpy()
+    nt = max(0, args.cpu_threads)
+    threads = oracle.threads_used(nt)
+    fn, m, cfg, dtype = reference_sample(args, nt)
+    if fn is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"no CPU oracle leg for the "
+                          f"{args.workload} workload (its parity is checked in tests/)"}), flush=True)
+        return
     for _ in range(args.warmup):
-        oracle.probit(u[: 1 << 14])
+        fn()
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.probit(u)
+        fn()
         times.append(time.perf_counter() - t0)
     t = sum(times) / len(times)
     val = m / t / 1e9
     line = {"metric": METRIC, "value": val, "unit": "Gsamples/s", "n_gpus": args.gpus, "device": "cpu (host cores)",
             "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": FP64_WORKLOAD, "n_per_gpu": 1 << 28,
-                       "sample": f"each step evaluates the first 2^20 of the 2^28 elements", "sample_n": m},
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic", "impl": "reference",
+            "config": cfg,
             "cpu_baseline": {"value": val, "unit": "Gsamples/s", "cores": threads, "kind": "oracle",
-                             "sample": f"2^20 elements of the 2^28 workload per step"},
+                             "sample": cfg["sample"]},
             "e2e": {"value": val, "unit": "Gsamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -157,6 +157,50 @@ def test_f32_ragged_and_misaligned(n):
     assert not f32_violations(out[1:].cpu().numpy(), w).any()
 
 
+def test_f32_full_size_sampled():
+    """The FP32 bench workload (2^28 floats of the 24-bit grid, default
+    variant, the launch the bench times) against the oracle on 2^16 sampled
+    outputs."""
+    n = 1 << 28
+    _, u = W.uniform24(1, n, device=DEV)
+    z = torch.empty_like(u)
+    qm.qm_normal_quantile_f32(u, z, qm.QM_VAR_DEFAULT)
+    torch.cuda.synchronize()
+    idx = torch.from_numpy(np.random.default_rng(1).integers(0, n, 1 << 16)).to(DEV)
+    us = u[idx].cpu().numpy()
+    zs = z[idx].cpu().numpy()
+    assert not f32_violations(zs, oracle.probit(us.astype(np.float64))).any()
+    del u, z
+    torch.cuda.empty_cache()
+
+
+def test_f32_many_passes_with_edges():
+    """A ragged size with several passes of the vector kernel's main loop and
+    edge inputs planted everywhere (so float4 groups take the edge path in
+    the main loop, the remainder loop and the scalar tail): the same bits as
+    the element-wise path, and the oracle on a sample."""
+    n = (1 << 23) + 7
+    rng = np.random.default_rng(23)
+    host = rng.random(n + 1).astype(np.float32)
+    edges = np.array([0.0, 1.0, 0.5, -0.0, 1e-40, 2.0**-126, 2.0**-127, np.nan, -0.25, 1.5,
+                      np.inf, 1.0 - 2.0**-24, 0.5 + 2.0**-24, 0.5 - 2.0**-25], dtype=np.float32)
+    pos = rng.integers(0, n + 1, 4096)
+    host[pos] = edges[rng.integers(0, edges.size, pos.size)]
+    host[-3:] = edges[:3]                                              # in the scalar tail
+    dev = torch.from_numpy(host).to(DEV)
+    vec = torch.empty(n + 1, dtype=torch.float32, device=DEV)
+    qm.qm_normal_quantile_f32(dev, vec, qm.QM_VAR_DEFAULT)            # float4 path
+    sca = torch.zeros(n + 2, dtype=torch.float32, device=DEV)
+    qm.qm_normal_quantile_f32(dev, sca[1:], qm.QM_VAR_DEFAULT)        # misaligned: element-wise
+    torch.cuda.synchronize()
+    a = vec.cpu().numpy().view(np.int32)
+    b = sca[1:].cpu().numpy().view(np.int32)
+    assert np.array_equal(a, b)
+    smp = np.concatenate([pos, rng.integers(0, n + 1, 1 << 14), np.arange(n - 2, n + 1)])
+    w = oracle.probit(host[smp].astype(np.float64))
+    assert not f32_violations(vec.cpu().numpy()[smp], w).any()
+
+
 def test_f32_in_place():
     k, u = W.uniform24(9, 4099)
     t = u.clone().to(DEV)
