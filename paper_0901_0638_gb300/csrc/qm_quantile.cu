@@ -648,10 +648,10 @@ k_fused_normal_f32(PhiloxKeys K, uint64_t blk0, size_t n, float* out, double* pa
     for (size_t b = (size_t)blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += stride) {
         const uint4 w = philox_block_keys(K, blk0 + b);
         float z[4];
-        z[0] = probit_grid24_tbl_s(w.x >> 8, stbl);
-        z[1] = probit_grid24_tbl_s(w.y >> 8, stbl);
-        z[2] = probit_grid24_tbl_s(w.z >> 8, stbl);
-        z[3] = probit_grid24_tbl_s(w.w >> 8, stbl);
+        z[0] = probit_grid24_word_s(w.x, stbl);
+        z[1] = probit_grid24_word_s(w.y, stbl);
+        z[2] = probit_grid24_word_s(w.z, stbl);
+        z[3] = probit_grid24_word_s(w.w, stbl);
         const size_t i0 = b * 4;
         const bool full = i0 + 4 <= n;
         if (OUT) {
