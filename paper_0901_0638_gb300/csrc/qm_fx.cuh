@@ -8,18 +8,21 @@
 // with a 53-bit integer significand M; (E, top K bits of M) select a segment
 // whose local expansion G of Q(v) = Phi^{-1}(1 - e^{-v}/2) comes from the
 // recycling ODE Q'' + Q' = Q Q'^2 (Sec. 2.3, Sec. 6).  With the offset
-// t_u = T 2^-52 > 0 back from the segment's end (T an exact integer; the end
-// of the top segment is x = 1, where z = 0) and tau = t_u 2^K in (0, 1]:
+// t_u = T 2^-52 > 0 back from the segment's end (T in [1, 2^(52-K)] an exact
+// integer; the end of the top segment is x = 1, where z = 0), H is stored as
+// a polynomial in tau' = (T - 1) 2^(K-52) in [0, 1) (the expansion in
+// t_u 2^K moved by one unit of T, so that tau' 2^64 fits 64 bits and T - 1
+// is the complement of the significand's low bits):
 //
-//     |z| = a0 + t_u H,   H = beta_0 + tau (beta_1 + tau (beta_2 + tau F)) > 0,
-//     F   = beta_3 + tau (beta_4 + tau (beta_5 + tau beta_6))   (single precision)
+//     |z| = a0 + t_u H,   H = beta_0 + tau' (beta_1 + tau' (beta_2 + tau' F)) > 0,
+//     F   = beta_3 + tau' (beta_4 + tau' (beta_5 + tau' beta_6))   (single precision)
 //
 // The Horner steps for beta_0 and beta_1 run on signed 64-bit accumulators
-// times tau as an unsigned Q0.64 integer (unsigned mulhi plus a sign
+// times tau' as an unsigned Q0.64 integer (unsigned mulhi plus a sign
 // correction); beta_3..beta_6 are stored pre-scaled to the accumulator's
 // units, and the single-precision chain F enters the beta_2 step as
-// B2 + rn(F tau), F tau formed in single precision from an exact two-float
-// split of tau.  The
+// B2 + rn(F tau'), F tau' formed in single precision from an exact two-float
+// split of tau'.  The
 // normalisation of x is integer arithmetic, H becomes a double by bit
 // assembly and t_u exactly (two instruction mixes, below), and the final FMA
 // is the one FP64 operation of the method.  A segment is 48 bytes in two
@@ -123,12 +126,12 @@ __device__ __forceinline__ unsigned long long probit_mag_fx_sx(const fxt::FxTabl
     const int ec = min(max(e, 0), fxt::E_LAST);
     const unsigned j = (unsigned)(Mx >> sK) & ((1u << K) - 1u);
     const int idx = (ec << K) + (int)j;
-    // offset back from the segment end: Tu in [1, 2^sK]
-    const unsigned long long Tu = (1ull << sK) - (Mx & ((1ull << sK) - 1ull));
-    // tau 2^64, with tau = 1 (Tu = 2^sK) mapped to 2^64 - 1; written without a
-    // shift that overflows 64 bits
-    const unsigned long long top = Tu >> sK;                        // 1 iff tau = 1
-    const unsigned long long Tau = ((Tu - top) << (12 + K)) | (0ull - top);
+    // offset back from the segment end, Tu = Tp + 1 in [1, 2^sK]: Tp is the
+    // complement of the significand's low sK bits.  H is stored in
+    // tau' = Tp 2^-sK in [0, 1) (re-expanded by one unit of the offset), so
+    // tau' 2^64 is a plain shift that never overflows.
+    const unsigned long long Tp = ~Mx & ((1ull << sK) - 1ull);
+    const unsigned long long Tau = Tp << (12 + K);
 
     unsigned long long a0b, B0, B1, B2s;
     ld256(&T->a[idx], a0b, B0, B1, B2s);                           // a0, B0, B1, B2 | s0
@@ -137,16 +140,16 @@ __device__ __forceinline__ unsigned long long probit_mag_fx_sx(const fxt::FxTabl
     const int s0 = (int)((long long)B2s >> 52);
 
     // single-precision tail from the top bits of the offset
-    const float tf = __uint_as_float(0x4B000000u | (unsigned)(Tu >> 25)) - 8388608.0f;
+    const float tf = __uint_as_float(0x4B000000u | (unsigned)(Tp >> 25)) - 8388608.0f;
     const float tau_f = tf * __uint_as_float((unsigned)(127 + K - 27) << 23);
     float F = __fmaf_rn(f.w, tau_f, f.z);
     F = __fmaf_rn(F, tau_f, f.y);
     F = __fmaf_rn(F, tau_f, f.x);
-    // innermost step in single precision: tau = Tu 2^-46 = th 2^-23 + tl 2^-46
-    // exactly (both halves are integers below 2^23, or th = 2^23 at tau = 1),
-    // F tau = fl(fl(F 2^-23 th) + F 2^-46 tl); acc = B2 + rn(F tau)
-    const float th = __uint_as_float(0x4B000000u | (unsigned)(Tu >> 23)) - 8388608.0f;
-    const float tl = __uint_as_float(0x4B000000u | ((unsigned)Tu & 0x7FFFFFu)) - 8388608.0f;
+    // innermost step in single precision: tau' = Tp 2^-46 = th 2^-23 + tl 2^-46
+    // exactly (both halves are integers below 2^23),
+    // F tau' = fl(fl(F 2^-23 th) + F 2^-46 tl); acc = B2 + rn(F tau')
+    const float th = __uint_as_float(0x4B000000u | (unsigned)(Tp >> 23)) - 8388608.0f;
+    const float tl = __uint_as_float(0x4B000000u | ((unsigned)Tp & 0x7FFFFFu)) - 8388608.0f;
     const float f23 = F * 1.1920928955078125e-07f;                 // 2^-23, exact
     const float G = __fmaf_rn(f23 * 1.1920928955078125e-07f, tl, __fmul_rn(f23, th));
     long long acc = B2 + ((MIX & FX_CVT_HW) ? __float2ll_rn(G) : f32_to_i64_rn_alu(G));
@@ -158,13 +161,14 @@ __device__ __forceinline__ unsigned long long probit_mag_fx_sx(const fxt::FxTabl
     const int lh = __clzll(ha);
     const unsigned long long hm = ((ha << lh) + 0x400ull) >> 11;
     const unsigned long long hbits = hm + ((unsigned long long)(1022 + 63 - lh + s0) << 52);
-    // t_u as a double (exact, 1 <= Tu <= 2^47): 1 + t_u has the bits
+    // t_u as a double (exact, 1 <= Tu <= 2^sK): 1 + t_u has the bits
     // 0x3FF0... + Tu and taking 1 away again is exact (Sterbenz); or by
     // normalising Tu and inserting the exponent
     double tu;
     if (MIX & FX_TU_FADD) {
-        tu = __dadd_rn(__longlong_as_double((long long)(0x3FF0000000000000ull + Tu)), -1.0);
+        tu = __dadd_rn(__longlong_as_double((long long)(0x3FF0000000000001ull + Tp)), -1.0);
     } else {
+        const unsigned long long Tu = Tp + 1ull;
         const int lt = __clzll(Tu);
         tu = __longlong_as_double((long long)((Tu << (lt - 11)) + ((unsigned long long)(1033 - lt) << 52)));
     }

@@ -20,13 +20,19 @@ error); |z| grows away from the end, so H > 0 on every segment:
     G = a_0 + t_u H(t_u),  H = sum_{k=0}^{6} beta_k tau^k,
     tau = t_u 2^K in (0, 1].
 
+With the integer offset Tu = t_u 2^52 in [1, 2^(52-K)], the kernel reads
+Tu - 1 = ~m & (2^(52-K) - 1) straight from the significand bits, so H is
+stored re-expanded in tau' = tau - 2^(K-52) = (Tu - 1) 2^(K-52) in
+[0, 1 - 2^(K-52)] (an exact change of expansion point, so the same
+polynomial): tau' 2^64 = (Tu - 1) << (12 + K) always fits 64 bits.
+
 On GB300 the FP64 pipe issues about 1/62 of the FP32 rate, so beta_0..beta_2
-are applied by a fixed-point Horner chain on 64-bit integers with tau as an
-unsigned Q0.64 number (acc_k = B_k + mulhi(acc_{k+1}, tau 2^64), every acc in
+are applied by a fixed-point Horner chain on 64-bit integers with tau' as an
+unsigned Q0.64 number (acc_k = B_k + mulhi(acc_{k+1}, tau' 2^64), every acc in
 units of 2^s0), beta_3..beta_6 by a single-precision chain F on the
 coefficients f_k = beta_k 2^-s0 (already in the accumulator's units), which
-enters as acc_2 = B_2 + rn(F tau): F tau is formed in single precision from
-the exact split tau = th 2^-23 + tl 2^-46 of the integer offset (one
+enters as acc_2 = B_2 + rn(F tau'): F tau' is formed in single precision from
+the exact split tau' = th 2^-23 + tl 2^-46 of the integer offset (one
 multiply and one FMA) and converted to int64 rounding to nearest even; then
 z = fma(t_u, acc_0 2^s0, a_0), with t_u = (1 + t_u) - 1 formed exactly by one
 double-precision add.
@@ -119,8 +125,15 @@ def f32(x):
     return float(np.float32(float(x)))
 
 
+def shift_poly(beta, delta):
+    """Coefficients in tau' of H(tau' + delta) (exact re-expansion)."""
+    n = len(beta)
+    return [sum(beta[i] * mp.binomial(i, k) * delta ** (i - k) for i in range(k, n)) for k in range(n)]
+
+
 def quantise(e, j, K, g):
     beta = [g[k + 1] * mp.mpf(2) ** (-K * k) for k in range(DEG)]
+    beta = shift_poly(beta, mp.mpf(2) ** (K - 52))             # argument tau' = tau - 2^(K-52)
     assert beta[0] > 0, (e, j)
     hmax = sum(abs(x) for x in beta)                              # tau in [0, 1]
     s0 = int(mp.floor(mp.log(hmax, 2))) + 1 - 62                  # |acc| < 2^62
@@ -134,15 +147,16 @@ def quantise(e, j, K, g):
 
 def emulate(q, K, Tu):
     """The kernel's arithmetic for the integer offset Tu; returns the double z."""
-    Tau = (Tu << (12 + K)) - (Tu >> (52 - K))                     # tau = 1 -> 1 - 2^-64
+    Tp = Tu - 1                                                   # the kernel's ~m & (2^(52-K) - 1)
+    Tau = Tp << (12 + K)                                          # tau' 2^64
     assert 0 <= Tau < 2**64
-    tf = f32(float(Tu >> 25)) * 2.0 ** (K - 27)
+    tf = f32(float(Tp >> 25)) * 2.0 ** (K - 27)
     F = np.float32(q["bf"][-1])
     for cf in reversed(q["bf"][:-1]):
         F = np.float32(float(F) * tf + cf)
-    # innermost step in single precision: tau = Tu 2^-46 = th 2^-23 + tl 2^-46
+    # innermost step in single precision: tau' = Tp 2^-46 = th 2^-23 + tl 2^-46
     # exactly; G = fl(fl(F 2^-23 th) + F 2^-46 tl) (a multiply, then one FMA)
-    th, tl = float(Tu >> 23), float(Tu & 0x7FFFFF)
+    th, tl = float(Tp >> 23), float(Tp & 0x7FFFFF)
     f23 = float(F) * 2.0 ** -23
     p = np.float32(f23 * th)
     G = np.float32(float(Fraction(f23 * 2.0 ** -23) * Fraction(tl) + Fraction(float(p))))
@@ -209,7 +223,8 @@ def main():
         "// FP64 normal quantile, exponential coordinate, segment expansions of\n",
         "// G(t) = Q(V - log(1 + t/m_c)) from the recycling ODE Q'' + Q' = Q Q'^2,\n",
         "// re-expanded about the segment end and stored for fixed-point evaluation:\n",
-        "// G = a0 + t_u H, H = sum beta_k tau^k > 0, tau = (m_end - m) 2^K in (0, 1],\n",
+        "// G = a0 + t_u H, H = sum beta_k tau'^k > 0, tau' = (m_end - m) 2^K - 2^(K-52)\n",
+        "// in [0, 1) (t_u = m_end - m),\n",
         "// beta_0..2 as int64 B_k = beta_k 2^-s0 (A: a0, B0, B1, B2 | s0 << 52),\n",
         "// beta_3..6 as float f_k = beta_k 2^-s0 (F).\n",
         f"// Binade e = -1 - E = 0..{E_LAST}, {2**K_MAIN} segments each; index e 2^{K_MAIN} + j.\n",
