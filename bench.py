@@ -38,8 +38,8 @@ ISSUE_PEAK_TINSTR = SMS * SCHEDULERS * LANES * MAX_SM_GHZ / 1e3   # thread-instr
 # k_f64_fixed: thread-instructions issued per element and DRAM bytes per
 # element, from the ncu capture of the 2^24-element case of this workload
 # (profiles/k_f64_fixed_fp64_mixture.md); re-measured whenever the kernel changes
-FIXED_INSTR_PER_ELEM = 145.5
-FIXED_DRAM_BYTES_PER_ELEM = (137.334e6 + 88.190e6) / 2**24   # writes still in L2 at exit not counted
+FIXED_INSTR_PER_ELEM = 148.1
+FIXED_DRAM_BYTES_PER_ELEM = (137.285e6 + 87.372e6) / 2**24   # writes still in L2 at exit not counted
 # k_f32_table DRAM read + write bytes of one 2^26-element launch (ncu), per element
 F32_DRAM_BYTES_PER_ELEM = (268.489e6 + 217.546e6) / 2**26
 

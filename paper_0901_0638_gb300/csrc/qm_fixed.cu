@@ -25,8 +25,10 @@ namespace {
 
 constexpr int kBlock = 256;
 
+// Eight blocks of 256 per SM (32 registers, full occupancy): more warps to
+// cover the latency of the table gathers; measured 0.6 % faster than six.
 template <int U>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, 8)
 k_f64_fixed(const double* __restrict__ in, double* out, size_t n)
 {
     const size_t nv = n / 2;
