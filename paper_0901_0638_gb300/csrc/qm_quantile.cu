@@ -921,7 +921,6 @@ extern "C" qm_status qm_sample_fused(int target, const qm_params* p, uint64_t ke
             if (!p || !(p->nu > 0.0)) return fail(QM_ERR_INVALID, "qm_sample_fused: Student t needs nu > 0");
         }
         const size_t nblk = (n + 1) / 2;
-        const int g = grid_for(k_fused_f64<0, true, true>, B, nblk);
         TSel tk{0, 0, nullptr, nullptr};
         if (target == QM_DIST_STUDENT_T) {
             const void* tseg = nullptr;
@@ -931,21 +930,28 @@ extern "C" qm_status qm_sample_fused(int target, const qm_params* p, uint64_t ke
             tk.seg = (const ttbl::SegT*)tseg;
             tk.tail = ttail;
         }
-        double* part = nullptr;
-        if (moments4) {
-            part = partials_scratch(g);
-            if (!part) return fail(QM_ERR_NOMEM, "qm_sample_fused: scratch allocation failed");
-        }
         double* o = (double*)out;
         const uint64_t b0 = ctr0 / 4;
         const PhiloxKeys key = philox_keys(key_in);
         qm_status fst;
         const fxt::FxTable* fxT = (const fxt::FxTable*)fx_table_device(&fst);
         if (!fxT) return fst;
+        // Each variant's grid from its own occupancy (the write-only kernel
+        // holds fewer registers); the two moment variants share one grid, so
+        // the per-block partials, and with them the summation order, match.
+        int g = 0;
+        double* part = nullptr;
 #define QM_LAUNCH_F64(KIND)                                                                        \
-    if (o && part) k_fused_f64<KIND, true, true><<<g, B, 0, s>>>(key, b0, n, o, part, tk, fxT);   \
-    else if (o) k_fused_f64<KIND, true, false><<<g, B, 0, s>>>(key, b0, n, o, nullptr, tk, fxT);  \
-    else k_fused_f64<KIND, false, true><<<g, B, 0, s>>>(key, b0, n, nullptr, part, tk, fxT);
+    if (moments4) {                                                                                \
+        g = grid_for(k_fused_f64<KIND, true, true>, B, nblk);                                      \
+        part = partials_scratch(g);                                                                \
+        if (!part) return fail(QM_ERR_NOMEM, "qm_sample_fused: scratch allocation failed");       \
+        if (o) k_fused_f64<KIND, true, true><<<g, B, 0, s>>>(key, b0, n, o, part, tk, fxT);        \
+        else k_fused_f64<KIND, false, true><<<g, B, 0, s>>>(key, b0, n, nullptr, part, tk, fxT);   \
+    } else {                                                                                       \
+        g = grid_for(k_fused_f64<KIND, true, false>, B, nblk);                                     \
+        k_fused_f64<KIND, true, false><<<g, B, 0, s>>>(key, b0, n, o, nullptr, tk, fxT);           \
+    }
         if (target == QM_DIST_NORMAL) { QM_LAUNCH_F64(0) }
         else if (target == QM_DIST_STUDENT_T) { QM_LAUNCH_F64(1) }
         else { QM_LAUNCH_F64(2) }
