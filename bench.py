@@ -35,11 +35,13 @@ FP64_WORKLOAD = ("fp64 normal quantile Phi^-1, n=2^28 doubles per GPU, seed-2 ta
 NOMINAL_FP64_TFLOPS = 1.25     # GB300 nominal dense FP64 (profiling recipe table)
 SMS, SCHEDULERS, LANES, MAX_SM_GHZ = 152, 4, 32, 2.07
 ISSUE_PEAK_TINSTR = SMS * SCHEDULERS * LANES * MAX_SM_GHZ / 1e3   # thread-instructions/ns -> T/s
-# k_f64_fixed: thread-instructions issued per element and DRAM bytes per
-# element, from the ncu capture of the 2^24-element case of this workload
+# k_f64_fixed: thread-instructions issued per element, counted by ncu in one
+# pass on this command's own 2^28-element launch (smsp__inst_executed.sum x 32
+# / n; per-thread setup is spread over ~6.7 double2 per thread at this size),
+# and DRAM bytes per element from the full capture of the 2^24-element case
 # (profiles/k_f64_fixed_fp64_mixture.md); re-measured whenever the kernel changes
-FIXED_INSTR_PER_ELEM = 148.1
-FIXED_DRAM_BYTES_PER_ELEM = (137.285e6 + 87.372e6) / 2**24   # writes still in L2 at exit not counted
+FIXED_INSTR_PER_ELEM = 141.66
+FIXED_DRAM_BYTES_PER_ELEM = (137.287e6 + 88.500e6) / 2**24   # writes still in L2 at exit not counted
 # k_f32_table DRAM read + write bytes of one 2^26-element launch (ncu), per element
 F32_DRAM_BYTES_PER_ELEM = (268.489e6 + 217.546e6) / 2**26
 
