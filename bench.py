@@ -159,6 +159,24 @@ def cpu_oracle_leg(n_total: int, budget_s: float = 12.0):
             "sample": f"first {m} elements of the seed-2 mixture (of 2^28), {dt:.1f} s"}
 
 
+T2_VOTE_D_MIN = 1.0373472162855378e-3   # d above this <=> t_2 coordinate below 15.5 (Sec. 7.3)
+
+
+def vote_t2_fraction(u):
+    """Share of the warp votes of the HYBRID_VOTE kernel that take the t_2
+    rational: the kernel votes over aligned groups of 32 consecutive
+    elements, and a group takes t_2 only if every d = min(u, 1 - u) lies in
+    its domain (lanes past the end count as inside).  A property of the input
+    and of the kernel's grouping, computed from the input."""
+    import torch
+    d = torch.minimum(u, 1.0 - u)
+    ok = d > T2_VOTE_D_MIN
+    pad = (-ok.numel()) % 32
+    if pad:
+        ok = torch.cat([ok, torch.ones(pad, dtype=torch.bool, device=ok.device)])
+    return float(ok.view(-1, 32).all(dim=1).float().mean())
+
+
 def reference_sample(args, nt):
     """The oracle's work for one step of the reference arm: a bounded sample
     of the workload `args.workload`, from the same generators as the device
@@ -527,6 +545,8 @@ def main():
             torch.cuda.synchronize(dev)
             t = ev_a.elapsed_time(ev_b) / reps
             extras[f"fp64_{name}"] = {"ms": t, "gsamples_s": n / (t * 1e-3) / 1e9}
+            if name == "hybrid_vote":
+                extras[f"fp64_{name}"]["votes_taking_t2"] = vote_t2_fraction(u)
         # the branchy variants on 53-bit uniforms alone (seed 8, no tail
         # stress): the inputs where the vote and the extra t_2 branch matter
         del z
@@ -544,6 +564,8 @@ def main():
             torch.cuda.synchronize(dev)
             t = ev_a.elapsed_time(ev_b) / 3
             uni[name] = {"ms": t, "gsamples_s": n / (t * 1e-3) / 1e9}
+            if name == "hybrid_vote":
+                uni[name]["votes_taking_t2"] = vote_t2_fraction(uu)
         extras["fp64_uniform53_only"] = uni
         del uu, zu
         z = torch.empty_like(u)
