@@ -196,7 +196,9 @@ qm_status launch_d(const CopulaDev* dev, bool tcop, PhiloxKeys K, uint64_t blk0,
     if (!fxT) return fst;
     int bps = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, tcop ? k_tcopula<D> : k_copula<D>, 128, 0);
-    const size_t cap = (size_t)(sm_count() > 0 ? sm_count() : 1) * (bps > 0 ? bps : 1);
+    // up to 8 waves of resident blocks (each sample's output depends only on
+    // its index; 7.04 vs 6.98 G samples/s persistent at d = 8)
+    const size_t cap = (size_t)(sm_count() > 0 ? sm_count() : 1) * (bps > 0 ? bps : 1) * 8;
     size_t g = (n + 127) / 128;
     if (g > cap) g = cap;
     if (tcop) k_tcopula<D><<<(int)g, 128, 0, s>>>(dev, K, blk0, out, n, fxT);
