@@ -904,7 +904,8 @@ extern "C" qm_status qm_sample_fused(int target, const qm_params* p, uint64_t ke
         int g;
         double* part = nullptr;
         if (moments4) {
-            g = grid_for(k_fused_normal_f32<true, true>, B, nblk);
+            // one grid for both moment variants (same partials, same order)
+            g = grid_for(k_fused_normal_f32<true, true>, B, nblk, 4);
             part = partials_scratch(g);
             if (!part) return fail(QM_ERR_NOMEM, "qm_sample_fused: scratch allocation failed");
             const PhiloxKeys K = philox_keys(key_in);
