@@ -61,7 +61,10 @@ typedef enum {
     QM_VAR_DEFAULT = 0,      /* FP32: TABLE; FP64: FIXED                        */
     QM_VAR_BRANCHFREE = 1,   /* exponential coordinate, one rational for the
                                 whole range (FP32: Sec. 6.1 form z = v P/Q on
-                                v <= 25; FP64: Sec. 7.2 form on v <= 42 plus a
+                                v <= 25, a reproduction of the paper's form
+                                that reaches 4.1 ulp, just outside the 4-ulp
+                                FP32 bound that TABLE and SQRT_FORM meet;
+                                FP64: Sec. 7.2 form on v <= 42 plus a
                                 deep-tail rational on 42 < v <= 745)            */
     QM_VAR_HYBRID_VOTE = 2,  /* FP64: t_2 coordinate when the whole warp has
                                 v < 15.5, else the exponential form (Sec. 7.3,
@@ -112,7 +115,13 @@ typedef struct {
  * host memory (cudaHostAlloc / cudaHostRegister; with unified addressing its
  * pointer is a device pointer): the kernel then streams the data over the
  * host link itself, with no staging copy.  Pageable host memory is not
- * accepted (the kernel cannot address it).                                  */
+ * accepted (the kernel cannot address it).
+ * In place (u == z), three FP64 variants whose kernels read some inputs a
+ * second time after storing others switch algorithm, with results still
+ * within the FP64 bound but not bit-identical to the out-of-place call:
+ * TABLE runs as BRANCHFREE (about 14x slower), COMPACT as HYBRID_VOTE, and
+ * T2_MULTI as its per-element form without the compaction.  The default
+ * (FIXED) and every other variant run the same kernel in place.            */
 qm_status qm_normal_quantile_f32(const float* u, float* z, size_t n,
                                  int variant, void* stream);
 qm_status qm_normal_quantile_f64(const double* u, double* z, size_t n,
@@ -148,7 +157,13 @@ qm_status qm_philox_fill_u32(uint64_t key, uint64_t ctr0, uint32_t* out,
  *       (x itself is never rounded), FP64 only.
  * out: float[n] / double[n] (device) or NULL.  moments4: double[4] (device)
  * or NULL; if given it receives sum z, sum z^2, sum z^3, sum z^4 over the n
- * samples (overwritten, not accumulated).  At least one of out / moments4. */
+ * samples (overwritten, not accumulated).  At least one of out / moments4.
+ * Moment calls keep their per-block partials in one library-owned scratch
+ * buffer per device (one cudaMalloc at the first moment call on a device,
+ * sized for the largest grid, never freed or replaced until exit).  Every
+ * moment call on a device shares it: calls that overlap on the GPU
+ * (different streams with no ordering between them) race and return wrong
+ * moments; calls ordered on one stream are safe.                           */
 qm_status qm_sample_fused(int target, const qm_params* p, uint64_t key,
                           uint64_t ctr0, void* out, int out_is_f64, size_t n,
                           double* moments4, void* stream);
@@ -347,6 +362,11 @@ qm_status qm_batch_run(qm_batch* b, void* stream);
 /* Baseline: one plain launch per segment on `stream`. */
 qm_status qm_batch_run_separate(qm_batch* b, void* stream);
 qm_status qm_batch_get_tuning(const qm_batch* b, qm_tuning* t);
+/* Re-tiles the batch for tuning t and re-uploads its device table.  The call
+ * first blocks the host until the batch's last qm_batch_run (on whatever
+ * stream it was queued) has finished, so a run in flight never sees the
+ * table change under it; qm_batch_destroy waits the same way before it
+ * frees the table. */
 qm_status qm_batch_set_tuning(qm_batch* b, const qm_tuning* t);
 /* Autotuner: times every candidate tuning on this batch (reps graph launches
  * each, synchronising `stream`), keeps the fastest, appends it to the tuning

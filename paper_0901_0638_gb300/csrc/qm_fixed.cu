@@ -2,12 +2,12 @@
 // table evaluated in 64-bit fixed point (QM_VAR_FIXED, the FP64 default); the
 // method is described in qm_fx.cuh.  GB300 issues FP64 at about 1/62 of its
 // FP32 rate; the integer pipes carry the segment polynomial, and one FP64 FMA
-// per element remains.  A segment's 64 bytes arrive in two 256-bit loads
-// (each lane gathers a random segment, and the L1 cost of a gather grows with
-// the number of load instructions).
+// per element remains.  A segment's 48 bytes sit in two arrays and arrive in
+// one 256-bit and one 128-bit load (each lane gathers a random segment, and
+// the L1 cost of a gather grows with the number of load instructions).
 //
-// Every 0 < u < 1 (subnormal u included) takes the same path: binades
-// e = -1 - E < 64 have 64 segments, deeper ones (down to x = 2^-1073) 32.
+// Every 0 < u < 1 (subnormal u included) takes the same path: every binade
+// e = -1 - E = 0 .. 1072 (x = 2d down to 2^-1073) has 64 segments.
 // u = 1/2 gives +0, u = 0 gives -inf, u = 1 gives +inf, anything else NaN.
 // This file holds the table (qm_fx_tables.h); fx_table_device() gives its
 // device address to the kernels of other files.

@@ -15,6 +15,7 @@
 
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -750,7 +751,15 @@ k_fused_f64(PhiloxKeys K, uint64_t blk0, size_t n, double* out, double* partials
     if (MOM) block_reduce4(acc, partials);
 }
 
-// Per-device scratch for moment partials (allocated on first use).
+// Moment launches use grids of at most kMomentWaves waves of resident blocks.
+constexpr int kMomentWaves = 4;
+
+// Per-device scratch for moment partials.  Allocated once, at the first
+// moment call on a device, for the largest grid a moment launch can have
+// (SMs x the hardware's resident-block limit x kMomentWaves), and never
+// freed or replaced: a pointer handed to one caller stays valid for every
+// later kernel until the process exits.  All moment calls on a device share
+// it, so calls that overlap on the GPU race (documented in qm.h).
 static double* partials_scratch(int nblocks)
 {
     static std::mutex mu;
@@ -759,14 +768,19 @@ static double* partials_scratch(int nblocks)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
     std::lock_guard<std::mutex> lk(mu);
-    if (cap[dev] < nblocks) {
-        if (ptr[dev]) cudaFree(ptr[dev]);
-        ptr[dev] = nullptr;
-        cap[dev] = 0;
-        if (cudaMalloc(&ptr[dev], sizeof(double) * 4 * (size_t)nblocks) != cudaSuccess) return nullptr;
-        cap[dev] = nblocks;
+    if (!ptr[dev]) {
+        int sms = 0, per_sm = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev) != cudaSuccess)
+            return nullptr;
+        const int slots = std::max(1, sms) * std::max(1, per_sm) * kMomentWaves;
+        if (cudaMalloc(&ptr[dev], sizeof(double) * 4 * (size_t)slots) != cudaSuccess) {
+            ptr[dev] = nullptr;
+            return nullptr;
+        }
+        cap[dev] = slots;
     }
-    return ptr[dev];
+    return nblocks <= cap[dev] ? ptr[dev] : nullptr;
 }
 
 }  // namespace qm
@@ -905,9 +919,9 @@ extern "C" qm_status qm_sample_fused(int target, const qm_params* p, uint64_t ke
         double* part = nullptr;
         if (moments4) {
             // one grid for both moment variants (same partials, same order)
-            g = grid_for(k_fused_normal_f32<true, true>, B, nblk, 4);
+            g = grid_for(k_fused_normal_f32<true, true>, B, nblk, kMomentWaves);
             part = partials_scratch(g);
-            if (!part) return fail(QM_ERR_NOMEM, "qm_sample_fused: scratch allocation failed");
+            if (!part) return fail(QM_ERR_NOMEM, "qm_sample_fused: moment scratch unavailable");
             const PhiloxKeys K = philox_keys(key_in);
             if (out) k_fused_normal_f32<true, true><<<g, B, 0, s>>>(K, ctr0 / 4, n, (float*)out, part);
             else k_fused_normal_f32<false, true><<<g, B, 0, s>>>(K, ctr0 / 4, n, nullptr, part);
@@ -952,7 +966,7 @@ extern "C" qm_status qm_sample_fused(int target, const qm_params* p, uint64_t ke
     if (moments4) {                                                                                \
         g = grid_for(k_fused_f64<KIND, true, true>, B, nblk);                                      \
         part = partials_scratch(g);                                                                \
-        if (!part) return fail(QM_ERR_NOMEM, "qm_sample_fused: scratch allocation failed");       \
+        if (!part) return fail(QM_ERR_NOMEM, "qm_sample_fused: moment scratch unavailable");       \
         if (o) k_fused_f64<KIND, true, true><<<g, B, 0, s>>>(key, b0, n, o, part, tk, fxT);        \
         else k_fused_f64<KIND, false, true><<<g, B, 0, s>>>(key, b0, n, nullptr, part, tk, fxT);   \
     } else {                                                                                       \

@@ -120,6 +120,11 @@ struct qm_batch {
     cudaGraphExec_t exec = nullptr;
     int grid = 0;
     std::string signature;
+    // recorded on the caller's stream after every launch that reads the
+    // device table, so that a re-upload (new tuning) or the final free waits
+    // for the launches already queued, whatever stream they went to
+    cudaEvent_t last_run = nullptr;
+    bool ran = false;
 };
 
 namespace qm {
@@ -132,9 +137,26 @@ static void drop_graph(qm_batch* b)
     b->graph = nullptr;
 }
 
-// Recompute tile prefixes for the current tuning and upload the table.
+// Wait for the last launch that reads the device table (any stream).
+static qm_status wait_last_run(qm_batch* b)
+{
+    if (b->ran && b->last_run && cudaEventSynchronize(b->last_run) != cudaSuccess)
+        return fail(QM_ERR_CUDA, "qm_batch: waiting for the previous run failed");
+    b->ran = false;
+    return QM_OK;
+}
+
+static void mark_run(qm_batch* b, cudaStream_t s)
+{
+    if (b->last_run && cudaEventRecord(b->last_run, s) == cudaSuccess) b->ran = true;
+}
+
+// Recompute tile prefixes for the current tuning and upload the table (after
+// the launches already queued against the old table have finished).
 static qm_status layout(qm_batch* b)
 {
+    const qm_status ws = wait_last_run(b);
+    if (ws != QM_OK) return ws;
     const unsigned long long tile = (unsigned long long)b->tuning.block * b->tuning.ept;
     unsigned long long t0 = 0;
     for (auto& s : b->host) {
@@ -271,6 +293,11 @@ extern "C" qm_status qm_batch_create(const qm_segment* segs, int nseg, const qm_
         delete b;
         return fail(QM_ERR_CUDA, "qm_batch_create: stream creation failed");
     }
+    if (cudaEventCreateWithFlags(&b->last_run, cudaEventDisableTiming) != cudaSuccess) {
+        b->last_run = nullptr;
+        qm_batch_destroy(b);
+        return fail(QM_ERR_CUDA, "qm_batch_create: event creation failed");
+    }
     const qm_status st = layout(b);
     if (st != QM_OK) {
         qm_batch_destroy(b);
@@ -317,6 +344,7 @@ extern "C" qm_status qm_batch_run(qm_batch* b, void* stream)
     }
     const cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
     if (e != cudaSuccess) return fail(QM_ERR_CUDA, "qm_batch_run: graph launch: %s", cudaGetErrorString(e));
+    mark_run(b, (cudaStream_t)stream);
     return QM_OK;
 }
 
@@ -379,9 +407,11 @@ extern "C" qm_status qm_batch_tune(qm_batch* b, int reps, void* stream, qm_tunin
 extern "C" qm_status qm_batch_destroy(qm_batch* b)
 {
     if (!b) return QM_OK;
+    (void)wait_last_run(b);           // queued launches still read the table
     drop_graph(b);
     if (b->dev) cudaFree(b->dev);
     if (b->capture) cudaStreamDestroy(b->capture);
+    if (b->last_run) cudaEventDestroy(b->last_run);
     delete b;
     return QM_OK;
 }

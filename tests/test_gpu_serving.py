@@ -139,3 +139,34 @@ def test_server_argument_errors():
         srv.submit({"n": 1 << 20, "kind": qm.QM_REQ_NORMAL_F64, "key": 1})   # 8 MiB > 1 MiB
     assert e.value.status == qm.QM_ERR_NOMEM
     srv.close()
+
+
+def test_replay_timeout_returns_status_and_server_keeps_serving():
+    """Failure detection on the host: a replay whose bounded wait runs out
+    returns QM_ERR_TIMEOUT at its limit (the wait is a host loop, nothing on
+    the GPU is left waiting), and the same server then serves a new trace
+    with correct results."""
+    import time
+    srv = qm.Server(mem_budget=1 << 26, max_batch=16, streams=2)
+    # request 1 arrives at once; request 2 only after the replay's 0.05 s limit
+    trace = [{"id": 1, "n": 4096, "kind": qm.QM_REQ_NORMAL_F64, "key": 901, "t_arrival": 0.0},
+             {"id": 2, "n": 4096, "kind": qm.QM_REQ_NORMAL_F64, "key": 902, "t_arrival": 5.0}]
+    t0 = time.perf_counter()
+    with pytest.raises(qm.QMError) as e:
+        srv.replay(trace, timeout_s=0.05)
+    assert e.value.status == qm.QM_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 2.0          # gave up at its limit, not at request 2
+    assert "of 2 done" in qm.qm_last_error()
+    time.sleep(0.2)
+    stale = srv.poll()                             # request 1 may complete after the timeout
+    assert all(c.id == 1 and c.status == 0 for c in stale)
+    srv.release(1)
+    # the same server serves a fresh trace: every kind, oracle parity
+    trace2 = [{"id": 10 + k, "n": 3000 + 97 * k, "kind": kind, "nu": 4.0, "key": 910 + k,
+               "t_arrival": 0.001 * k} for k, kind in enumerate(range(4))]
+    done = srv.replay(trace2, timeout_s=60.0)
+    assert sorted(c.id for c in done) == [10, 11, 12, 13] and all(c.status == 0 for c in done)
+    for c in done:
+        check_parity(c, fetch(c))
+        srv.release(c.id)
+    srv.close()
