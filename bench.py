@@ -12,6 +12,15 @@ Prints ONE JSON line (rank 0).  Under torchrun each rank processes its own
 2^28-element slice of the same counter-based stream (weak scaling, no
 collective on the data path).  --impl reference times the CPU FP64 oracle on a
 bounded sample of the same workload instead.
+
+Beside the headline, the default run (rank 0) adds: the other FP64 and FP32
+variants on the same inputs, the end-to-end figure on pinned host buffers,
+the CPU oracle on a bounded sample, and three legs with their own clock
+records -- "fused" (Philox -> FP32 Phi^{-1} for 2^32 samples, written and as
+moments, the moments asserted within 5 sigma of 0, 1, 0, 3), "batch" (the
+256-segment ragged recycling batch, one graph launch against one launch per
+segment) and "serving" (the Poisson request trace, continuous batching
+against one plain launch per request, with p50/p99 latency).
 """
 from __future__ import annotations
 
@@ -35,15 +44,96 @@ FP64_WORKLOAD = ("fp64 normal quantile Phi^-1, n=2^28 doubles per GPU, seed-2 ta
 NOMINAL_FP64_TFLOPS = 1.25     # GB300 nominal dense FP64 (profiling recipe table)
 SMS, SCHEDULERS, LANES, MAX_SM_GHZ = 152, 4, 32, 2.07
 ISSUE_PEAK_TINSTR = SMS * SCHEDULERS * LANES * MAX_SM_GHZ / 1e3   # thread-instructions/ns -> T/s
-# k_f64_fixed: thread-instructions issued per element, counted by ncu in one
-# pass on this command's own 2^28-element launch (smsp__inst_executed.sum x 32
-# / n; per-thread setup is spread over ~6.7 double2 per thread at this size),
-# and DRAM bytes per element from the full capture of the 2^24-element case
-# (profiles/k_f64_fixed_fp64_mixture.md); re-measured whenever the kernel changes
-FIXED_INSTR_PER_ELEM = 141.66
-FIXED_DRAM_BYTES_PER_ELEM = (137.287e6 + 88.500e6) / 2**24   # writes still in L2 at exit not counted
-# k_f32_table DRAM read + write bytes of one 2^26-element launch (ncu), per element
-F32_DRAM_BYTES_PER_ELEM = (268.489e6 + 217.546e6) / 2**26
+# Issue rates measured on this GPU by probe kernels (thread-level operations
+# per second, 2.07 GHz): FP64 FMA 0.50-0.60 T/s, FP32 FMA 36-37 T/s, MUFU
+# 4.8 T/s.  They price the method's arithmetic in the composite roofline.
+DFMA_PER_S, FFMA_PER_S, MUFU_PER_S = 0.55e12, 36.5e12, 4.8e12
+FALLBACK_HBM_GBS = 6800.0      # profiling recipe fallback, used only without the measured file
+# ncu counters (DRAM bytes and issued instructions per element) are recorded
+# in profiles/counters.json together with a fingerprint of the kernel's
+# sources; a counter whose kernel has changed since is not used (traffic null).
+COUNTERS_JSON = os.path.join(ROOT, "profiles", "counters.json")
+KERNEL_FILES = {
+    "k_f64_fixed": ["paper_0901_0638_gb300/csrc/qm_fixed.cu", "paper_0901_0638_gb300/csrc/qm_fx.cuh",
+                    "paper_0901_0638_gb300/csrc/qm_fx_tables.h", "paper_0901_0638_gb300/_build.py"],
+    "k_f32_table": ["paper_0901_0638_gb300/csrc/qm_quantile.cu", "paper_0901_0638_gb300/csrc/qm_device.cuh",
+                    "paper_0901_0638_gb300/csrc/qm_tables.h", "paper_0901_0638_gb300/_build.py"],
+}
+
+
+def hbm_peak():
+    """Measured HBM copy bandwidth (GB/s) and where it came from."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v, "measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback 6.8 TB/s (no measured peak file)"
+
+
+def kernel_fingerprint(kernel):
+    """Hash of the kernel's sources with comments and whitespace removed."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for rel in KERNEL_FILES[kernel]:
+        with open(os.path.join(ROOT, rel)) as f:
+            src = f.read()
+        if rel.endswith(".py"):
+            src = re.sub(r"#[^\n]*", "", src)
+        else:
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            src = re.sub(r"//[^\n]*", "", src)
+        h.update(re.sub(r"\s+", " ", src).encode())
+    return h.hexdigest()[:16]
+
+
+def recorded_counters(kernel):
+    """The ncu counters of `kernel` if they were taken on its current sources."""
+    try:
+        with open(COUNTERS_JSON) as f:
+            rec = json.load(f).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("fingerprint") != kernel_fingerprint(kernel):
+        return None
+    return rec
+
+
+def record_counters(csv_path, n, command):
+    """Reads an ncu --csv --print-units base metrics log (details page) and
+    stores, per kernel of KERNEL_FILES found in it, DRAM bytes and issued
+    instructions per element (averaged over its launches, n elements each)."""
+    import csv
+    import re
+    rows = {}
+    with open(csv_path) as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    for r in csv.DictReader(lines):
+        name = r.get("Kernel Name", "")
+        k = next((k for k in KERNEL_FILES if re.search(r"\b" + k + r"\b", name)), None)
+        if k is None:
+            continue
+        launch = rows.setdefault(k, {}).setdefault(r["ID"], {})
+        launch[r["Metric Name"]] = float(r["Metric Value"].replace(",", ""))
+    try:
+        with open(COUNTERS_JSON) as f:
+            out = json.load(f)
+    except (OSError, ValueError):
+        out = {}
+    for k, launches in rows.items():
+        ls = list(launches.values())
+        avg = lambda m: sum(x.get(m, 0.0) for x in ls) / len(ls)
+        out[k] = {"fingerprint": kernel_fingerprint(k), "n": n, "launches": len(ls),
+                  "dram_bytes_per_element": (avg("dram__bytes_read.sum") + avg("dram__bytes_write.sum")) / n,
+                  "inst_per_element": 32 * avg("smsp__inst_executed.sum") / n,
+                  "duration_ns": avg("gpu__time_duration.sum"), "command": command,
+                  "per_launch": {m: avg(m) for m in sorted(ls[0])}}
+    with open(COUNTERS_JSON, "w") as f:
+        json.dump(out, f, indent=1, sort_keys=True)
+        f.write("\n")
+    print(json.dumps(out, indent=1))
 
 
 def parse():
@@ -61,7 +151,15 @@ def parse():
                                                           "hyperbolic", "copula", "tcopula"],
                    help="fp64: the headline line; fp32/batch/serve: the other hot-path kernels "
                         "(for profiling and context)")
-    p.add_argument("--serve-seconds", type=float, default=2.0)
+    p.add_argument("--serve-seconds", type=float, default=10.0,
+                   help="length of the serving trace (the serving leg and --workload serve)")
+    p.add_argument("--no-legs", action="store_true",
+                   help="default run: skip the fused, batch and serving legs")
+    p.add_argument("--record-counters", metavar="NCU_CSV", default=None,
+                   help="store per-element DRAM bytes and instructions of the kernels in an ncu "
+                        "--csv --print-units base log (n = 2^--n-log2 per launch) in profiles/, "
+                        "then exit (no GPU needed)")
+    p.add_argument("--counters-command", default="", help="the command that produced NCU_CSV")
     p.add_argument("--batch-hi", type=int, default=24,
                    help="ragged batch: segment lengths log-uniform in [2^10, 2^hi]")
     return p.parse_args()
@@ -280,15 +378,126 @@ def timed(fn, stream, steps, warmup):
     return e0.elapsed_time(e1) / steps
 
 
-def side_workload(args):
-    """fp32 / batch / serve workloads: one JSON line each (rank 0 only)."""
+# 5-sigma bounds of the first four sample moments of 2^32 standard normals:
+# sd(z^k) = sqrt(1, 2, 15, 96) (E z^2 = 1, Var z^2 = 2, E z^6 = 15,
+# Var z^4 = 105 - 9) over sqrt(2^32)
+MOMENT_5SIGMA_2P32 = (7.6e-5, 1.1e-4, 3.0e-4, 7.5e-4)
+
+
+def fused_leg(qm, dev, stream, n_log2=32, steps=3, warmup=1, gpu_index=0):
+    """Fused Philox4x32-10 (seed 3) -> FP32 Phi^{-1} for 2^n_log2 samples,
+    written (4 B each) and, separately, reduced on the device to the first
+    four moments, which must lie within 5 sigma of (0, 1, 0, 3) at 2^32;
+    then the FP64 sampler (53-bit grid) for 2^(n_log2 - 2) samples written."""
+    import torch
+    n = 1 << n_log2
+    out = torch.empty(n, dtype=torch.float32, device=dev)
+    mom = torch.empty(4, dtype=torch.float64, device=dev)
+    clk = ClockSampler(gpu_index)
+    clk.start()
+    ms_w = timed(lambda: qm.qm_sample_fused(qm.QM_DIST_NORMAL, 3, 0, out, stream=stream),
+                 stream, steps, warmup)
+    ms_m = timed(lambda: qm.qm_sample_fused(qm.QM_DIST_NORMAL, 3, 0, None, n=n, moments4=mom,
+                                            stream=stream), stream, steps, warmup)
+    clocks = clk.stop()
+    m = (mom / n).cpu().tolist()
+    del out
+    dev_m = [abs(m[0]), abs(m[1] - 1.0), abs(m[2]), abs(m[3] - 3.0)]
+    bounds = [b * (2.0 ** 16 / 2.0 ** (n_log2 / 2)) for b in MOMENT_5SIGMA_2P32]
+    assert all(x < b for x, b in zip(dev_m, bounds)), f"fused moments {m} outside 5 sigma {bounds}"
+    n64 = n >> 2
+    out64 = torch.empty(n64, dtype=torch.float64, device=dev)
+    ms_64 = timed(lambda: qm.qm_sample_fused(qm.QM_DIST_NORMAL, 3, 0, out64, out_is_f64=True,
+                                             stream=stream), stream, steps, warmup)
+    del out64
+    peak, _ = hbm_peak()
+    return {"workload": f"fused Philox4x32-10 (seed 3) -> fp32 Phi^-1, n=2^{n_log2}: written "
+                        f"({4 * n >> 30} GiB) and moments only; fp64 sampler 2^{n_log2 - 2} written",
+            "n": n, "written": {"ms": ms_w, "gsamples_s": n / (ms_w * 1e-3) / 1e9,
+                                "write_gbs": 4 * n / (ms_w * 1e-3) / 1e9,
+                                "hbm_frac_of_write": 4 * n / (ms_w * 1e-3) / 1e9 / peak},
+            "moments": {"ms": ms_m, "gsamples_s": n / (ms_m * 1e-3) / 1e9, "mean": m[0], "m2": m[1],
+                        "m3": m[2], "m4": m[3], "check": "within 5 sigma of (0, 1, 0, 3)",
+                        "bounds": bounds, "passed": True},
+            "fp64_written": {"n": n64, "ms": ms_64, "gsamples_s": n64 / (ms_64 * 1e-3) / 1e9,
+                             "hbm_frac_of_write": 8 * n64 / (ms_64 * 1e-3) / 1e9 / peak},
+            "bound": "alu (Philox integer work; no HBM traffic for uniforms)", "clocks": clocks}
+
+
+def batch_leg(qm, W, dev, stream, hi=24, steps=10, warmup=3, tune=True, gpu_index=0):
+    """256 ragged recycling segments (seed 4, lengths log-uniform in
+    [2^10, 2^hi]): one persistent graph launch against one plain launch per
+    segment, after the autotuner has picked the tiles."""
+    import torch
+    lens, targets = W.ragged_segments(4, 256, hi=hi)
+    spec = []
+    for j, (nj, tg) in enumerate(zip(lens, targets)):
+        if tg == 8:
+            x = W.exponential(4, nj, 0, j + 1, dev)
+            spec.append((qm.QM_DIST_EXPONENTIAL, qm.QM_DIST_NORMAL, 0.0, x, torch.empty_like(x)))
+        else:
+            x = W.normal_box_muller(4, nj, 0, j + 1, dev)
+            spec.append((qm.QM_DIST_NORMAL, qm.QM_DIST_STUDENT_T, W.NU_SET[tg], x, torch.empty_like(x)))
+    b = qm.Batch(spec)
+    if tune:
+        b.tune(reps=3, stream=stream)
+    tuning = b.tuning()
+    tot = int(sum(lens))
+    clk = ClockSampler(gpu_index)
+    clk.start()
+    ms = timed(lambda: b.run(stream), stream, steps, warmup)
+    ms_sep = timed(lambda: b.run_separate(stream), stream, steps, warmup)
+    clocks = clk.stop()
+    b.close()
+    del spec
+    return {"workload": f"ragged recycling batch: 256 segments, lengths log-uniform [2^10, 2^{hi}] "
+                        "(seed 4), normal->t_nu for nu in {1,2,3,4,5,8,10,30} and exp->normal",
+            "elements": tot, "tuning": tuning, "autotuned": tune,
+            "graph": {"ms": ms, "gsamples_s": tot / (ms * 1e-3) / 1e9, "launches": 1},
+            "separate_launches": {"ms": ms_sep, "gsamples_s": tot / (ms_sep * 1e-3) / 1e9,
+                                  "launches": sum(1 for x in lens if x)},
+            "speedup": ms_sep / ms, "clocks": clocks}
+
+
+def serving_leg(qm, W, seconds=10.0, gpu_index=0):
+    """The serving trace (Poisson 2e4 requests/s, seed 5, n log-uniform in
+    [2^8, 2^24], four target kinds, 8 GiB admission budget), replayed in
+    real time through continuous batching and through one plain launch per
+    request (FIFO, one stream): sustained Gsamples/s, p50/p99 latency."""
     import numpy as np
+    tr = W.serving_trace(5, rate=2e4, seconds=seconds)
+    for r in tr:
+        r["id"] = r["key"]
+    tot = sum(r["n"] for r in tr)
+    res = {}
+    clk = ClockSampler(gpu_index)
+    clk.start()
+    for name, mb, st in (("batched", 512, 2), ("plain", 1, 1)):
+        srv = qm.Server(mem_budget=8 << 30, max_batch=mb, streams=st, release_on_done=True)
+        done = srv.replay(tr, timeout_s=900)
+        lat = np.array([c.t_done - c.t_arrival for c in done])
+        span = max(c.t_done for c in done) - min(c.t_arrival for c in done)
+        res[name] = {"gsamples_s": tot / span / 1e9, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                     "p99_ms": 1e3 * float(np.percentile(lat, 99)), "makespan_s": span,
+                     "launches": srv.stats()["launches"]}
+        srv.close()
+    res["clocks"] = clk.stop()
+    res.update({"workload": f"serving: Poisson 2e4 req/s for {seconds} s (seed 5), n log-uniform "
+                            "[2^8, 2^24], 4 target kinds, 8 GiB budget",
+                "requests": len(tr), "samples": tot, "offered_gsamples_s": tot / seconds / 1e9})
+    return res
+
+
+def side_workload(args):
+    """fp32 / fused / batch / serve / hyperbolic / copula workloads: one JSON
+    line each (rank 0 only)."""
     import torch
     import paper_0901_0638_gb300 as qm
     from paper_0901_0638_gb300 import workloads as W
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     qm.load()
+    peak, peak_src = hbm_peak()
     line = {"metric": METRIC, "unit": "Gsamples/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "data": "synthetic"}
     if args.workload == "fp32":
@@ -298,43 +507,19 @@ def side_workload(args):
         ms = timed(lambda: qm.qm_normal_quantile_f32(u, z, qm.QM_VAR_DEFAULT, stream=stream),
                    stream, args.steps, args.warmup)
         gbs = 8 * n / (ms * 1e-3) / 1e9
+        rec = recorded_counters("k_f32_table")
         line.update(value=n / (ms * 1e-3) / 1e9, ms_per_step=ms, dtype="f32",
                     config={"workload": f"fp32 normal quantile, n=2^{args.n_log2} floats, "
                                         "u=fl32((k+1/2)2^-24), k = top 24 bits of Philox seed 1"},
-                    roofline={"bound": "hbm", "kernel": "k_f32_table", "achieved": gbs, "peak": 6780.7,
-                              "unit": "GB/s", "frac": gbs / 6780.7,
-                              "traffic": F32_DRAM_BYTES_PER_ELEM * n,
-                              "traffic_note": "DRAM bytes per launch, per-element figure of the 2^26 "
-                                              "capture x n (algorithmic: 8 B/element; writes still in "
-                                              "L2 at exit not counted)"})
+                    roofline={"bound": "hbm", "kernel": "k_f32_table", "achieved": gbs, "peak": peak,
+                              "unit": "GB/s", "frac": gbs / peak, "peak_source": peak_src,
+                              "traffic": rec["dram_bytes_per_element"] * n if rec else None,
+                              "algorithmic_bytes_per_element": 8})
     elif args.workload == "fused":
-        # Philox4x32-10 (seed 3) -> FP32 normal for 2^32 samples: written (16 GiB)
-        # and, separately, reduced on the device to the first four moments
-        n = 1 << (args.n_log2 if args.n_log2 != 28 else 32)
-        out = torch.empty(n, dtype=torch.float32, device=dev)
-        mom = torch.empty(4, dtype=torch.float64, device=dev)
-        ms_w = timed(lambda: qm.qm_sample_fused(qm.QM_DIST_NORMAL, 3, 0, out, stream=stream),
-                     stream, args.steps, args.warmup)
-        ms_m = timed(lambda: qm.qm_sample_fused(qm.QM_DIST_NORMAL, 3, 0, None, n=n, moments4=mom,
-                                                stream=stream), stream, args.steps, args.warmup)
-        m = (mom / n).cpu().tolist()
-        del out
-        # FP64 normals from 53-bit Philox integers (fixed-point FP64 evaluation),
-        # 2^30 samples written (8 GiB)
-        n64 = n >> 2
-        out64 = torch.empty(n64, dtype=torch.float64, device=dev)
-        ms_64 = timed(lambda: qm.qm_sample_fused(qm.QM_DIST_NORMAL, 3, 0, out64, out_is_f64=True,
-                                                 stream=stream), stream, args.steps, args.warmup)
-        del out64
-        gbs = 4 * n / (ms_w * 1e-3) / 1e9
-        line.update(value=n / (ms_w * 1e-3) / 1e9, ms_per_step=ms_w, dtype="f32",
-                    config={"workload": f"fused Philox4x32-10 (seed 3) -> fp32 normal, n=2^{n.bit_length()-1}, "
-                                        "written (16 GiB) and moments-only", "n": n},
-                    roofline={"bound": "alu", "achieved_gbs_written": gbs, "hbm_frac_of_write": gbs / 6780.7},
-                    moments={"ms_per_step": ms_m, "gsamples_s": n / (ms_m * 1e-3) / 1e9,
-                             "mean": m[0], "m2": m[1], "m3": m[2], "m4": m[3]},
-                    fp64={"n": n64, "ms_per_step": ms_64, "gsamples_s": n64 / (ms_64 * 1e-3) / 1e9,
-                          "hbm_frac_of_write": 8 * n64 / (ms_64 * 1e-3) / 1e9 / 6780.7})
+        n_log2 = args.n_log2 if args.n_log2 != 28 else 32
+        r = fused_leg(qm, dev, stream, n_log2, args.steps, args.warmup)
+        line.update(value=r["written"]["gsamples_s"], ms_per_step=r["written"]["ms"], dtype="f32",
+                    config={"workload": r["workload"], "n": r["n"]}, fused=r)
     elif args.workload == "hyperbolic":
         # exponential -> hyperbolic recycling (alpha, beta, delta) = (1.3, 0.4, 0.7)
         # over 2^n two-sided exponential base samples resident in HBM
@@ -354,7 +539,7 @@ def side_workload(args):
                                         f"({a}, {b}, {d}), n=2^{args.n_log2} two-sided exponential samples"},
                     roofline={"bound": "alu", "note": "FP64 Horner (5 FMA + 1 add per element) on "
                                                       "segment tables; 16 B/element",
-                              "hbm_frac": 16 * n / (ms * 1e-3) / 1e9 / 6780.7})
+                              "hbm_frac": 16 * n / (ms * 1e-3) / 1e9 / peak})
         h.close()
     elif args.workload in ("copula", "tcopula"):
         # Gaussian copula (or t copula with nu = 4), d = 8, equicorrelation
@@ -381,55 +566,24 @@ def side_workload(args):
                     roofline={"bound": "alu", "note": "FP64: d normals (fixed point, 1 DFMA each) + "
                                                       "d(d+1)/2 FMA + t maps per sample; 8 d B written "
                                                       "per sample",
-                              "hbm_frac_of_write": 8 * d * n / (ms * 1e-3) / 1e9 / 6780.7})
+                              "hbm_frac_of_write": 8 * d * n / (ms * 1e-3) / 1e9 / peak})
         c.close()
     elif args.workload == "batch":
-        lens, targets = W.ragged_segments(4, 256, hi=args.batch_hi)
-        spec = []
-        keep = []
-        for j, (nj, tg) in enumerate(zip(lens, targets)):
-            if tg == 8:
-                x = W.exponential(4, nj, 0, j + 1, dev)
-                spec.append((qm.QM_DIST_EXPONENTIAL, qm.QM_DIST_NORMAL, 0.0, x, torch.empty_like(x)))
-            else:
-                x = W.normal_box_muller(4, nj, 0, j + 1, dev)
-                spec.append((qm.QM_DIST_NORMAL, qm.QM_DIST_STUDENT_T, W.NU_SET[tg], x, torch.empty_like(x)))
-        b = qm.Batch(spec)
-        tuning = b.tuning()
-        tot = sum(lens)
-        ms = timed(lambda: b.run(stream), stream, args.steps, args.warmup)
-        ms_sep = timed(lambda: b.run_separate(stream), stream, args.steps, args.warmup)
-        line.update(value=tot / (ms * 1e-3) / 1e9, ms_per_step=ms, dtype="f64",
-                    config={"workload": "ragged recycling batch: 256 segments, lengths log-uniform "
-                                        "[2^10, 2^24] (seed 4), normal->t_nu for nu in {1,2,3,4,5,8,10,30} "
-                                        "and exp->normal", "elements": tot, "tuning": tuning},
-                    separate_launches={"ms_per_step": ms_sep, "value": tot / (ms_sep * 1e-3) / 1e9})
+        r = batch_leg(qm, W, dev, stream, args.batch_hi, args.steps, args.warmup)
+        line.update(value=r["graph"]["gsamples_s"], ms_per_step=r["graph"]["ms"], dtype="f64",
+                    config={"workload": r["workload"], "elements": r["elements"]}, batch=r)
     else:
-        tr = W.serving_trace(5, rate=2e4, seconds=args.serve_seconds)
-        for r in tr:
-            r["id"] = r["key"]
-        tot = sum(r["n"] for r in tr)
-        res = {}
-        for name, mb, st in (("batched", 512, 2), ("plain", 1, 1)):
-            srv = qm.Server(mem_budget=8 << 30, max_batch=mb, streams=st, release_on_done=True)
-            done = srv.replay(tr, timeout_s=900)
-            lat = np.array([c.t_done - c.t_arrival for c in done])
-            span = max(c.t_done for c in done) - min(c.t_arrival for c in done)
-            res[name] = {"gsamples_s": tot / span / 1e9, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
-                         "p99_ms": 1e3 * float(np.percentile(lat, 99)), "makespan_s": span,
-                         "launches": srv.stats()["launches"]}
-            srv.close()
-        line.update(value=res["batched"]["gsamples_s"], ms_per_step=None, dtype="mixed",
-                    config={"workload": f"serving: Poisson 2e4 req/s for {args.serve_seconds} s (seed 5), "
-                                        "n log-uniform [2^8, 2^24], 4 target kinds, 8 GiB budget",
-                            "requests": len(tr), "samples": tot,
-                            "offered_gsamples_s": tot / args.serve_seconds / 1e9},
-                    serving=res)
+        r = serving_leg(qm, W, args.serve_seconds)
+        line.update(value=r["batched"]["gsamples_s"], ms_per_step=None, dtype="mixed",
+                    config={"workload": r["workload"], "requests": r["requests"], "samples": r["samples"],
+                            "offered_gsamples_s": r["offered_gsamples_s"]}, serving=r)
     print(json.dumps(line), flush=True)
 
 
 def main():
     args = parse()
+    if args.record_counters:
+        return record_counters(args.record_counters, 1 << args.n_log2, args.counters_command)
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
@@ -495,37 +649,42 @@ def main():
     ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, pg, dev)
     value = world * n / (ms * 1e-3) / 1e9
 
-    # roofline of the dominant kernel.  k_f64_fixed (the default) runs the
-    # segment polynomial on the integer pipes with one FP64 FMA per element:
-    # it is bound by instruction issue, so its work unit is the issued
-    # thread-instruction (ncu count per element) against the issue peak of
-    # 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz; the HBM and FP64 views
-    # are reported beside it.
+    # roofline of the dominant kernel, on the method's algorithmic work per
+    # element: the slower of its bytes at the measured HBM copy bandwidth and
+    # its arithmetic at the measured issue rates (FIXED: 16 B, one FP64 FMA,
+    # six FP32 FMAs; the branchy FP64 variants: about 45-60 FP64 operations).
     secs = ms * 1e-3
-    hbm_view = {"achieved_gbs": 16 * n / secs / 1e9, "peak_gbs": 6780.7,
-                "frac": 16 * n / secs / 1e9 / 6780.7, "bytes_per_element": 16}
-    if args.variant in ("default", "fixed"):
-        achieved = FIXED_INSTR_PER_ELEM * n / secs / 1e12
-        traffic = FIXED_DRAM_BYTES_PER_ELEM * n if FIXED_DRAM_BYTES_PER_ELEM else None
-        roofline = {"bound": "alu", "kernel": "k_f64_fixed", "achieved": achieved,
-                    "peak": ISSUE_PEAK_TINSTR, "unit": "Tinstr/s", "frac": achieved / ISSUE_PEAK_TINSTR,
-                    "traffic": traffic,
-                    "traffic_note": "DRAM bytes per launch, per-element figure of the 2^24 capture x n "
-                                    "(algorithmic: 16 B/element; writes still in L2 at exit not counted)",
-                    "work_per_element": f"{FIXED_INSTR_PER_ELEM} issued thread-instructions (ncu)",
-                    "peak_source": "issue slots: 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz",
-                    "hbm_view": hbm_view,
-                    "fp64_view": {"dfma_per_element": 1, "achieved_tflops": 2 * n / secs / 1e12,
-                                  "peak_tflops": NOMINAL_FP64_TFLOPS}}
-    else:
-        flops = (n - n_sub - n_edge) * 10 + n_sub * 100
-        achieved = flops / secs / 1e12
-        roofline = {"bound": "alu", "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": None,
-                    "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe table); measured DFMA issue "
-                                   "1.20 TFLOP/s", "hbm_view": hbm_view}
+    peak, peak_src = hbm_peak()
+    gbs = 16 * n / secs / 1e9
+    fixed = args.variant in ("default", "fixed")
+    fp64_ops = 1 if fixed else 50
+    terms = {"hbm_ps": 16 / (peak * 1e9) * 1e12, "fp64_ps": fp64_ops / DFMA_PER_S * 1e12,
+             "fp32_ps": (6 if fixed else 0) / FFMA_PER_S * 1e12}
+    bound = max(terms, key=terms.get)
+    t_elem = secs / n
+    rec = recorded_counters("k_f64_fixed") if fixed else None
+    roofline = {"bound": "hbm" if bound == "hbm_ps" else "alu",
+                "kernel": "k_f64_fixed" if fixed else args.variant,
+                "achieved": gbs if bound == "hbm_ps" else fp64_ops * n / secs / 1e12,
+                "peak": peak if bound == "hbm_ps" else DFMA_PER_S / 1e12,
+                "unit": "GB/s" if bound == "hbm_ps" else "T FP64 FMA/s",
+                "frac": terms[bound] * 1e-12 / t_elem,
+                "peak_source": peak_src if bound == "hbm_ps" else "measured FP64 FMA issue rate (probe)",
+                "traffic": rec["dram_bytes_per_element"] * n if rec else None,
+                "algorithmic_bytes_per_element": 16,
+                "terms_ps_per_element": terms, "measured_ps_per_element": t_elem * 1e12,
+                "hbm_frac_of_nominal_7900": gbs / 7900.0}
+    if rec:
+        # implementation efficiency, not the roofline: the kernel's own issued
+        # instructions (ncu, on these sources) against the issue-slot peak
+        roofline["issue_view"] = {"inst_per_element": rec["inst_per_element"],
+                                  "achieved_tinstr_s": rec["inst_per_element"] * n / secs / 1e12,
+                                  "peak_tinstr_s": ISSUE_PEAK_TINSTR,
+                                  "frac": rec["inst_per_element"] * n / secs / 1e12 / ISSUE_PEAK_TINSTR,
+                                  "counters": "profiles/counters.json (" + rec["command"] + ")"}
 
     extras = {}
+    legs = {}
     cpu = None
     e2e = None
     if not args.no_extras and rank == 0:
@@ -585,7 +744,7 @@ def main():
             torch.cuda.synchronize(dev)
             t = ev_a.elapsed_time(ev_b) / 5
             extras[f"fp32_{name}"] = {"ms": t, "gsamples_s": n / (t * 1e-3) / 1e9,
-                                      "hbm_frac": 8 * n / (t * 1e-3) / 1e9 / 6780.7}
+                                      "hbm_frac": 8 * n / (t * 1e-3) / 1e9 / peak}
         del u32, z32
         z = torch.empty_like(u)
         # end to end through the C ABI with host buffers (pinned): the kernel
@@ -647,6 +806,18 @@ def main():
                                                 "kernel, copy out"}}
         del hu, hz
         cpu = cpu_oracle_leg(n)
+        if not args.no_legs:
+            # the other configurations of the metric, each with its own clocks:
+            # fused generate+transform at 2^32 (moments asserted within 5
+            # sigma), the ragged batch (graph vs one launch per segment), and
+            # the serving trace (continuous batching vs one launch per request)
+            del u, z
+            torch.cuda.empty_cache()
+            legs["fused"] = fused_leg(qm, dev, stream, gpu_index=local)
+            torch.cuda.empty_cache()
+            legs["batch"] = batch_leg(qm, W, dev, stream, gpu_index=local)
+            torch.cuda.empty_cache()
+            legs["serving"] = serving_leg(qm, W, args.serve_seconds, gpu_index=local)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Gsamples/s", "n_gpus": world,
@@ -660,7 +831,7 @@ def main():
                            "dominant_kernel": "k_f64_fixed" if args.variant in ("default", "fixed")
                                               else args.variant},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": args.steps, "clocks": clocks, "variants": extras}
+                "gpu_launches": args.steps, "clocks": clocks, "variants": extras, **legs}
         print(json.dumps(line), flush=True)
     if pg is not None:
         pg.barrier()
