@@ -614,7 +614,8 @@ def main():
                 "compact": qm.QM_VAR_COMPACT,
                 "branchfree": qm.QM_VAR_BRANCHFREE, "hybrid_vote": qm.QM_VAR_HYBRID_VOTE,
                 "mixed_halley": qm.QM_VAR_MIXED_HALLEY, "almost_normal": qm.QM_VAR_ALMOST_NORMAL,
-                "t2_multi": qm.QM_VAR_T2_MULTI, "cuda_normcdfinv": qm.QM_VAR_CUDA_LIBM}
+                "t2_multi": qm.QM_VAR_T2_MULTI, "paper_exact": qm.QM_VAR_PAPER_EXACT,
+                "paper_exact_b": qm.QM_VAR_PAPER_EXACT_B, "cuda_normcdfinv": qm.QM_VAR_CUDA_LIBM}
     var = variants[args.variant]
     u = W.mixture_f64(2, n, first=shard_first(rank, n), device=dev)
     z = torch.empty_like(u)
@@ -704,7 +705,7 @@ def main():
             torch.cuda.synchronize(dev)
             t = ev_a.elapsed_time(ev_b) / reps
             extras[f"fp64_{name}"] = {"ms": t, "gsamples_s": n / (t * 1e-3) / 1e9}
-            if name == "hybrid_vote":
+            if name in ("hybrid_vote", "paper_exact"):
                 extras[f"fp64_{name}"]["votes_taking_t2"] = vote_t2_fraction(u)
         # the branchy variants on 53-bit uniforms alone (seed 8, no tail
         # stress): the inputs where the vote and the extra t_2 branch matter
@@ -712,7 +713,8 @@ def main():
         uu = W.uniform53(8, n, device=dev)
         zu = torch.empty_like(uu)
         uni = {}
-        for name in ("fixed", "compact", "hybrid_vote", "t2_multi", "almost_normal"):
+        for name in ("fixed", "compact", "hybrid_vote", "t2_multi", "almost_normal", "paper_exact",
+                     "paper_exact_b"):
             v = variants[name]
             qm.qm_normal_quantile_f64(uu, zu, v, stream=stream)
             torch.cuda.synchronize(dev)
@@ -723,7 +725,7 @@ def main():
             torch.cuda.synchronize(dev)
             t = ev_a.elapsed_time(ev_b) / 3
             uni[name] = {"ms": t, "gsamples_s": n / (t * 1e-3) / 1e9}
-            if name == "hybrid_vote":
+            if name in ("hybrid_vote", "paper_exact"):
                 uni[name]["votes_taking_t2"] = vote_t2_fraction(uu)
         extras["fp64_uniform53_only"] = uni
         del uu, zu
@@ -733,7 +735,8 @@ def main():
         _, u32 = W.uniform24(1, n, device=dev)
         z32 = torch.empty_like(u32)
         for name, v in (("table", qm.QM_VAR_TABLE), ("sqrt_form", qm.QM_VAR_SQRT_FORM),
-                        ("paper_form", qm.QM_VAR_BRANCHFREE), ("almost_normal", qm.QM_VAR_ALMOST_NORMAL),
+                        ("paper_form", qm.QM_VAR_BRANCHFREE), ("paper_exact", qm.QM_VAR_PAPER_EXACT),
+                        ("almost_normal", qm.QM_VAR_ALMOST_NORMAL),
                         ("cuda_normcdfinvf", qm.QM_VAR_CUDA_LIBM)):
             qm.qm_normal_quantile_f32(u32, z32, v, stream=stream)
             torch.cuda.synchronize(dev)

@@ -94,12 +94,28 @@ typedef enum {
                                 on pieces of the sqrt(a) axis; polynomials
                                 only (no divide).  FP64: one Horner loop over a
                                 per-lane coefficient row (no branch).           */
-    QM_VAR_T2_MULTI = 10     /* FP64: the hybrid with more branches (Sec. 7.4):
+    QM_VAR_T2_MULTI = 10,    /* FP64: the hybrid with more branches (Sec. 7.4):
                                 t_2 coordinate for v <= 1000 (the Sec. 7.3
                                 rational on v <= 15.5, a second (14,15) t_2
                                 rational on the near tail 15.5 < v <= 1000,
                                 coefficients selected per lane), the rest
                                 compacted per tile onto the exponential form.  */
+    QM_VAR_PAPER_EXACT = 11, /* reproduction of the paper's own kernels from its
+                                printed coefficients and arithmetic.  FP32: the
+                                (5,6) rational of Sec. 6.1 / Appendix A, with
+                                the fast logarithm and division.  FP64: the
+                                Appendix C hybrid, t_2 (14,15) rational when the
+                                whole warp (32 consecutive elements) has
+                                v < 15.5 (Sec. 7.3), else the Appendix B
+                                (13,13) exponential-coordinate rational.
+                                Certified by the paper on v <= 25 (FP32) and
+                                u >= 2.875e-19 (FP64); beyond, the printed
+                                rationals are extrapolated as printed (no
+                                deep-tail piece), and the FP32 form returns NaN
+                                for u below 2^-127.  Edges as in the contract. */
+    QM_VAR_PAPER_EXACT_B = 12 /* FP64: the branch-free Appendix B kernel alone
+                                (Sec. 7.2), printed (13,13) coefficients, log,
+                                rounded reciprocal; same domain as above.      */
 } qm_variant;
 
 typedef struct {
@@ -108,9 +124,10 @@ typedef struct {
 
 /* ---- normal quantile ------------------------------------------------------
  * z[i] = Phi^{-1}(u[i]) for i < n (Sec. 1, Eq. 1).  FP32 variants: DEFAULT,
- * BRANCHFREE, SQRT_FORM, TABLE, ALMOST_NORMAL, CUDA_LIBM; FP64 variants:
- * DEFAULT, BRANCHFREE, HYBRID_VOTE, MIXED_HALLEY, COMPACT, TABLE, FIXED,
- * ALMOST_NORMAL, T2_MULTI, CUDA_LIBM (others: QM_ERR_INVALID).
+ * BRANCHFREE, SQRT_FORM, TABLE, ALMOST_NORMAL, CUDA_LIBM, PAPER_EXACT; FP64
+ * variants: DEFAULT, BRANCHFREE, HYBRID_VOTE, MIXED_HALLEY, COMPACT, TABLE,
+ * FIXED, ALMOST_NORMAL, T2_MULTI, CUDA_LIBM, PAPER_EXACT, PAPER_EXACT_B
+ * (others: QM_ERR_INVALID).
  * u, z: contiguous arrays of n elements, in device memory or in page-locked
  * host memory (cudaHostAlloc / cudaHostRegister; with unified addressing its
  * pointer is a device pointer): the kernel then streams the data over the

@@ -17,7 +17,7 @@ QM_OK, QM_ERR_INVALID, QM_ERR_UNSUPPORTED, QM_ERR_CUDA, QM_ERR_NOMEM, QM_ERR_TIM
 QM_DIST_UNIFORM, QM_DIST_NORMAL, QM_DIST_STUDENT_T, QM_DIST_EXPONENTIAL = range(4)
 (QM_VAR_DEFAULT, QM_VAR_BRANCHFREE, QM_VAR_HYBRID_VOTE, QM_VAR_MIXED_HALLEY,
  QM_VAR_COMPACT, QM_VAR_SQRT_FORM, QM_VAR_CUDA_LIBM, QM_VAR_TABLE, QM_VAR_FIXED,
- QM_VAR_ALMOST_NORMAL, QM_VAR_T2_MULTI) = range(11)
+ QM_VAR_ALMOST_NORMAL, QM_VAR_T2_MULTI, QM_VAR_PAPER_EXACT, QM_VAR_PAPER_EXACT_B) = range(13)
 
 LIB_PATH = _build.LIB
 

@@ -15,6 +15,10 @@ bool bad_overlap(const void* a, size_t abytes, const void* b, size_t bbytes);
 // FP64 normal quantile, fixed-point segment evaluation (qm_fixed.cu); u and z
 // device arrays of n doubles, in place allowed; stream is a cudaStream_t.
 qm_status launch_f64_fixed(const double* u, double* z, size_t n, void* stream);
+// The paper's own kernels from its printed coefficients (qm_paper.cu):
+// Appendix A in FP32; Appendix C (with_vote = 1) or Appendix B in FP64.
+qm_status launch_paper_f32(const float* u, float* z, size_t n, void* stream);
+qm_status launch_paper_f64(const double* u, double* z, size_t n, int with_vote, void* stream);
 // Device address of the fixed-point FP64 table (fxt::SEG_FX) on the current
 // device, or NULL with *st set.
 const void* fx_table_device(qm_status* st);

@@ -807,6 +807,7 @@ extern "C" qm_status qm_normal_quantile_f32(const float* u, float* z, size_t n, 
     case QM_VAR_BRANCHFREE: return launch_map(u, z, n, F32Paper(), s, "f32 branch-free");
     case QM_VAR_CUDA_LIBM: return launch_map(u, z, n, F32Libm(), s, "f32 normcdfinvf");
     case QM_VAR_ALMOST_NORMAL: return launch_map(u, z, n, F32AlmostNormal(), s, "f32 almost-normal");
+    case QM_VAR_PAPER_EXACT: return launch_paper_f32(u, z, n, stream);
     case QM_VAR_DEFAULT:
     case QM_VAR_TABLE: {
         if ((uintptr_t)u % 16 != 0 || (uintptr_t)z % 16 != 0)
@@ -833,6 +834,8 @@ extern "C" qm_status qm_normal_quantile_f64(const double* u, double* z, size_t n
     case QM_VAR_CUDA_LIBM: return launch_map(u, z, n, F64Libm(), s, "f64 normcdfinv");
     case QM_VAR_DEFAULT:
     case QM_VAR_FIXED: return launch_f64_fixed(u, z, n, stream);
+    case QM_VAR_PAPER_EXACT: return launch_paper_f64(u, z, n, 1, stream);
+    case QM_VAR_PAPER_EXACT_B: return launch_paper_f64(u, z, n, 0, stream);
     case QM_VAR_HYBRID_VOTE: {
         const int g = grid_for(k_f64_hybrid_vote<2>, 256, (n + 1) / 2);
         k_f64_hybrid_vote<2><<<g, 256, 0, s>>>(u, z, n);
