@@ -26,24 +26,40 @@ stored re-expanded in tau' = tau - 2^(K-52) = (Tu - 1) 2^(K-52) in
 [0, 1 - 2^(K-52)] (an exact change of expansion point, so the same
 polynomial): tau' 2^64 = (Tu - 1) << (12 + K) always fits 64 bits.
 
+Every coefficient beta_k is positive on every segment (asserted below): the
+tail quantile |Phi^{-1}| as a function of the offset back from the segment
+end has all its derivatives positive, so every Horner accumulator is
+non-negative and the chain runs on unsigned integers.
+
 On GB300 the FP64 pipe issues about 1/62 of the FP32 rate, so beta_0..beta_2
-are applied by a fixed-point Horner chain on 64-bit integers with tau' as an
-unsigned Q0.64 number (acc_k = B_k + mulhi(acc_{k+1}, tau' 2^64), every acc in
-units of 2^s0), beta_3..beta_6 by a single-precision chain F on the
-coefficients f_k = beta_k 2^-s0 (already in the accumulator's units), which
-enters as acc_2 = B_2 + rn(F tau'): F tau' is formed in single precision from
-the exact split tau' = th 2^-23 + tl 2^-46 of the integer offset (one
-multiply and one FMA) and converted to int64 rounding to nearest even; then
-z = fma(t_u, acc_0 2^s0, a_0), with t_u = (1 + t_u) - 1 formed exactly by one
-double-precision add.
+are applied by a fixed-point Horner chain on 64-bit unsigned integers in the
+half offset th = tau'/2 in [0, 1/2), an unsigned Q0.64 number below 2^63, on
+the coefficients beta'_k = beta_k 2^k (the same polynomial in th):
+acc_k = B_k + floor(acc_{k+1} th 2^64 / 2^64), every acc in units of 2^s0 and
+below 2^62.  With both factors that small, the 128-bit product's high half
+is exact from four 32 x 32 -> 64-bit multiply-adds with no carry out.
+beta'_3..beta'_6 go through a single-precision chain F on f_k = beta'_k 2^-s0
+(already in the accumulator's units), which enters as acc_2 = B_2 + rn(F th):
+F th is formed in single precision from the exact split
+th = hi 2^-24 + lo 2^-47 of the integer offset (one multiply and one FMA),
+and converted to an integer rounding to nearest even, exactly, as two 32-bit
+halves (G = g_h 2^24 + g_l).  s0 puts H(0) 2^-s0 in [2^61, 2^62), and H
+varies by less than a factor 2 across a segment (asserted; at most 1.6 %), so
+acc_0 lies in [2^61, 2^63): its leading bit is bit 61 or 62, and H becomes a
+double by one rounding shift and one add of the exponent field
+(e0 + top) << 52, e0 = 1083 + s0 stored per segment, the significand's
+implicit bit carrying into the exponent.  Then z = fma(t_u, H, a_0), with
+t_u = (1 + t_u) - 1 formed exactly by one double-precision add.
 
 Binades: e = -1 - E in [0, 1072], 64 segments each (K = 6), so every
 double 0 < u < 1 (subnormal u included: x is normalised as an integer)
-falls in a segment.
+falls in a segment.  The table starts with 64 zero rows for e = -1, i.e.
+x = 1 exactly (u = 1/2): a0 = 0 and H = +0 there (an all-zero accumulator
+with a zero exponent field assembles to +0), so z = +0 needs no branch.
 
 Entry: two arrays, so that a lane gathers 48 bytes with one 256-bit and one
-128-bit load: A[i] = {a0 (double), B0, B1 (int64), B2 | s0 << 52} (32 bytes;
-B2 in the low 52 bits, sign extended, s0 in the top 12) and
+128-bit load: A[i] = {a0 (double), B0, B1 (uint64), B2 | e0 << 52} (32 bytes;
+B2 in the low 52 bits, e0 in the top 12) and
 F[i] = {f3, f4, f5, f6} (float, 16 bytes).
 
 The generator checks every segment by emulating the kernel's integer and
@@ -134,41 +150,62 @@ def shift_poly(beta, delta):
 def quantise(e, j, K, g):
     beta = [g[k + 1] * mp.mpf(2) ** (-K * k) for k in range(DEG)]
     beta = shift_poly(beta, mp.mpf(2) ** (K - 52))             # argument tau' = tau - 2^(K-52)
-    assert beta[0] > 0, (e, j)
-    hmax = sum(abs(x) for x in beta)                              # tau in [0, 1]
-    s0 = int(mp.floor(mp.log(hmax, 2))) + 1 - 62                  # |acc| < 2^62
-    B = [int(mp.nint(beta[k] / mp.mpf(2) ** s0)) for k in range(NI)]
-    assert abs(B[2]) < 2**51 and -2**11 <= s0 < 2**11, (e, j, B[2], s0)   # B2 | s0 << 52
-    bf = [f32(beta[k] / mp.mpf(2) ** s0) for k in range(NI, DEG)]
-    for x in bf:                                                   # normal floats (or 0)
-        assert x == 0 or 2.0**-126 <= abs(x) < 2.0**62, (e, j, x)
-    return {"a0": float(g[0]), "B": B, "bf": bf, "s0": s0}
+    assert all(b > 0 for b in beta), (e, j)                       # unsigned fixed point
+    bh = [beta[k] * mp.mpf(2) ** k for k in range(DEG)]           # argument th = tau'/2
+    assert sum(beta) < 2 * beta[0], (e, j)                        # H(1/2) / H(0) < 2
+    s0 = int(mp.floor(mp.log(beta[0], 2))) - 61                   # H(0) 2^-s0 in [2^61, 2^62)
+    B = [int(mp.nint(bh[k] / mp.mpf(2) ** s0)) for k in range(NI)]
+    e0 = 1083 + s0                                                # exponent field base (below)
+    assert 0 < B[2] < 2**51 and 0 < e0 < 2**11, (e, j, B[2], s0)  # B2 | e0 << 52
+    bf = [f32(bh[k] / mp.mpf(2) ** s0) for k in range(NI, DEG)]
+    for x in bf:                                                   # normal floats
+        assert 2.0**-126 <= x < 2.0**62, (e, j, x)
+    return {"a0": float(g[0]), "B": B, "bf": bf, "s0": s0, "e0": e0}
+
+
+def mulhi_limbs(a, b):
+    """floor(a b / 2^64) as the kernel forms it from 32-bit limbs (a < 2^62,
+    b < 2^63): a1 b1 + hi32(a0 b1 + a1 b0 + hi32(a0 b0)), with no partial sum
+    reaching 2^64.  Equal to the exact high half."""
+    a0, a1, b0, b1 = a & 0xFFFFFFFF, a >> 32, b & 0xFFFFFFFF, b >> 32
+    m1 = a1 * b0 + ((a0 * b0) >> 32)
+    m2 = a0 * b1 + m1
+    assert m2 < 2**64
+    r = a1 * b1 + (m2 >> 32)
+    assert r == (a * b) >> 64
+    return r
 
 
 def emulate(q, K, Tu):
     """The kernel's arithmetic for the integer offset Tu; returns the double z."""
     Tp = Tu - 1                                                   # the kernel's ~m & (2^(52-K) - 1)
-    Tau = Tp << (12 + K)                                          # tau' 2^64
-    assert 0 <= Tau < 2**64
-    tf = f32(float(Tp >> 25)) * 2.0 ** (K - 27)
+    Tau = Tp << (11 + K)                                          # th 2^64 = tau' 2^63
+    assert 0 <= Tau < 2**63
+    tf = f32(float(Tp >> 25)) * 2.0 ** (K - 28)
     F = np.float32(q["bf"][-1])
     for cf in reversed(q["bf"][:-1]):
         F = np.float32(float(F) * tf + cf)
-    # innermost step in single precision: tau' = Tp 2^-46 = th 2^-23 + tl 2^-46
-    # exactly; G = fl(fl(F 2^-23 th) + F 2^-46 tl) (a multiply, then one FMA)
+    # innermost step in single precision: th = Tp 2^-47 = hi 2^-24 + lo 2^-47
+    # exactly; G = fl(fl(F 2^-24 hi) + F 2^-47 lo) (a multiply, then one FMA)
     th, tl = float(Tp >> 23), float(Tp & 0x7FFFFF)
-    f23 = float(F) * 2.0 ** -23
-    p = np.float32(f23 * th)
-    G = np.float32(float(Fraction(f23 * 2.0 ** -23) * Fraction(tl) + Fraction(float(p))))
-    acc = q["B"][NI - 1] + int(np.rint(float(G)))                 # float -> int64, nearest even
-    assert abs(acc) < 2**63
-    for k in reversed(range(NI - 1)):
-        acc = q["B"][k] + ((acc * Tau) >> 64)
-        assert abs(acc) < 2**63
-    assert 0 < acc < 2**62
-    lz = 64 - acc.bit_length()
-    mant = ((acc << lz) + 0x400) >> 11                            # rounded 53-bit significand
-    hd = float(Fraction(mant) * Fraction(2) ** (63 - lz - 52 + q["s0"]))
+    f24 = float(F) * 2.0 ** -24
+    p = np.float32(f24 * th)
+    G = np.float32(float(Fraction(f24 * 2.0 ** -23) * Fraction(tl) + Fraction(float(p))))
+    assert 0 <= float(G) < 2.0**48                                # two 24-bit halves
+    gh = int(float(G) * 2.0 ** -24)                               # truncated high half
+    gl = float(G) - gh * 2.0**24                                  # exact
+    acc = q["B"][NI - 1] + gh * 2**24 + int(np.rint(gl))          # = B2 + rint(G)
+    assert acc == q["B"][NI - 1] + int(np.rint(float(G))) and acc < 2**62
+    acc = q["B"][1] + mulhi_limbs(acc, Tau)
+    assert acc < 2**62
+    acc = q["B"][0] + mulhi_limbs(acc, Tau)
+    assert 2**61 <= acc < 2**63                                   # leading bit 61 or 62
+    top = acc >> 62
+    mant = (acc + (256 << top)) >> (9 + top)                      # rounded 53-bit significand
+    hd = float(Fraction(mant) * Fraction(2) ** (9 + top + q["s0"]))
+    # the kernel's bit assembly: mant (implicit bit included) + (e0 + top) << 52
+    bits = mant + ((q["e0"] + top) << 52)
+    assert np.frombuffer(np.uint64(bits).tobytes(), dtype=np.float64)[0] == hd
     t = Fraction(Tu) * Fraction(2) ** -52
     return float(t * Fraction(hd) + Fraction(q["a0"]))
 
@@ -225,22 +262,27 @@ def main():
         "// re-expanded about the segment end and stored for fixed-point evaluation:\n",
         "// G = a0 + t_u H, H = sum beta_k tau'^k > 0, tau' = (m_end - m) 2^K - 2^(K-52)\n",
         "// in [0, 1) (t_u = m_end - m),\n",
-        "// beta_0..2 as int64 B_k = beta_k 2^-s0 (A: a0, B0, B1, B2 | s0 << 52),\n",
-        "// beta_3..6 as float f_k = beta_k 2^-s0 (F).\n",
-        f"// Binade e = -1 - E = 0..{E_LAST}, {2**K_MAIN} segments each; index e 2^{K_MAIN} + j.\n",
+        "// in the half offset th = tau'/2: beta'_k = beta_k 2^k, all positive;\n",
+        "// beta'_0..2 as integers B_k = beta'_k 2^-s0 (A: a0, B0, B1, B2 | e0 << 52,\n",
+        "// e0 = 1083 + s0, H(0) 2^-s0 in [2^61, 2^62)),\n",
+        "// beta'_3..6 as float f_k = beta'_k 2^-s0 (F).\n",
+        f"// Binade e = -1 - E = 0..{E_LAST}, {2**K_MAIN} segments each; index (e + 1) 2^{K_MAIN} + j;\n",
+        f"// rows 0..{2**K_MAIN - 1} (e = -1, x = 1 exactly: u = 1/2) are zero, so that z = +0 there.\n",
         f"// Emulated worst relative error over the checked points: {worst:.3g}.\n",
         "#pragma once\n#include \"qm_fx.cuh\"   // layout (K, E_LAST, N_ALL, FxTable) and evaluation\n\n",
         "namespace qm {\nnamespace fxt {\n\n",
         "__device__ const FxTable SEG_FX = {\n {\n",
     ]
+    lines += ["  {0x0p+0,0ll,0ll,0ll},\n"] * 2**K_MAIN          # e = -1: a0 = 0, H = +0
     for e, j, q, _ in res:
         B = q["B"]
-        b2s = ((q["s0"] & 0xFFF) << 52) | (B[2] & (2**52 - 1))
+        b2s = (q["e0"] << 52) | B[2]
         if b2s >= 2**63:
             b2s -= 2**64
         lits = [f"{b}ll" for b in B[:2]] + [f"{b2s}ll" if b2s != -2**63 else "(-0x7fffffffffffffffll - 1)"]
         lines.append("  {" + hexd(q["a0"]) + "," + ",".join(lits) + "},\n")
     lines.append(" },\n {\n")
+    lines += ["  {0x0p+0f,0x0p+0f,0x0p+0f,0x0p+0f},\n"] * 2**K_MAIN
     for e, j, q, _ in res:
         lines.append("  {" + ",".join(hexf(x) for x in q["bf"]) + "},\n")
     lines.append(" }\n};\n\n}  // namespace fxt\n}  // namespace qm\n")
