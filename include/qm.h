@@ -215,7 +215,11 @@ qm_status qm_sample_moments_noalloc(uint64_t key, uint64_t ctr0, size_t n,
  * Sec. 3.2 integrated from the tail coordinate of Sec. 3.3, see
  * qm_t_table_build -- then uploaded (a synchronous cudaMalloc + copy of
  * ~18 KB, kept until exit; at most 256 distinct nu per process, then
- * QM_ERR_NOMEM); nu outside both: QM_ERR_UNSUPPORTED);
+ * QM_ERR_NOMEM); nu outside both: QM_ERR_UNSUPPORTED).  On upload every
+ * segment is re-expanded about its start and stored for evaluation in 64-bit
+ * fixed point with one FP64 FMA (the offline tables too, at the first use
+ * on a device); a table whose coefficients fail the conversion's sign or
+ * range checks is refused with QM_ERR_UNSUPPORTED;
  * (EXPONENTIAL, NORMAL): out = Phi^{-1}(1 - e^{-in}) (Sec. 2.3, Sec. 6);
  * (UNIFORM, NORMAL): out = Phi^{-1}(in) (FP64 default variant).
  * Anything else: QM_ERR_UNSUPPORTED.  in, out: double[n] (device).        */
@@ -353,8 +357,9 @@ qm_status qm_tcopula_table_build(double nu, double* chi_seg, double* g_seg, int*
  * or out-of-range nu, null pointers, in/out partial overlap and overlapping
  * outputs of two segments are rejected (QM_ERR_INVALID / QM_ERR_UNSUPPORTED).
  * Tuning: block in {128, 256, 512}, ept in {1, 2, 4}, estrin in {0, 1}
- * (Estrin instead of Horner for the Student-t segment polynomial; the two
- * round differently, so bit-exact comparisons need the same choice).  With
+ * (Estrin instead of Horner for the single-precision part of the Student-t
+ * segment polynomial; the two round differently, so bit-exact comparisons
+ * need the same choice).  With
  * tuning == NULL the tuning cache ($QM_TUNE_CACHE, default
  * ~/.cache/qm_tune.txt) is consulted, else (256, 2, 0).  The batch owns its
  * device table and graph; the caller owns the data arrays.                  */

@@ -318,7 +318,7 @@ static void worker_loop(qm_server* s)
                     const void* tseg = nullptr;
                     const double* ttail = nullptr;
                     t_select(c.nu, &d.t.k, &tseg, &ttail);   // validated (and built) at submit
-                    d.t.seg = (const ttbl::SegT*)tseg;
+                    d.t.seg = (const ttbl::SegTX*)tseg;
                     d.t.tail = ttail;
                 }
                 d.tile0 = t0;
@@ -372,7 +372,20 @@ extern "C" qm_status qm_server_create(const qm_server_config* cfg, qm_server** o
     }
     {
         qm_status fst;
-        if (!fx_table_device(&fst)) return fst;      // the worker's kernels read this table
+        if (!fx_table_device(&fst)) {                 // the worker's kernels read this table
+            delete s;
+            return fst;
+        }
+        // the offline Student-t tables (converted to their device form at
+        // first use) are built here, not at the first Student-t request
+        int tk = 0;
+        const void* tseg = nullptr;
+        const double* ttail = nullptr;
+        const qm_status tst = t_select(ttbl::T_NU[0], &tk, &tseg, &ttail);
+        if (tst != QM_OK) {
+            delete s;
+            return tst;
+        }
     }
     if (!s->arena.init(cfg->mem_budget)) {
         delete s;

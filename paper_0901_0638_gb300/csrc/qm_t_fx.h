@@ -1,0 +1,52 @@
+// qm_t_fx.h -- layout of the Student-t segment rows as the device evaluates
+// them: the normal -> t_nu recycling map (Sec. 3) in 64-bit fixed point with
+// one FP64 FMA per element.
+//
+// The host tables (offline fits for the tabulated nu, or tables built at run
+// time for any other nu) hold, per segment j of width 1/32 on 0 <= |z| < 8.75,
+// the coefficients c_0..c_9 of the expansion in s = |z| - (j + 1/2)/32 (in
+// s = |z| for j = 0, the central series).  Before upload every segment is
+// re-expanded about its start z_j = j/32 (sigma = |z| - z_j in [0, 1/32);
+// z_0 = 0): on every segment of every nu these coefficients are non-negative
+// (the map is absolutely monotone on z > 0; checked at conversion), so
+//
+//     |t| = a0 + sigma P,   P = sum_k d_k tau^k,   tau = 16 sigma in [0, 1/2),
+//
+// with d_k = c'_{k+1} 16^-k >= 0, runs on unsigned integers: d_0..d_4 as
+// integers D_k = d_k 2^-s0 (s0 puts D_0 in [2^59, 2^60], which keeps D_4
+// below 2^52 beside the exponent field; P varies by less than a factor 2
+// across a segment, so the accumulator stays in [2^59, 2^61)), a
+// Horner chain acc = D_k + floor(acc tau), and d_5..d_8 as single-precision
+// f_k = d_k 2^-s0 whose chain enters the d_4 step (the d_5 term is at most
+// ~4e-6 of |t|, for nu = 0.75 at |z| = 8.75, so single precision costs it
+// ~2e-13).  P becomes a double by one rounding shift and the exponent field
+// e0 = 1081 + s0, and |t| = fma(sigma, P, a0) is the one FP64 operation
+// besides the exact sigma = |z| - z_j.
+#pragma once
+#include <stdint.h>
+
+#include "qm.h"
+
+namespace qm {
+namespace ttbl {
+
+struct alignas(64) SegTX {
+    double a0;                      // |t| at the segment start
+    unsigned long long D0, D1, D2;  // d_0..d_2 2^-s0
+    unsigned long long D3;          // d_3 2^-s0
+    unsigned long long D4e;         // d_4 2^-s0 (below 2^52) | e0 << 52
+    float f[4];                     // d_5..d_8 2^-s0
+};
+static_assert(sizeof(SegTX) == 64, "one 64-byte row per segment");
+
+}  // namespace ttbl
+
+// Converts nseg segment rows of coefficients c_0..c_9 (seg10[10 j + k],
+// expansion about the segment centre (j + 1/2)/32, about 0 for j = 0) into
+// the fixed-point rows above.  Checks the sign, range and accuracy conditions
+// (the conversion is re-evaluated at points of every segment against the
+// original polynomial, within 1e-13 relative); QM_ERR_UNSUPPORTED if a
+// segment violates one.
+qm_status t_pack_fx(const double* seg10, int nseg, ttbl::SegTX* out);
+
+}  // namespace qm

@@ -33,6 +33,7 @@
 
 #include "qm.h"
 #include "qm_host.h"
+#include "qm_t_fx.h"
 #include "qm_t_tables.h"
 
 namespace qm {
@@ -245,12 +246,89 @@ qm_status t_table_build(double nu_d, double* seg, double* tail)
     return QM_OK;
 }
 
+// Segment rows in the fixed-point form of qm_t_fx.h (280 rows per nu).  The
+// re-expansion is done in double: its k = m term dominates every sum, so the
+// rounding stays at a few ulp, far inside the map's 1e-12 bound (and long
+// double is a software quad type on some hosts, slow at first use).
+qm_status t_pack_fx(const double* seg10, int nseg, ttbl::SegTX* out)
+{
+    static const double binom[10][10] = {
+        {1}, {1, 1}, {1, 2, 1}, {1, 3, 3, 1}, {1, 4, 6, 4, 1}, {1, 5, 10, 10, 5, 1},
+        {1, 6, 15, 20, 15, 6, 1}, {1, 7, 21, 35, 35, 21, 7, 1}, {1, 8, 28, 56, 70, 56, 28, 8, 1},
+        {1, 9, 36, 84, 126, 126, 84, 36, 9, 1}};
+    for (int j = 0; j < nseg; ++j) {
+        const double* c = seg10 + 10 * j;
+        double cp[10];
+        const double dl = (j == 0) ? 0.0 : -1.0 / 64;          // s = sigma + dl
+        for (int m = 0; m < 10; ++m) {
+            double acc = 0.0, p = 1.0;
+            for (int k = m; k < 10; ++k) {
+                acc += (double)c[k] * binom[k][m] * p;
+                p *= dl;
+            }
+            cp[m] = acc;
+        }
+        double d[9];
+        for (int k = 0; k < 9; ++k) d[k] = ldexp(cp[k + 1], -4 * k);
+        if (!(d[0] > 0.0))
+            return fail(QM_ERR_UNSUPPORTED, "Student t: segment %d has a non-positive slope", j);
+        for (int k = 1; k < 9; ++k) {
+            if (d[k] < 0.0) {
+                if (-d[k] > 1e-18 * d[0])
+                    return fail(QM_ERR_UNSUPPORTED, "Student t: segment %d coefficient %d negative", j, k);
+                d[k] = 0.0;                                          // rounding residue
+            }
+        }
+        double pmax = 0.0;
+        for (int k = 0; k < 9; ++k) pmax += ldexp(d[k], -k);         // P at tau = 1/2
+        if (!(pmax < 2.0 * d[0]))
+            return fail(QM_ERR_UNSUPPORTED, "Student t: segment %d varies too fast", j);
+        int e2 = 0;
+        frexp(d[0], &e2);                                            // d_0 in [2^(e2-1), 2^e2)
+        const int s0 = e2 - 60;                                       // D_0 in [2^59, 2^60]
+        unsigned long long D[5];
+        for (int k = 0; k < 5; ++k) D[k] = (unsigned long long)llround(ldexp(d[k], -s0));
+        const int e0 = 1081 + s0;
+        float f[4];
+        double gmax = 0.0;                                      // F tau at tau = 1/2
+        for (int k = 0; k < 4; ++k) {
+            f[k] = (float)ldexp(d[k + 5], -s0);
+            gmax += ldexp((double)f[k], -k - 1);
+        }
+        if (D[4] >= (1ull << 52) || e0 <= 0 || e0 >= 2048 || !(gmax < 281474976710656.0))
+            return fail(QM_ERR_UNSUPPORTED, "Student t: segment %d outside the fixed-point range", j);
+        ttbl::SegTX& r = out[j];
+        r.a0 = (double)cp[0];
+        r.D0 = D[0];
+        r.D1 = D[1];
+        r.D2 = D[2];
+        r.D3 = D[3];
+        r.D4e = D[4] | ((unsigned long long)e0 << 52);
+        for (int k = 0; k < 4; ++k) r.f[k] = f[k];
+        // the stored row against the original expansion at the segment's
+        // start, middle and end (quantisation of a0, D_k and f_k)
+        for (int q = 0; q <= 2; ++q) {
+            const double sig = (q == 0 ? 0.0 : q == 1 ? 1.0 / 64 : 1.0 / 32 - 1.0 / 4096);
+            const double tau = 16.0 * sig, s = sig + dl;
+            double P = 0.0, ref = 0.0;
+            for (int k = 8; k >= 0; --k)
+                P = P * tau + (k < 5 ? ldexp((double)D[k], s0) : ldexp((double)f[k - 5], s0));
+            for (int k = 9; k >= 0; --k) ref = ref * s + (double)c[k];
+            const double got = (double)r.a0 + sig * P;
+            if (ref != 0.0 && fabs(got / ref - 1.0) > 1e-13)
+                return fail(QM_ERR_UNSUPPORTED, "Student t: segment %d fixed-point form off by %g", j,
+                            fabs(got / ref - 1.0));
+        }
+    }
+    return QM_OK;
+}
+
 namespace {
 
 struct Entry {
     int device;
     double nu;
-    ttbl::SegT* seg;     // device, NSEG entries
+    ttbl::SegTX* seg;    // device, NSEG fixed-point rows
     double* tail;        // device, 3 + NT doubles
 };
 
@@ -277,19 +355,16 @@ qm_status t_table_device(double nu, const void** seg_dev, const double** tail_de
     std::vector<double> seg(10 * NSEG), tail(3 + NT);
     const qm_status st = t_table_build(nu, seg.data(), tail.data());
     if (st != QM_OK) return st;
-    std::vector<ttbl::SegT> packed(NSEG);
-    for (int j = 0; j < NSEG; ++j) {
-        for (int k = 0; k < 5; ++k) packed[j].a[k] = seg[10 * j + k];
-        for (int k = 0; k < 5; ++k) packed[j].b[k] = (float)seg[10 * j + 5 + k];
-        packed[j].pad = 0.0f;
-    }
+    std::vector<ttbl::SegTX> packed(NSEG);
+    const qm_status pst = t_pack_fx(seg.data(), NSEG, packed.data());
+    if (pst != QM_OK) return pst;
     Entry e{dev, nu, nullptr, nullptr};
-    if (cudaMalloc(&e.seg, sizeof(ttbl::SegT) * NSEG) != cudaSuccess ||
+    if (cudaMalloc(&e.seg, sizeof(ttbl::SegTX) * NSEG) != cudaSuccess ||
         cudaMalloc(&e.tail, sizeof(double) * tail.size()) != cudaSuccess) {
         if (e.seg) cudaFree(e.seg);
         return fail(QM_ERR_NOMEM, "Student t: table allocation failed");
     }
-    if (cudaMemcpy(e.seg, packed.data(), sizeof(ttbl::SegT) * NSEG, cudaMemcpyHostToDevice) != cudaSuccess ||
+    if (cudaMemcpy(e.seg, packed.data(), sizeof(ttbl::SegTX) * NSEG, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(e.tail, tail.data(), sizeof(double) * tail.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaFree(e.seg);
         cudaFree(e.tail);
@@ -303,12 +378,13 @@ qm_status t_table_device(double nu, const void** seg_dev, const double** tail_de
 
 namespace {
 
-// The offline tables of the tabulated nu, as device pointers: the segments in
-// this module's copy of SEG_T, the tail (nu, log kappa, TAIL_DEG, R_k) in a
-// small buffer built once per device.
+// The offline tables of the tabulated nu, as device pointers: the segments of
+// this module's SEG_T read back once per device and converted to the
+// fixed-point rows (NNU x NSEG), the tail (nu, log kappa, TAIL_DEG, R_k) in a
+// small buffer; both built once per device and kept until exit.
 struct StaticT {
     int device;
-    const ttbl::SegT* seg;
+    ttbl::SegTX* seg;
     double* tail;          // NNU x (3 + TAIL_DEG + 1)
 };
 std::vector<StaticT> g_static;
@@ -322,9 +398,20 @@ qm_status static_tables(int dev, const StaticT** out)
             return QM_OK;
         }
     StaticT e{dev, nullptr, nullptr};
-    void* seg = nullptr;
-    if (cudaGetSymbolAddress(&seg, ttbl::SEG_T) != cudaSuccess)
-        return fail(QM_ERR_CUDA, "Student t: table address lookup failed");
+    std::vector<ttbl::SegT> offline(ttbl::NNU * NSEG);
+    if (cudaMemcpyFromSymbol(offline.data(), ttbl::SEG_T, sizeof(ttbl::SegT) * offline.size()) != cudaSuccess)
+        return fail(QM_ERR_CUDA, "Student t: table read failed");
+    std::vector<double> seg10(10 * NSEG);
+    std::vector<ttbl::SegTX> packed(ttbl::NNU * NSEG);
+    for (int k = 0; k < ttbl::NNU; ++k) {
+        for (int j = 0; j < NSEG; ++j) {
+            const ttbl::SegT& g = offline[k * NSEG + j];
+            for (int c = 0; c < 5; ++c) seg10[10 * j + c] = g.a[c];
+            for (int c = 0; c < 5; ++c) seg10[10 * j + 5 + c] = g.b[c];
+        }
+        const qm_status pst = t_pack_fx(seg10.data(), NSEG, packed.data() + k * NSEG);
+        if (pst != QM_OK) return pst;
+    }
     double kappa[ttbl::NNU], rt[ttbl::NNU][ttbl::TAIL_DEG + 1];
     if (cudaMemcpyFromSymbol(kappa, ttbl::T_KAPPA, sizeof(kappa)) != cudaSuccess ||
         cudaMemcpyFromSymbol(rt, ttbl::T_TAIL, sizeof(rt)) != cudaSuccess)
@@ -339,11 +426,17 @@ qm_status static_tables(int dev, const StaticT** out)
     }
     if (cudaMalloc(&e.tail, sizeof(double) * tail.size()) != cudaSuccess)
         return fail(QM_ERR_NOMEM, "Student t: table allocation failed");
-    if (cudaMemcpy(e.tail, tail.data(), sizeof(double) * tail.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (cudaMalloc(&e.seg, sizeof(ttbl::SegTX) * packed.size()) != cudaSuccess) {
         cudaFree(e.tail);
+        return fail(QM_ERR_NOMEM, "Student t: table allocation failed");
+    }
+    if (cudaMemcpy(e.tail, tail.data(), sizeof(double) * tail.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(e.seg, packed.data(), sizeof(ttbl::SegTX) * packed.size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+        cudaFree(e.tail);
+        cudaFree(e.seg);
         return fail(QM_ERR_CUDA, "Student t: table upload failed");
     }
-    e.seg = (const ttbl::SegT*)seg;
     g_static.push_back(e);
     *out = &g_static.back();
     return QM_OK;

@@ -10,9 +10,11 @@ process and after the other tests.
 """
 import ctypes
 
+import numpy as np
 import pytest
 import torch
 
+import oracle
 import paper_0901_0638_gb300 as qm
 
 pytestmark = pytest.mark.gpu
@@ -47,6 +49,28 @@ def test_noalloc_matches_allocating_path_twice_in_a_row():
         for m in got:
             assert torch.all((m - ref).abs() <= 2 * 67 * 2.0 ** -24 * scale), (m, ref)
         assert torch.equal(got[0], got[1])
+
+
+def test_noalloc_moments_against_oracle_samples():
+    """Independently of the library's other paths: the same samples from
+    the oracle (its own Philox stream and FP64 quantile at the exact grid
+    points (k + 1/2) 2^-24), summed in FP64.  Each device sample is within
+    4 ulp (2^-21 relative) of the exact value, so its k-th power within
+    k 2^-21, plus the FP32 partial sums' (64 + 3) 2^-24."""
+    lib = qm.load()
+    n, key, ctr0 = (1 << 18) + 5, 3, 64
+    k = oracle.philox_stream(key, ctr0, n) >> 8
+    z = oracle.probit((k.astype(np.float64) + 0.5) * 2.0 ** -24)
+    ref = np.array([np.sum(z ** p) for p in (1, 2, 3, 4)])
+    scale = np.array([np.sum(np.abs(z) ** p) for p in (1, 2, 3, 4)])
+    m = torch.full((4,), float("nan"), dtype=torch.float64, device="cuda")
+    st = lib.qm_sample_moments_noalloc(ctypes.c_uint64(key), ctypes.c_uint64(ctr0), ctypes.c_size_t(n),
+                                       ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(None))
+    assert st == qm.QM_OK, qm.qm_last_error()
+    torch.cuda.synchronize()
+    got = m.cpu().numpy()
+    tol = (67 * 2.0 ** -24 + np.array([1, 2, 3, 4]) * 2.0 ** -21) * scale
+    assert np.all(np.abs(got - ref) <= tol), (got, ref)
 
 
 def test_noalloc_rejects_oversize_and_bad_arguments():
