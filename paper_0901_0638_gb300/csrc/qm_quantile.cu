@@ -209,7 +209,7 @@ struct F64T2Multi {
 };
 
 struct ExpToNormal {
-    __device__ double operator()(double x) const { return exp_to_normal_tbl(x); }
+    __device__ double operator()(double x) const { return exp_to_normal_fx(x); }
 };
 
 struct TDynMap {

@@ -62,7 +62,7 @@ k_batch(const DevSeg* __restrict__ segs, int nseg, unsigned long long ntiles, co
             const size_t i = base + (size_t)k * blockDim.x + threadIdx.x;
             double y;
             if (sg.kind == KIND_T) y = recycle_t_sel<ESTRIN>(sg.t, x[k]);
-            else if (sg.kind == KIND_EXP) y = exp_to_normal_tbl(x[k]);
+            else if (sg.kind == KIND_EXP) y = exp_to_normal_fx(x[k]);
             else y = probit_fx<FX_FP64_LEAN>(fxT, x[k]);
             if (i < sg.n) __stcs(sg.out + i, y);
         }
@@ -78,7 +78,7 @@ k_single(const double* __restrict__ in, double* out, size_t n, int kind, TSel t,
         const double x = __ldcs(in + i);
         double y;
         if (kind == KIND_T) y = recycle_t_sel<false>(t, x);
-        else if (kind == KIND_EXP) y = exp_to_normal_tbl(x);
+        else if (kind == KIND_EXP) y = exp_to_normal_fx(x);
         else y = probit_fx<FX_FP64_LEAN>(fxT, x);
         __stcs(out + i, y);
     }

@@ -1,0 +1,219 @@
+"""Generate csrc/qm_exp_fx_tables.h: the exponential -> normal recycling map
+z = Phi^{-1}(1 - e^{-x}) on given Exp(1) samples x (Sec. 2.3, Sec. 6), in the
+fixed-point row form of csrc/qm_t_fx.h (one FP64 FMA per element).
+
+The local expansions are those of gen_exp_tables.py (the exponential-
+background recycling ODE Q'' + Q' = Q Q'^2 composed with each region's
+coordinate).  Each is re-expanded exactly about a point from which |z| has
+non-negative coefficients (asserted here for every row), so the device runs
+one unsigned fixed-point chain for every lane:
+
+* V rows, x >= ln 2 + 1/32 (v = x - ln 2): segments of width w = 1/32 on
+  v < 1 and 1/8 on 1 <= v < 64, about the segment END v_e, in t = v_e - v:
+      |z| = a0 - t H(t),   H >= 0,   tau = 2^k t (k = 3, or 1 for w = 1/8).
+* V row 0, -1/64 <= v < 1/32 (the central piece, z through 0 at x = ln 2):
+      z = v P(t),  t = 1/32 - v,  P(v) = Q(v)/v from the series about v = 0,
+      re-expanded about v = 1/32, tau = 8 t.
+* X rows, 2^-26 <= x < ln 2 - 1/64: binades 2^E <= x < 2^(E+1), 32 segments
+  each, in the offset t_u = m_end - m of the significand m of x back from the
+  segment end (Tu = Tp + 1 integer, t_u = Tu 2^-52):
+      |z| = a0 + t_u H,   tau = Tp 2^-48 in [0, 1/2),   z = -|z|.
+H (or P) = sum_k d_k tau^k: d_0..d_4 as integers D_k = d_k 2^-s0 (D_0 in
+[2^59, 2^60]), d_5..d_8 as floats, e0 = 1081 + s0 (the layout of qm_t_fx.h).
+Every row is checked by emulating the device's integer and single-precision
+steps against mpmath at points of the row, and the worst relative error is
+printed.  Usage:  python -m paper_0901_0638_gb300.fit.gen_exp_fx_tables
+"""
+from __future__ import annotations
+
+import math
+import multiprocessing as mproc
+import os
+import sys
+from fractions import Fraction as Fr
+
+import mpmath as mp
+import numpy as np
+
+from . import targets as T
+from .gen_exp_tables import V_COARSE, V_FINE, V_MAX, V_SPLIT, X_EMIN, X_K, v_seg, x_seg
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+OUT = os.path.join(os.path.dirname(HERE), "csrc", "qm_exp_fx_tables.h")
+NV = V_FINE * V_SPLIT + V_COARSE * (V_MAX - V_SPLIT)
+NX = (-X_EMIN) << X_K
+LN2 = mp.log(2)
+
+
+def reexpand(c, h, sign=1):
+    """Coefficients in t of sum_k c_k s^k with s = h + sign t (exact, mpmath)."""
+    n = len(c)
+    return [sum(c[k] * mp.binomial(k, m) * h ** (k - m) for k in range(m, n)) * sign ** m for m in range(n)]
+
+
+def quantise(d, taumax, label):
+    """The fixed-point row fields for P(tau) = sum d_k tau^k, tau in [0, taumax]."""
+    d = list(d) + [mp.mpf(0)] * (9 - len(d))
+    assert d[0] > 0, label
+    for k in range(1, 9):
+        if d[k] < 0:
+            assert -d[k] <= mp.mpf(10) ** -18 * d[0], (label, k, float(d[k] / d[0]))
+            d[k] = mp.mpf(0)
+    assert sum(d[k] * mp.mpf(taumax) ** k for k in range(9)) < 2 * d[0], label
+    e2 = int(mp.floor(mp.log(d[0], 2))) + 1
+    s0 = e2 - 60
+    D = [int(mp.nint(d[k] / mp.mpf(2) ** s0)) for k in range(5)]
+    f = [float(np.float32(float(d[k + 5] / mp.mpf(2) ** s0))) for k in range(4)]
+    e0 = 1081 + s0
+    assert 2**59 <= D[0] <= 2**60 and D[4] < 2**52 and 0 < e0 < 2048, label
+    assert sum(f[k] * float(taumax) ** (k + 1) for k in range(4)) < 2.0**48, label
+    return D, f, s0, e0
+
+
+def f32(x):
+    return float(np.float32(x))
+
+
+def emulate(a0, D, f, s0, Sig, mlt):
+    """The device's chain for a row: fma(mlt, P, a0) with P from Sig = tau 2^64."""
+    assert 0 <= Sig < 2**63
+    tf = f32(float(Sig >> 41) * 2.0**-23)
+    F = f32(f[3])
+    for k in (2, 1, 0):
+        F = f32(F * tf + f[k])
+    th, tl = float(Sig >> 40), float((Sig >> 17) & 0x7FFFFF)
+    f24 = F * 2.0**-24
+    G = f32(f32(f24 * th) + f24 * 2.0**-23 * tl)
+    acc = D[4] + int(np.rint(G))
+    for k in (3, 2, 1, 0):
+        assert acc < 2**62
+        acc = D[k] + ((acc * Sig) >> 64)
+    assert 2**59 <= acc < 2**61
+    top = acc >> 60
+    pm = (acc + (64 << top)) >> (7 + top)
+    P = Fr(pm) * Fr(2) ** (7 + top + s0)
+    return float(Fr(mlt) * P + Fr(a0))
+
+
+def sig_of(t, k):
+    """floor(t 2^(64 + k)) from the double t >= 0, as the device forms it."""
+    if t == 0:
+        return 0
+    m, e = math.frexp(t)                  # t = m 2^e, m in [0.5, 1)
+    M = int(m * 2**53)                    # 53-bit significand
+    sh = e - 53 + 64 + k
+    return (M << sh) & (2**63 - 1) if sh >= 0 else (M >> -sh if sh > -64 else 0)
+
+
+def v_row(j):
+    mp.mp.dps = 50
+    _, b, _ = v_seg(j)
+    if j < V_FINE * V_SPLIT:
+        w, k = mp.mpf(1) / V_FINE, 3
+        vc = mp.mpf(0) if j == 0 else (mp.mpf(j) + mp.mpf("0.5")) / V_FINE
+        ve = mp.mpf(j + 1) / V_FINE
+    else:
+        q = j - V_FINE * V_SPLIT + V_COARSE * V_SPLIT
+        w, k = mp.mpf(1) / V_COARSE, 1
+        vc = (mp.mpf(q) + mp.mpf("0.5")) / V_COARSE
+        ve = mp.mpf(q + 1) / V_COARSE
+    if j == 0:
+        # z = v P(v), P(v) = sum b_{i+1} v^i about v = 0, re-expanded about
+        # v = 1/32 in t = 1/32 - v
+        p = reexpand(b[1:], ve, -1)
+        d = [p[i] / mp.mpf(2) ** (k * i) for i in range(len(p))]
+        a0 = 0.0
+        taumax = mp.mpf(3) / 8                           # t <= 3/64 (v >= -1/64)
+    else:
+        g = reexpand(b, ve - vc, -1)                      # |z|(v_e - t) = sum g_m t^m
+        a0 = float(g[0])
+        H = [-g[m + 1] for m in range(len(g) - 1)]
+        d = [H[i] / mp.mpf(2) ** (k * i) for i in range(len(H))]
+        taumax = mp.mpf(2) ** k * w
+    D, f, s0, e0 = quantise(d, taumax, ("V", j))
+    # check: the device arithmetic at points of the row against mpmath
+    worst = 0.0
+    vlo = mp.mpf(-1) / 64 if j == 0 else ve - w
+    for frac in (0.0, 0.13, 0.5, 0.87, 0.999):
+        v = float(vlo + (ve - vlo) * frac)
+        if j == 0 and v == 0.0:
+            continue
+        t = float(mp.mpf(float(ve)) - mp.mpf(v))        # exact in the device (or rounded for row 0)
+        Sig = sig_of(t, k)
+        mlt = v if j == 0 else -t
+        z = emulate(a0, D, f, s0, Sig, mlt)
+        vv = mp.mpf(v)
+        ref = T.q_exp(vv) if vv >= 0 else -T.q_exp(-mp.log(2 - mp.exp(-vv)))
+        worst = max(worst, float(abs(mp.mpf(z) / ref - 1)))
+    return j, a0, D, f, e0, worst
+
+
+def x_row(i):
+    mp.mp.dps = 50
+    E, j = -1 - i // (1 << X_K), i % (1 << X_K)
+    _, _, c, a, _ = x_seg((E, j))
+    mend = 1 + mp.mpf(j + 1) / 2**X_K
+    if mp.mpf(2) ** E * (1 + mp.mpf(j) / 2**X_K) >= LN2 - mp.mpf(1) / 64:
+        return i, 0.0, [2**59, 0, 0, 0, 0], [0.0] * 4, 1, 0.0       # not used by the kernel
+    # |z| = F(r), r = m c - 1 = (m_end c - 1) - c t_u
+    cm = mp.mpf(c)
+    g = reexpand(a, mend * cm - 1, -1)
+    g = [g[m] * cm ** m for m in range(len(g))]           # coefficients in t_u
+    a0 = float(g[0])
+    Hu = [g[m + 1] for m in range(len(g) - 1)]             # H(t_u) = sum Hu_i t_u^i
+    # t_u = tau / 16 + 2^-52 (tau = Tp 2^-48): H as a polynomial in tau
+    h0 = mp.mpf(2) ** -52
+    Ht = reexpand(Hu, h0, 1)                               # H(h0 + s), s = tau / 16
+    d = [Ht[m] / mp.mpf(16) ** m for m in range(len(Ht))]
+    D, f, s0, e0 = quantise(d, mp.mpf("0.5"), ("X", E, j))
+    worst = 0.0
+    for Tp in (0, 1, 2**23, 2**46, 2**47 - 1):
+        m = mend - mp.mpf(Tp + 1) * mp.mpf(2) ** -52
+        x = float(m * mp.mpf(2) ** E)
+        if x >= float(LN2 - mp.mpf(1) / 64) or x < 2.0**-26:
+            continue
+        tu = float(mp.mpf(Tp + 1) * mp.mpf(2) ** -52)
+        z = emulate(a0, D, f, s0, Tp << 16, tu)
+        ref = T.q_exp(-mp.log(2 * (-mp.expm1(-mp.mpf(x)))))
+        worst = max(worst, float(abs(mp.mpf(z) / ref - 1)))
+    return i, a0, D, f, e0, worst
+
+
+def row_literal(a0, D, f, e0):
+    d4e = D[4] | (e0 << 52)
+    return ("  {" + float(a0).hex() + "," + ",".join(f"{x}ull" for x in D[:4]) + f",{d4e}ull,{{" +
+            ",".join(float(np.float32(x)).hex() + "f" for x in f) + "}},\n")
+
+
+def main():
+    with mproc.Pool(max(1, os.cpu_count() or 2)) as pool:
+        vs = pool.map(v_row, range(NV), chunksize=4)
+        xs = pool.map(x_row, range(NX), chunksize=4)
+    wv = max(r[5] for r in vs)
+    wx = max(r[5] for r in xs)
+    print(f"exp -> normal fixed-point rows: V {NV} (worst {wv:.3g}), X {NX} (worst {wx:.3g})", file=sys.stderr)
+    L = [
+        "// Generated by paper_0901_0638_gb300/fit/gen_exp_fx_tables.py -- do not edit.\n",
+        "// Exponential -> normal recycling map z = Phi^{-1}(1 - e^{-x}) in the fixed-point\n",
+        "// row form of qm_t_fx.h: V rows (x >= ln 2 - 1/64, in v = x - ln 2) and X rows\n",
+        "// (2^-26 <= x < ln 2 - 1/64, binades of x, 32 segments each); see the generator.\n",
+        f"// Emulated worst relative error: V {wv:.3g}, X {wx:.3g}.\n",
+        "#pragma once\n#include \"qm_t_fx.h\"\n\nnamespace qm {\nnamespace efx {\n\n",
+        f"constexpr int V_FINE = {V_FINE};\nconstexpr int V_COARSE = {V_COARSE};\n",
+        f"constexpr int V_MAX = {V_MAX};\nconstexpr int NV = {NV};\n",
+        f"constexpr int X_K = {X_K};\nconstexpr int X_EMIN = {X_EMIN};\nconstexpr int NX = {NX};\n\n",
+        "__device__ const ttbl::SegTX ROWS_V[NV] = {\n",
+    ]
+    for _, a0, D, f, e0, _ in vs:
+        L.append(row_literal(a0, D, f, e0))
+    L.append("};\n\n__device__ const ttbl::SegTX ROWS_X[NX] = {\n")
+    for _, a0, D, f, e0, _ in xs:
+        L.append(row_literal(a0, D, f, e0))
+    L.append("};\n\n}  // namespace efx\n}  // namespace qm\n")
+    with open(OUT, "w") as fh:
+        fh.write("".join(L))
+    print("wrote", OUT, file=sys.stderr)
+
+
+if __name__ == "__main__":
+    main()

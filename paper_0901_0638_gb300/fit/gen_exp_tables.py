@@ -1,23 +1,21 @@
-"""Generate csrc/qm_exp_tables.h: the exponential -> normal recycling map
-z = Q_E(x) = Phi^{-1}(1 - e^{-x}) on given Exp(1) samples x (Sec. 2.3, Sec. 6).
+"""Local expansions of the exponential -> normal recycling map
+z = Q_E(x) = Phi^{-1}(1 - e^{-x}) on given Exp(1) samples x (Sec. 2.3, Sec. 6),
+used by gen_exp_fx_tables.py (which writes the device rows).
 
-Three regions, each a set of local expansions of the exponential-background
-recycling ODE solution Q(v) = Phi^{-1}(1 - e^{-v}/2), Q'' + Q' = Q Q'^2
+Each is a local expansion of the exponential-background recycling ODE
+solution Q(v) = Phi^{-1}(1 - e^{-v}/2), Q'' + Q' = Q Q'^2
 (rode.taylor_exp_background), composed with the coordinate change of the
 region:
 
-* x >= ln 2 (V table): z = Q(v), v = x - ln 2.  Segments of width 1/32 on
+* x >= ln 2 (v_seg): z = Q(v), v = x - ln 2.  Segments of width 1/32 on
   v in [0, 1) (segment 0 expanded at v = 0, where Q(0) = 0) and 1/8 on
   [1, 64); local variable s = v - v_c.
-* ln 2 - 1/64 < x < ln 2 (Y series): z = -H(y), y = ln 2 - x,
-  H(y) = Q(g(y)), g(y) = -log(2 - e^y) (so that 2(1 - e^{-x}) = e^{-g}),
-  one expansion at y = 0 (H(0) = 0).
-* 2^-26 <= x <= ln 2 - 1/64 (X table): z = -F(r), x = 2^E m, segment j =
-  top 5 bits of m, r = m c_j - 1, F(r) = Q(g_x(x)), g_x(x) = -log(2(1 - e^{-x}));
-  same entry layout and evaluation as the FP64 normal table.
+* 2^-26 <= x <= ln 2 - 1/64 (x_seg): z = -F(r), x = 2^E m, segment j =
+  top 5 bits of m, r = m c_j - 1, F(r) = Q(g_x(x)), g_x(x) = -log(2(1 - e^{-x})).
+* y_series: the expansion at x = ln 2 in y = ln 2 - x (no longer used on the
+  device: segment 0 of the V expansions covers v >= -1/64 instead).
 Below 2^-26, u = x - x^2/2 is 1 - e^{-x} to double precision and the normal
-table is used on it directly.  Usage:
-python -m paper_0901_0638_gb300.fit.gen_exp_tables
+table is used on it directly.
 """
 from __future__ import annotations
 
@@ -116,50 +114,3 @@ def x_seg(args):
         ref = T.q_exp(gx(x))
         worst = max(worst, abs(sum(a[n] * r**n for n in range(DEG_X + 1)) / ref - 1))
     return E, j, c, a[: DEG_X + 1], float(worst)
-
-
-def hexd(x):
-    return float(x).hex()
-
-
-def hexf(x):
-    return float(np.float32(float(x))).hex() + "f"
-
-
-def main():
-    nv = V_FINE * V_SPLIT + V_COARSE * (V_MAX - V_SPLIT)
-    xjobs = [(E, j) for E in range(-1, X_EMIN - 1, -1) for j in range(2**X_K)]
-    with mproc.Pool(max(1, os.cpu_count() or 2)) as pool:
-        vs = pool.map(v_seg, range(nv), chunksize=8)
-        xs = pool.map(x_seg, xjobs, chunksize=8)
-    ys, yw = y_series()
-    print(f"V table: {nv} segments, truncation <= {max(w for _, _, w in vs):.3g}", file=sys.stderr)
-    print(f"Y series: truncation <= {yw:.3g}", file=sys.stderr)
-    print(f"X table: {len(xs)} segments, truncation <= {max(x[4] for x in xs):.3g}", file=sys.stderr)
-    L = [
-        "// Generated by paper_0901_0638_gb300/fit/gen_exp_tables.py -- do not edit.\n",
-        "// Exponential -> normal recycling map z = Phi^{-1}(1 - e^{-x}): local\n",
-        "// expansions of the exponential-background recycling ODE (see the generator).\n",
-        "#pragma once\n#include \"qm_tables.h\"\n#include \"qm_t_tables.h\"\n\nnamespace qm {\nnamespace etbl {\n\n",
-        f"constexpr int V_FINE = {V_FINE};\nconstexpr int V_COARSE = {V_COARSE};\n",
-        f"constexpr int V_SPLIT = {V_SPLIT};\nconstexpr int V_MAX = {V_MAX};\nconstexpr int NV = {nv};\n",
-        f"constexpr int Y_MAX_INV = {Y_MAX_INV};\nconstexpr int DEG_Y = {DEG_Y};\n",
-        f"constexpr int X_K = {X_K};\nconstexpr int X_EMIN = {X_EMIN};\n\n",
-        f"__device__ const ttbl::SegT SEG_V[NV] = {{\n",
-    ]
-    for j, b, _ in vs:
-        L.append("  {{" + ",".join(hexd(x) for x in b[:5]) + "},{" + ",".join(hexf(x) for x in b[5:10]) +
-                 "},0.0f},\n")
-    L.append("};\n\n__device__ const double Y_SERIES[DEG_Y + 1] = {" + ",".join(hexd(x) for x in ys) + "};\n\n")
-    L.append(f"__device__ const tbl::SegF64 SEG_X[{len(xs)}] = {{\n")
-    for E, j, c, a, _ in xs:
-        L.append("  {{" + ",".join(hexd(x) for x in a[:4]) + "}," + hexd(c) + ",{" +
-                 ",".join(hexf(x) for x in a[4:8]) + "},{0.0f,0.0f}},\n")
-    L.append("};\n\n}  // namespace etbl\n}  // namespace qm\n")
-    with open(OUT, "w") as f:
-        f.write("".join(L))
-    print("wrote", OUT, file=sys.stderr)
-
-
-if __name__ == "__main__":
-    main()

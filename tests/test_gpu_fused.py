@@ -99,6 +99,16 @@ def test_recycle_exp_to_normal():
         10.0 ** -np.linspace(0, 300, 301), np.linspace(0.01, 40, 4001), np.linspace(40, 744, 300),
         math.log(2) + np.arange(-40, 41) * 2.0**-53,
         [0.0, np.inf, -1.0, np.nan, 0.28768207245178093, 1.3862943611198906, 0.35],
+        # segment and region boundaries of the evaluation: v = x - ln 2 at
+        # j/32 and q/8 (segment ends), v = -1/64 (the central piece), the
+        # binade and segment starts of x below ln 2, x = 2^-26, v = 64
+        np.array([math.log(2) + j / 32 + dd for j in range(1, 32) for dd in (-1e-16, 0.0, 1e-16)]),
+        np.array([math.log(2) + q / 8 + dd for q in range(8, 512, 7) for dd in (-1e-15, 0.0, 1e-15)]),
+        math.log(2) - 1 / 64 + np.array([-1e-17, 0.0, 2e-17, 1e-16]),
+        np.array([np.nextafter(2.0**E * (1 + j / 32), to) for E in range(-26, 0) for j in (0, 1, 15, 31)
+                  for to in (0.0, 1.0)]),
+        [2.0**-26, np.nextafter(2.0**-26, 0.0), np.nextafter(2.0**-26, 1.0), math.log(2) + 64.0,
+         np.nextafter(math.log(2) + 64.0, 0.0)],
     ])
     w = oracle.recycle_exp(x)
     t = torch.from_numpy(x).to(DEV)
