@@ -653,7 +653,9 @@ def main():
     # roofline of the dominant kernel, on the method's algorithmic work per
     # element: the slower of its bytes at the measured HBM copy bandwidth and
     # its arithmetic at the measured issue rates (FIXED: 16 B, one FP64 FMA,
-    # six FP32 FMAs; the branchy FP64 variants: about 45-60 FP64 operations).
+    # and the six multiply-adds of its degree-6 segment polynomial, which the
+    # kernel runs on the integer pipes, priced at the FP32 FMA rate; the
+    # branchy FP64 variants: about 45-60 FP64 operations).
     secs = ms * 1e-3
     peak, peak_src = hbm_peak()
     gbs = 16 * n / secs / 1e9

@@ -357,8 +357,8 @@ qm_status qm_tcopula_table_build(double nu, double* chi_seg, double* g_seg, int*
  * or out-of-range nu, null pointers, in/out partial overlap and overlapping
  * outputs of two segments are rejected (QM_ERR_INVALID / QM_ERR_UNSUPPORTED).
  * Tuning: block in {128, 256, 512}, ept in {1, 2, 4}, estrin in {0, 1}
- * (Estrin instead of Horner for the single-precision part of the Student-t
- * segment polynomial; the two round differently, so bit-exact comparisons
+ * (Estrin instead of Horner for the 32-bit inner part of the Student-t
+ * segment polynomial; the two truncate differently, so bit-exact comparisons
  * need the same choice).  With
  * tuning == NULL the tuning cache ($QM_TUNE_CACHE, default
  * ~/.cache/qm_tune.txt) is consulted, else (256, 2, 0).  The batch owns its

@@ -17,22 +17,22 @@
 // positive), so the polynomial is evaluated in the half offset
 // th = tau'/2 in [0, 1/2) on unsigned integers:
 //
-//     |z| = a0 + t_u H,   H = b0 + th (b1 + th (b2 + th F)) > 0,   b_k = beta_k 2^k,
-//     F   = b3 + th (b4 + th (b5 + th b6))   (single precision)
+//     |z| = a0 + t_u H,   H = b0 + th (b1 + th (b2 + th C)) > 0,   b_k = beta_k 2^k,
+//     C   = b3 + th (b4 + th (b5 + th b6))   (32-bit integers, scale per segment)
 //
 // The Horner steps for b0 and b1 run on unsigned 64-bit accumulators (below
-// 2^62) times th as a Q0.64 integer (below 2^63): the 128-bit product's high
-// half is exact from four 32 x 32 -> 64-bit multiply-adds, none of which
-// carries out.  b3..b6 are stored pre-scaled to the accumulator's units, and
-// the single-precision chain F enters the b2 step as B2 + rn(F th), F th
-// formed in single precision from an exact two-float split of th and turned
-// into an integer exactly (rounding to nearest even) as two 24-bit halves by
-// single-precision conversions.  The normalisation of x is integer
-// arithmetic, H becomes a double by bit assembly and t_u exactly (two
-// instruction mixes, below), and the final FMA is the one FP64 operation of
-// the method.  A segment is 48 bytes in two arrays (one 256-bit and one
-// 128-bit gather per element; the denser arrays also put more segments in a
-// cache line).
+// 2^62) times th as a Q0.64 integer (below 2^63): the high half of the
+// 128-bit product comes from three 32 x 32 -> 64-bit products (the low-limb
+// product, below one unit of the result, is left out, so a step can come out
+// one unit of 2^s0 low; the generator emulates exactly this).  b3..b6 form an
+// inner chain on 32-bit integers under a per-segment scale 2^c (three high
+// products by th as a Q0.32 integer), which enters the b2 step as
+// B2 + (C th) 2^(c-32) through one 32 x 32 -> 64-bit product and a shift of
+// 32 - c.  The normalisation of x is integer arithmetic, H becomes a double by
+// bit assembly and t_u exactly (two instruction mixes, below), and the final
+// FMA is the one FP64 operation of the method.  A segment is 48 bytes in two
+// arrays (one 256-bit and one 128-bit gather per element; the denser arrays
+// also put more segments in a cache line).
 #pragma once
 #include <stdint.h>
 
@@ -52,14 +52,15 @@ struct alignas(32) SegA {
     long long B0, B1, B2s;
 };
 
-// f_k = b_k 2^-s0, k = 3..6, rounded to single precision
-struct alignas(16) SegF {
-    float f3, f4, f5, f6;
+// C_k = b_k 2^-(s0 + c), k = 3..6, rounded to integers below 2^32 (C6 below
+// 2^27), and the join shift 32 - c (0 .. 31) in the top five bits of c6s
+struct alignas(16) SegC {
+    unsigned c3, c4, c5, c6s;
 };
 
 struct FxTable {
     SegA a[N_ALL];
-    SegF f[N_ALL];
+    SegC c[N_ALL];
 };
 
 }  // namespace fxt
@@ -73,21 +74,11 @@ __device__ __forceinline__ void ld256(const void* p, unsigned long long& a, unsi
 }
 
 // 16 bytes from the read-only path in one 128-bit load
-__device__ __forceinline__ float4 ld128f(const void* p)
+__device__ __forceinline__ uint4 ld128u(const void* p)
 {
-    float4 v;
-    asm("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+    uint4 v;
+    asm("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
     return v;
-}
-
-// rn(G) for 0 <= G < 2^48, rounding to nearest even, exactly: the high half
-// G div 2^24 by truncation, the low half G - 2^24 (G div 2^24) (exact in
-// single precision, below 2^24) by rounding; the conversions are 32-bit ones.
-__device__ __forceinline__ unsigned long long f32_to_u64_rn_split(float G)
-{
-    const unsigned gh = __float2uint_rz(G * 5.9604644775390625e-8f);            // G 2^-24, exact
-    const float gl = __fmaf_rn(__uint2float_rz(gh), -16777216.0f, G);           // exact
-    return (unsigned long long)gh * 16777216ull + __float2uint_rn(gl);
 }
 
 // Instruction mixes with bit-identical results, chosen per kernel by what
@@ -97,16 +88,38 @@ __device__ __forceinline__ unsigned long long f32_to_u64_rn_split(float G)
 // then the only FP64 instruction).
 enum { FX_TU_FADD = 2, FX_INT_LEAN = 2, FX_FP64_LEAN = 0 };
 
-// floor(a b / 2^64) for a < 2^62 and b < 2^63 from 32-bit limbs:
-// a1 b1 + hi32(a0 b1 + a1 b0 + hi32(a0 b0)); the partial sums stay below 2^64,
-// so this is the exact high half of the product.
+// floor(a b / 2^64), or one less, for a < 2^62 and b < 2^63, from three of
+// the four 32 x 32 -> 64-bit limb products: a1 b1 + hi32(a0 b1 + a1 b0).  The
+// middle sum stays below 2^64 (a1 b0 < 2^62, a0 b1 < 2^63); leaving out
+// hi32(a0 b0) < 2^32 lowers it by less than 2^32, so the result by at most 1.
 __device__ __forceinline__ unsigned long long mulhi_q(unsigned long long a, unsigned long long b)
 {
     const unsigned a0 = (unsigned)a, a1 = (unsigned)(a >> 32);
     const unsigned b0 = (unsigned)b, b1 = (unsigned)(b >> 32);
-    const unsigned long long m1 = (unsigned long long)a1 * b0 + __umulhi(a0, b0);
-    const unsigned long long m2 = (unsigned long long)a0 * b1 + m1;
-    return (unsigned long long)a1 * b1 + (m2 >> 32);
+    const unsigned long long m = (unsigned long long)a0 * b1 + (unsigned long long)a1 * b0;
+    return (unsigned long long)a1 * b1 + (m >> 32);
+}
+
+// The inner chain: C = C3 + th (C4 + th (C5 + th C6)) on 32-bit integers,
+// th32 = floor(th 2^32) < 2^31 (each step's high product truncates), then
+// floor(C th32 / 2^sh), sh = 32 - c, in the units 2^s0 of the outer chain.
+// With ESTRIN the same polynomial as (C3 + th C4) + th^2 (C5 + th C6), th^2
+// as hi32(th32 th32): two independent high products, then one (a shorter
+// dependent chain; it truncates differently, within the same bounds).
+template <bool ESTRIN = false>
+__device__ __forceinline__ unsigned long long fx_inner(uint4 c, unsigned th32)
+{
+    unsigned a;
+    if (ESTRIN) {
+        const unsigned lo = __umulhi(c.y, th32) + c.x;
+        const unsigned hi = __umulhi(c.w & 0x07FFFFFFu, th32) + c.z;
+        a = __umulhi(hi, __umulhi(th32, th32)) + lo;
+    } else {
+        a = __umulhi(c.w & 0x07FFFFFFu, th32) + c.z;
+        a = __umulhi(a, th32) + c.y;
+        a = __umulhi(a, th32) + c.x;
+    }
+    return ((unsigned long long)a * th32) >> (c.w >> 27);
 }
 
 // |Phi^{-1}| bits for x = 2d = S 2^(base - 52), 0 < S < 2^53 (any position of
@@ -133,24 +146,12 @@ __device__ __forceinline__ unsigned long long probit_mag_fx_sx(const fxt::FxTabl
 
     unsigned long long a0b, B0, B1, B2s;
     ld256(&T->a[idx], a0b, B0, B1, B2s);                           // a0, B0, B1, B2 | e0
-    const float4 f = ld128f(&T->f[idx]);                            // f3..f6
+    const uint4 c = ld128u(&T->c[idx]);                             // C3..C6 | sh
     const unsigned long long B2 = B2s & ((1ull << 52) - 1ull);
     const unsigned e0 = (unsigned)(B2s >> 52);                      // 1083 + s0
 
-    // single-precision tail from the top bits of the offset
-    const float tf = __uint_as_float(0x4B000000u | (unsigned)(Tp >> 25)) - 8388608.0f;
-    const float tau_f = tf * __uint_as_float((unsigned)(127 + K - 28) << 23);
-    float F = __fmaf_rn(f.w, tau_f, f.z);
-    F = __fmaf_rn(F, tau_f, f.y);
-    F = __fmaf_rn(F, tau_f, f.x);
-    // innermost step in single precision: th = Tp 2^-47 = hi 2^-24 + lo 2^-47
-    // exactly (both halves are integers below 2^23),
-    // F th = fl(fl(F 2^-24 hi) + F 2^-47 lo); acc = B2 + rn(F th)
-    const float th = __uint_as_float(0x4B000000u | (unsigned)(Tp >> 23)) - 8388608.0f;
-    const float tl = __uint_as_float(0x4B000000u | ((unsigned)Tp & 0x7FFFFFu)) - 8388608.0f;
-    const float f24 = F * 5.9604644775390625e-8f;                  // 2^-24, exact
-    const float G = __fmaf_rn(f24 * 1.1920928955078125e-07f, tl, __fmul_rn(f24, th));
-    unsigned long long acc = B2 + f32_to_u64_rn_split(G);
+    // th = Tp 2^-47: th32 = Tp >> 15 for the inner chain, Tau = th 2^64
+    unsigned long long acc = B2 + fx_inner(c, (unsigned)(Tp >> 15));
     acc = B1 + mulhi_q(acc, Tau);
     acc = B0 + mulhi_q(acc, Tau);                                   // H 2^-s0 (0 on the zero rows)
 

@@ -16,10 +16,15 @@
 // integers D_k = d_k 2^-s0 (s0 puts D_0 in [2^59, 2^60], which keeps D_4
 // below 2^52 beside the exponent field; P varies by less than a factor 2
 // across a segment, so the accumulator stays in [2^59, 2^61)), a
-// Horner chain acc = D_k + floor(acc tau), and d_5..d_8 as single-precision
-// f_k = d_k 2^-s0 whose chain enters the d_4 step (the d_5 term is at most
-// ~4e-6 of |t|, for nu = 0.75 at |z| = 8.75, so single precision costs it
-// ~2e-13).  P becomes a double by one rounding shift and the exponent field
+// Horner chain acc = D_k + mulhi(acc, tau 2^64) (the high half of the 128-bit
+// product from three 32-bit limb products: exact or one unit low), and
+// d_5..d_8 as an inner chain on 32-bit integers C_k = d_k 2^-(s0 + c) under
+// a per-segment scale 2^c, in tau32 = floor(tau 2^32): a = C_5 + hi32(tau32
+// (C_6 + ...)), every partial value below 2^32, which enters the d_4 step as
+// D_4 + floor(a tau32 / 2^(32 - c)); the shift 32 - c (0 .. 31) sits in the
+// top five bits of the C_8 word (C_8 below 2^27).  The d_5 term is at most
+// ~4e-6 of |t| (nu = 0.75 at |z| = 8.75), so the 32-bit chain costs it under
+// 1e-15.  P becomes a double by one rounding shift and the exponent field
 // e0 = 1081 + s0, and |t| = fma(sigma, P, a0) is the one FP64 operation
 // besides the exact sigma = |z| - z_j.
 #pragma once
@@ -35,7 +40,7 @@ struct alignas(64) SegTX {
     unsigned long long D0, D1, D2;  // d_0..d_2 2^-s0
     unsigned long long D3;          // d_3 2^-s0
     unsigned long long D4e;         // d_4 2^-s0 (below 2^52) | e0 << 52
-    float f[4];                     // d_5..d_8 2^-s0
+    unsigned c[4];                  // C_5, C_6, C_7, C_8 | (32 - c) << 27
 };
 static_assert(sizeof(SegTX) == 64, "one 64-byte row per segment");
 

@@ -27,6 +27,7 @@
 // with the central series (Q(0) = 0, Q'(0) = gamma) is checked.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -289,13 +290,35 @@ qm_status t_pack_fx(const double* seg10, int nseg, ttbl::SegTX* out)
         unsigned long long D[5];
         for (int k = 0; k < 5; ++k) D[k] = (unsigned long long)llround(ldexp(d[k], -s0));
         const int e0 = 1081 + s0;
-        float f[4];
-        double gmax = 0.0;                                      // F tau at tau = 1/2
-        for (int k = 0; k < 4; ++k) {
-            f[k] = (float)ldexp(d[k + 5], -s0);
-            gmax += ldexp((double)f[k], -k - 1);
+        // inner chain: C_k = d_{k+5} 2^-(s0 + c) on 32-bit integers, c the
+        // smallest scale (at least 1) that keeps every Horner partial value
+        // C_k + C_{k+1}/2 + ... (tau < 1/2) below 2^32
+        double fk[4];
+        for (int k = 0; k < 4; ++k) fk[k] = ldexp(d[k + 5], -s0);
+        auto partial_max = [](const double* v) {
+            double m = 0.0;
+            for (int k = 0; k < 4; ++k) {
+                double acc = 0.0;
+                for (int i = 3; i >= k; --i) acc = acc * 0.5 + v[i];
+                m = std::max(m, acc);
+            }
+            return m;
+        };
+        int cs = 1;                                                   // the scale c
+        {
+            const double pm = partial_max(fk);
+            if (pm > 0.0) cs = std::max(1, (int)std::ceil(std::log2(pm)) - 32);
         }
-        if (D[4] >= (1ull << 52) || e0 <= 0 || e0 >= 2048 || !(gmax < 281474976710656.0))
+        unsigned long long C[4];
+        for (;; ++cs) {
+            double cd[4];
+            for (int k = 0; k < 4; ++k) {
+                C[k] = (unsigned long long)llround(ldexp(fk[k], -cs));
+                cd[k] = (double)C[k];
+            }
+            if (partial_max(cd) < 4294967288.0 || cs > 32) break;
+        }
+        if (D[4] >= (1ull << 52) || e0 <= 0 || e0 >= 2048 || cs > 32 || C[3] >= (1ull << 27))
             return fail(QM_ERR_UNSUPPORTED, "Student t: segment %d outside the fixed-point range", j);
         ttbl::SegTX& r = out[j];
         r.a0 = (double)cp[0];
@@ -304,15 +327,16 @@ qm_status t_pack_fx(const double* seg10, int nseg, ttbl::SegTX* out)
         r.D2 = D[2];
         r.D3 = D[3];
         r.D4e = D[4] | ((unsigned long long)e0 << 52);
-        for (int k = 0; k < 4; ++k) r.f[k] = f[k];
+        for (int k = 0; k < 3; ++k) r.c[k] = (unsigned)C[k];
+        r.c[3] = (unsigned)C[3] | ((unsigned)(32 - cs) << 27);
         // the stored row against the original expansion at the segment's
-        // start, middle and end (quantisation of a0, D_k and f_k)
+        // start, middle and end (quantisation of a0, D_k and C_k)
         for (int q = 0; q <= 2; ++q) {
             const double sig = (q == 0 ? 0.0 : q == 1 ? 1.0 / 64 : 1.0 / 32 - 1.0 / 4096);
             const double tau = 16.0 * sig, s = sig + dl;
             double P = 0.0, ref = 0.0;
             for (int k = 8; k >= 0; --k)
-                P = P * tau + (k < 5 ? ldexp((double)D[k], s0) : ldexp((double)f[k - 5], s0));
+                P = P * tau + (k < 5 ? ldexp((double)D[k], s0) : ldexp((double)C[k - 5], s0 + cs));
             for (int k = 9; k >= 0; --k) ref = ref * s + (double)c[k];
             const double got = (double)r.a0 + sig * P;
             if (ref != 0.0 && fabs(got / ref - 1.0) > 1e-13)

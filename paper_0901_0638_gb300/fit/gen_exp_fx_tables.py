@@ -19,10 +19,10 @@ one unsigned fixed-point chain for every lane:
   segment end (Tu = Tp + 1 integer, t_u = Tu 2^-52):
       |z| = a0 + t_u H,   tau = Tp 2^-48 in [0, 1/2),   z = -|z|.
 H (or P) = sum_k d_k tau^k: d_0..d_4 as integers D_k = d_k 2^-s0 (D_0 in
-[2^59, 2^60]), d_5..d_8 as floats, e0 = 1081 + s0 (the layout of qm_t_fx.h).
-Every row is checked by emulating the device's integer and single-precision
-steps against mpmath at points of the row, and the worst relative error is
-printed.  Usage:  python -m paper_0901_0638_gb300.fit.gen_exp_fx_tables
+[2^59, 2^60]), d_5..d_8 as 32-bit integers under a per-row scale (the inner
+chain), e0 = 1081 + s0 (the layout of qm_t_fx.h).  Every row is checked by
+emulating the device's integer steps exactly against mpmath at points of the
+row, and the worst relative error is printed.  Usage:  python -m paper_0901_0638_gb300.fit.gen_exp_fx_tables
 """
 from __future__ import annotations
 
@@ -33,7 +33,6 @@ import sys
 from fractions import Fraction as Fr
 
 import mpmath as mp
-import numpy as np
 
 from . import targets as T
 from .gen_exp_tables import V_COARSE, V_FINE, V_MAX, V_SPLIT, X_EMIN, X_K, v_seg, x_seg
@@ -63,31 +62,50 @@ def quantise(d, taumax, label):
     e2 = int(mp.floor(mp.log(d[0], 2))) + 1
     s0 = e2 - 60
     D = [int(mp.nint(d[k] / mp.mpf(2) ** s0)) for k in range(5)]
-    f = [float(np.float32(float(d[k + 5] / mp.mpf(2) ** s0))) for k in range(4)]
+    # inner chain: C_k = d_{k+5} 2^-(s0 + c) on 32-bit integers, every Horner
+    # partial value (tau <= taumax) below 2^32; the shift 32 - c in the top
+    # five bits of the last word
+    fk = [d[k + 5] / mp.mpf(2) ** s0 for k in range(4)]
+
+    def partial_max(v):
+        return max(sum(v[i] * mp.mpf(taumax) ** (i - k) for i in range(k, 4)) for k in range(4))
+
+    pm = partial_max(fk)
+    c = max(1, int(mp.ceil(mp.log(pm, 2))) - 32) if pm > 0 else 1
+    while True:
+        C = [int(mp.nint(x / mp.mpf(2) ** c)) for x in fk]
+        if partial_max([mp.mpf(x) for x in C]) < 2**32 - 8:
+            break
+        c += 1
     e0 = 1081 + s0
     assert 2**59 <= D[0] <= 2**60 and D[4] < 2**52 and 0 < e0 < 2048, label
-    assert sum(f[k] * float(taumax) ** (k + 1) for k in range(4)) < 2.0**48, label
-    return D, f, s0, e0
+    assert 1 <= c <= 32 and C[3] < 2**27, (label, c, C)
+    return D, C[:3] + [C[3] | ((32 - c) << 27)], s0, e0
 
 
-def f32(x):
-    return float(np.float32(x))
+def mulhi3(a, b):
+    """floor(a b / 2^64) from three 32-bit limb products, as the device forms
+    it (a < 2^62, b < 2^63): the exact high half or one less."""
+    a0, a1, b0, b1 = a & 0xFFFFFFFF, a >> 32, b & 0xFFFFFFFF, b >> 32
+    m = a0 * b1 + a1 * b0
+    assert m < 2**64
+    r = a1 * b1 + (m >> 32)
+    assert 0 <= ((a * b) >> 64) - r <= 1
+    return r
 
 
-def emulate(a0, D, f, s0, Sig, mlt):
+def emulate(a0, D, w, s0, Sig, mlt):
     """The device's chain for a row: fma(mlt, P, a0) with P from Sig = tau 2^64."""
     assert 0 <= Sig < 2**63
-    tf = f32(float(Sig >> 41) * 2.0**-23)
-    F = f32(f[3])
-    for k in (2, 1, 0):
-        F = f32(F * tf + f[k])
-    th, tl = float(Sig >> 40), float((Sig >> 17) & 0x7FFFFF)
-    f24 = F * 2.0**-24
-    G = f32(f32(f24 * th) + f24 * 2.0**-23 * tl)
-    acc = D[4] + int(np.rint(G))
+    t32 = Sig >> 32
+    a = w[3] & 0x07FFFFFF
+    for ck in (w[2], w[1], w[0]):
+        a = ck + ((a * t32) >> 32)
+        assert a < 2**32
+    acc = D[4] + ((a * t32) >> (w[3] >> 27))
     for k in (3, 2, 1, 0):
         assert acc < 2**62
-        acc = D[k] + ((acc * Sig) >> 64)
+        acc = D[k] + mulhi3(acc, Sig)
     assert 2**59 <= acc < 2**61
     top = acc >> 60
     pm = (acc + (64 << top)) >> (7 + top)
@@ -154,7 +172,7 @@ def x_row(i):
     _, _, c, a, _ = x_seg((E, j))
     mend = 1 + mp.mpf(j + 1) / 2**X_K
     if mp.mpf(2) ** E * (1 + mp.mpf(j) / 2**X_K) >= LN2 - mp.mpf(1) / 64:
-        return i, 0.0, [2**59, 0, 0, 0, 0], [0.0] * 4, 1, 0.0       # not used by the kernel
+        return i, 0.0, [2**59, 0, 0, 0, 0], [0, 0, 0, 0], 1, 0.0       # not used by the kernel
     # |z| = F(r), r = m c - 1 = (m_end c - 1) - c t_u
     cm = mp.mpf(c)
     g = reexpand(a, mend * cm - 1, -1)
@@ -182,7 +200,7 @@ def x_row(i):
 def row_literal(a0, D, f, e0):
     d4e = D[4] | (e0 << 52)
     return ("  {" + float(a0).hex() + "," + ",".join(f"{x}ull" for x in D[:4]) + f",{d4e}ull,{{" +
-            ",".join(float(np.float32(x)).hex() + "f" for x in f) + "}},\n")
+            ",".join(f"{x:#x}u" for x in f) + "}},\n")
 
 
 def main():

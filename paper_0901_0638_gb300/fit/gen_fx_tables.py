@@ -31,19 +31,22 @@ tail quantile |Phi^{-1}| as a function of the offset back from the segment
 end has all its derivatives positive, so every Horner accumulator is
 non-negative and the chain runs on unsigned integers.
 
-On GB300 the FP64 pipe issues about 1/62 of the FP32 rate, so beta_0..beta_2
-are applied by a fixed-point Horner chain on 64-bit unsigned integers in the
-half offset th = tau'/2 in [0, 1/2), an unsigned Q0.64 number below 2^63, on
-the coefficients beta'_k = beta_k 2^k (the same polynomial in th):
-acc_k = B_k + floor(acc_{k+1} th 2^64 / 2^64), every acc in units of 2^s0 and
-below 2^62.  With both factors that small, the 128-bit product's high half
-is exact from four 32 x 32 -> 64-bit multiply-adds with no carry out.
-beta'_3..beta'_6 go through a single-precision chain F on f_k = beta'_k 2^-s0
-(already in the accumulator's units), which enters as acc_2 = B_2 + rn(F th):
-F th is formed in single precision from the exact split
-th = hi 2^-24 + lo 2^-47 of the integer offset (one multiply and one FMA),
-and converted to an integer rounding to nearest even, exactly, as two 32-bit
-halves (G = g_h 2^24 + g_l).  s0 puts H(0) 2^-s0 in [2^61, 2^62), and H
+On GB300 the FP64 pipe issues about 1/62 of the FP32 rate, so the
+polynomial runs on the integer pipes, in the half offset th = tau'/2 in
+[0, 1/2) on the coefficients beta'_k = beta_k 2^k (the same polynomial in
+th).  beta'_0..beta'_2 are applied by a Horner chain on 64-bit unsigned
+integers, th an unsigned Q0.64 number below 2^63:
+acc_k = B_k + mulhi(acc_{k+1}, th 2^64), every acc in units of 2^s0 and
+below 2^62.  mulhi is the high half of the 128-bit product formed from three
+32 x 32 -> 64-bit limb products, a1 b1 + hi32(a0 b1 + a1 b0) (the middle sum
+stays below 2^64): the exact high half or one less, emulated here exactly.
+beta'_3..beta'_6 form an inner chain on 32-bit integers
+C_k = beta'_k 2^-(s0 + c) under a per-segment scale 2^c, with th as a Q0.32
+number th32 = floor(th 2^32) < 2^31: a = C3 + hi32(th32 (C4 + hi32(th32
+(C5 + hi32(th32 C6))))), kept below 2^32 by the choice of c (asserted), and it
+enters as acc_2 = B_2 + floor(a th32 / 2^(32 - c)).  The join shift 32 - c
+(0 .. 31) sits in the top five bits of the C6 word (C6 < 2^27, asserted).
+s0 puts H(0) 2^-s0 in [2^61, 2^62), and H
 varies by less than a factor 2 across a segment (asserted; at most 1.6 %), so
 acc_0 lies in [2^61, 2^63): its leading bit is bit 61 or 62, and H becomes a
 double by one rounding shift and one add of the exponent field
@@ -60,12 +63,11 @@ with a zero exponent field assembles to +0), so z = +0 needs no branch.
 Entry: two arrays, so that a lane gathers 48 bytes with one 256-bit and one
 128-bit load: A[i] = {a0 (double), B0, B1 (uint64), B2 | e0 << 52} (32 bytes;
 B2 in the low 52 bits, e0 in the top 12) and
-F[i] = {f3, f4, f5, f6} (float, 16 bytes).
+C[i] = {C3, C4, C5, C6 | (32 - c) << 27} (uint32, 16 bytes).
 
 The generator checks every segment by emulating the kernel's integer and
-double-precision steps exactly (single-precision steps to within one
-rounding) at both ends and interior points of the segment, against the
-mpmath quantile, and prints the worst relative error.
+double-precision steps exactly at both ends and interior points of the
+segment, against the mpmath quantile, and prints the worst relative error.
 Usage:  python -m paper_0901_0638_gb300.fit.gen_fx_tables
 """
 from __future__ import annotations
@@ -137,10 +139,6 @@ def taylor(e, j, K):
     return g
 
 
-def f32(x):
-    return float(np.float32(float(x)))
-
-
 def shift_poly(beta, delta):
     """Coefficients in tau' of H(tau' + delta) (exact re-expansion)."""
     n = len(beta)
@@ -157,23 +155,45 @@ def quantise(e, j, K, g):
     B = [int(mp.nint(bh[k] / mp.mpf(2) ** s0)) for k in range(NI)]
     e0 = 1083 + s0                                                # exponent field base (below)
     assert 0 < B[2] < 2**51 and 0 < e0 < 2**11, (e, j, B[2], s0)  # B2 | e0 << 52
-    bf = [f32(bh[k] / mp.mpf(2) ** s0) for k in range(NI, DEG)]
-    for x in bf:                                                   # normal floats
-        assert 2.0**-126 <= x < 2.0**62, (e, j, x)
-    return {"a0": float(g[0]), "B": B, "bf": bf, "s0": s0, "e0": e0}
+    # inner chain: C_k = b'_k 2^-(s0 + c) on 32-bit integers; for th < 1/2
+    # the Horner value after the C_k step stays below C_k + C_{k+1}/2 + ...,
+    # and c keeps every one of these partial sums below 2^32
+    fk = [bh[k] / mp.mpf(2) ** s0 for k in range(NI, DEG)]
+
+    def partial_max(v):
+        return max(sum(v[i] * mp.mpf(2) ** (k - i) for i in range(k, len(v))) for k in range(len(v)))
+
+    c = max(1, int(mp.ceil(mp.log(partial_max(fk), 2))) - 32)
+    while True:
+        C = [int(mp.nint(x / mp.mpf(2) ** c)) for x in fk]
+        if partial_max([mp.mpf(x) for x in C]) < 2**32 - 8:
+            break
+        c += 1
+    assert 1 <= c <= 32 and C[-1] < 2**27, (e, j, c, C)         # join shift 32 - c in 0 .. 31
+    return {"a0": float(g[0]), "B": B, "C": C, "sh": 32 - c, "s0": s0, "e0": e0}
 
 
 def mulhi_limbs(a, b):
-    """floor(a b / 2^64) as the kernel forms it from 32-bit limbs (a < 2^62,
-    b < 2^63): a1 b1 + hi32(a0 b1 + a1 b0 + hi32(a0 b0)), with no partial sum
-    reaching 2^64.  Equal to the exact high half."""
+    """floor(a b / 2^64) as the kernel forms it from three 32-bit limb
+    products (a < 2^62, b < 2^63): a1 b1 + hi32(a0 b1 + a1 b0), the middle sum
+    below 2^64.  The exact high half or one less."""
     a0, a1, b0, b1 = a & 0xFFFFFFFF, a >> 32, b & 0xFFFFFFFF, b >> 32
-    m1 = a1 * b0 + ((a0 * b0) >> 32)
-    m2 = a0 * b1 + m1
-    assert m2 < 2**64
-    r = a1 * b1 + (m2 >> 32)
-    assert r == (a * b) >> 64
+    m = a0 * b1 + a1 * b0
+    assert m < 2**64
+    r = a1 * b1 + (m >> 32)
+    assert 0 <= ((a * b) >> 64) - r <= 1
     return r
+
+
+def inner(q, th32):
+    """The kernel's 32-bit inner chain C3 + th (C4 + th (C5 + th C6)) and its
+    join floor(C th32 / 2^sh) into the units of the outer chain."""
+    C = q["C"]
+    a = C[-1]
+    for ck in reversed(C[:-1]):
+        a = ck + ((a * th32) >> 32)
+        assert a < 2**32
+    return (a * th32) >> q["sh"]
 
 
 def emulate(q, K, Tu):
@@ -181,21 +201,8 @@ def emulate(q, K, Tu):
     Tp = Tu - 1                                                   # the kernel's ~m & (2^(52-K) - 1)
     Tau = Tp << (11 + K)                                          # th 2^64 = tau' 2^63
     assert 0 <= Tau < 2**63
-    tf = f32(float(Tp >> 25)) * 2.0 ** (K - 28)
-    F = np.float32(q["bf"][-1])
-    for cf in reversed(q["bf"][:-1]):
-        F = np.float32(float(F) * tf + cf)
-    # innermost step in single precision: th = Tp 2^-47 = hi 2^-24 + lo 2^-47
-    # exactly; G = fl(fl(F 2^-24 hi) + F 2^-47 lo) (a multiply, then one FMA)
-    th, tl = float(Tp >> 23), float(Tp & 0x7FFFFF)
-    f24 = float(F) * 2.0 ** -24
-    p = np.float32(f24 * th)
-    G = np.float32(float(Fraction(f24 * 2.0 ** -23) * Fraction(tl) + Fraction(float(p))))
-    assert 0 <= float(G) < 2.0**48                                # two 24-bit halves
-    gh = int(float(G) * 2.0 ** -24)                               # truncated high half
-    gl = float(G) - gh * 2.0**24                                  # exact
-    acc = q["B"][NI - 1] + gh * 2**24 + int(np.rint(gl))          # = B2 + rint(G)
-    assert acc == q["B"][NI - 1] + int(np.rint(float(G))) and acc < 2**62
+    acc = q["B"][NI - 1] + inner(q, Tp >> 15)                     # th32 = th 2^32 = Tp 2^-15
+    assert acc < 2**62
     acc = q["B"][1] + mulhi_limbs(acc, Tau)
     assert acc < 2**62
     acc = q["B"][0] + mulhi_limbs(acc, Tau)
@@ -242,10 +249,6 @@ def hexd(x):
     return float(x).hex()
 
 
-def hexf(x):
-    return float(np.float32(x)).hex() + "f"
-
-
 def main():
     jobs = [(e, j) for e in range(0, E_LAST + 1) for j in range(2**seg_k(e))]
     with mproc.Pool(max(1, os.cpu_count() or 1)) as pool:
@@ -265,7 +268,8 @@ def main():
         "// in the half offset th = tau'/2: beta'_k = beta_k 2^k, all positive;\n",
         "// beta'_0..2 as integers B_k = beta'_k 2^-s0 (A: a0, B0, B1, B2 | e0 << 52,\n",
         "// e0 = 1083 + s0, H(0) 2^-s0 in [2^61, 2^62)),\n",
-        "// beta'_3..6 as float f_k = beta'_k 2^-s0 (F).\n",
+        "// beta'_3..6 as 32-bit integers C_k = beta'_k 2^-(s0 + c) (C: C3, C4, C5,\n",
+        "// C6 | (32 - c) << 27).\n",
         f"// Binade e = -1 - E = 0..{E_LAST}, {2**K_MAIN} segments each; index (e + 1) 2^{K_MAIN} + j;\n",
         f"// rows 0..{2**K_MAIN - 1} (e = -1, x = 1 exactly: u = 1/2) are zero, so that z = +0 there.\n",
         f"// Emulated worst relative error over the checked points: {worst:.3g}.\n",
@@ -282,9 +286,11 @@ def main():
         lits = [f"{b}ll" for b in B[:2]] + [f"{b2s}ll" if b2s != -2**63 else "(-0x7fffffffffffffffll - 1)"]
         lines.append("  {" + hexd(q["a0"]) + "," + ",".join(lits) + "},\n")
     lines.append(" },\n {\n")
-    lines += ["  {0x0p+0f,0x0p+0f,0x0p+0f,0x0p+0f},\n"] * 2**K_MAIN
+    lines += ["  {0u,0u,0u,0u},\n"] * 2**K_MAIN
     for e, j, q, _ in res:
-        lines.append("  {" + ",".join(hexf(x) for x in q["bf"]) + "},\n")
+        C = q["C"]
+        w = C[:3] + [C[3] | (q["sh"] << 27)]
+        lines.append("  {" + ",".join(f"{x:#x}u" for x in w) + "},\n")
     lines.append(" }\n};\n\n}  // namespace fxt\n}  // namespace qm\n")
     with open(OUT, "w") as f:
         f.write("".join(lines))

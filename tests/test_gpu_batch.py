@@ -131,9 +131,8 @@ def test_batch_uniform_segments_match_the_streaming_kernel_bit_for_bit():
     table as the streaming FP64 kernel, with the offset t_u turned into a
     double by integer normalisation instead of the exact FP64 add; both are
     exact, so the results must be identical.  The inputs crowd the top
-    segment next to u = 1/2, where the single-precision tail passes through
-    0 and its conversion to an integer rounds, plus the tail-stress
-    mixture."""
+    segment next to u = 1/2, where the offset and the inner 32-bit chain
+    pass through 0, plus the tail-stress mixture."""
     rng = np.random.default_rng(41)
     k = np.concatenate([2**52 + rng.integers(-2**46, 2**46, 1 << 18), 2**52 + np.arange(-4096, 4096)])
     near = k.astype(np.float64) * 2.0**-53
