@@ -537,8 +537,9 @@ def side_workload(args):
         line.update(value=n / (ms * 1e-3) / 1e9, ms_per_step=ms, dtype="f64",
                     config={"workload": f"exponential -> hyperbolic recycling (alpha, beta, delta) = "
                                         f"({a}, {b}, {d}), n=2^{args.n_log2} two-sided exponential samples"},
-                    roofline={"bound": "alu", "note": "FP64 Horner (5 FMA + 1 add per element) on "
-                                                      "segment tables; 16 B/element",
+                    roofline={"bound": "alu", "note": "biased fixed-point segment rows (integer "
+                                                      "chain, one exact FP64 add and one DFMA per "
+                                                      "element); 16 B/element",
                               "hbm_frac": 16 * n / (ms * 1e-3) / 1e9 / peak})
         h.close()
     elif args.workload in ("copula", "tcopula"):

@@ -26,10 +26,16 @@
 // quadrature, and Q' = f_0(v)/f(Q)), the inner ones (|v| < ~0.5/rate) from a
 // pass forwards from Q(0) = 0, Q'(0+), which keeps Q's relative accuracy as
 // v -> 0; the two passes must agree where they meet.
+//
+// On the device each segment is a biased fixed-point row (pack_fx_biased,
+// qm_t_fx.h: the coefficients have no common sign, so the Horner accumulators
+// carry a bias that each step removes) evaluated by segts_eval with one DFMA;
+// the FP64 rows serve |v| < 2^E_MIN, |v| past the table, 0, inf and NaN.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <string>
 #include <vector>
 
 #include "qm.h"
@@ -255,12 +261,14 @@ qm_status hyp_table_build(double alpha, double beta, double delta, double* seg_r
 namespace {
 
 struct HypSide {
-    const ttbl::SegT* seg;     // 1 + 32 nb entries
+    const ttbl::SegT* seg;     // 1 + 32 nb FP64 rows (the series about 0, then the segments)
+    const ttbl::SegTX* fx;     // 32 nb fixed-point rows (binades E_MIN .. e_max)
     int e_max;
 };
 
-// |Q| on one side for a = |v|
-__device__ __forceinline__ double hyp_side_eval(const HypSide& S, double a)
+// |Q| on one side from the FP64 rows: |v| < 2^E_MIN (the series about 0),
+// |v| beyond the last binade (its last segment continued), 0, inf and NaN
+static __device__ __noinline__ double hyp_side_rare(const ttbl::SegT* seg, int e_max, double a)
 {
     const uint64_t ab = (uint64_t)__double_as_longlong(a);
     const int E = (int)(ab >> 52) - 1023;
@@ -270,13 +278,26 @@ __device__ __forceinline__ double hyp_side_eval(const HypSide& S, double a)
         idx = 0;
         s = a;
     } else {
-        const int Ec = min(E, S.e_max);
-        const uint32_t j = (E > S.e_max) ? 31u : (uint32_t)(ab >> 47) & 31u;
+        const int Ec = min(E, e_max);
+        const uint32_t j = (E > e_max) ? 31u : (uint32_t)(ab >> 47) & 31u;
         const uint64_t cb = ((uint64_t)(Ec + 1023) << 52) | ((uint64_t)j << 47) | (1ull << 46);
         s = __dadd_rn(a, -__longlong_as_double((long long)cb));     // exact within the binade
         idx = 1 + 32 * (Ec - E_MIN) + (int)j;
     }
-    return seg_poly(S.seg[idx], s);
+    return seg_poly(seg[idx], s);
+}
+
+// |Q| on one side for a = |v|: segment j of binade E from the bits, the
+// offset sigma = a - start exact (Sterbenz), tau = sigma / (2 w) =
+// (low 47 bits of the significand) 2^-48, and the biased fixed-point row
+__device__ __forceinline__ double hyp_side_eval(const HypSide& S, double a)
+{
+    const uint64_t ab = (uint64_t)__double_as_longlong(a);
+    const int E = (int)(ab >> 52) - 1023;
+    if (E < E_MIN || E > S.e_max) return hyp_side_rare(S.seg, S.e_max, a);
+    const uint64_t low = ab & ((1ull << 47) - 1ull);
+    const double sig = __dadd_rn(a, -__longlong_as_double((long long)(ab - low)));
+    return segts_eval(S.fx + 32 * (E - E_MIN) + (int)((ab >> 47) & 31u), low << 16, sig);
 }
 
 __device__ __forceinline__ double hyp_eval(const HypSide& R, const HypSide& L, double v)
@@ -286,7 +307,7 @@ __device__ __forceinline__ double hyp_eval(const HypSide& R, const HypSide& L, d
     // pick the side's table first and evaluate once (selecting between two
     // evaluations would run both)
     const bool neg = (vb >> 63) != 0;
-    const HypSide S{neg ? L.seg : R.seg, neg ? L.e_max : R.e_max};
+    const HypSide S{neg ? L.seg : R.seg, neg ? L.fx : R.fx, neg ? L.e_max : R.e_max};
     double x = hyp_side_eval(S, a);
     if ((vb & 0x7fffffffffffffffull) >= 0x7ff0000000000000ull) x = a;   // inf, NaN
     return with_sign_of(x, vb);
@@ -322,7 +343,8 @@ using namespace qm;
 struct qm_hyp {
     int device;
     HypSide right, left;
-    ttbl::SegT* mem;
+    ttbl::SegT* mem;       // FP64 rows of both sides
+    ttbl::SegTX* fxmem;    // fixed-point rows of both sides
     double info[5];
 };
 
@@ -350,16 +372,39 @@ extern "C" qm_status qm_hyp_create(double alpha, double beta, double delta, qm_h
         for (int k = 0; k < 5; ++k) packed[i].b[k] = (float)c[5 + k];
         packed[i].pad = 0.0f;
     }
+    // fixed-point rows of the segments (binade E, segment j: width 2^(E-5)),
+    // 32 per binade from E_MIN; binades past e_max stay zero and unused
+    const size_t fper = (size_t)(32 * QM_HYP_MAX_BINADES);
+    std::vector<ttbl::SegTX> fx(2 * fper);
+    for (int side = 0; side < 2; ++side) {
+        const double* tab = side ? sl.data() : sr.data();
+        for (int E = E_MIN; E <= e_max[side]; ++E)
+            for (int j = 0; j < 32; ++j) {
+                const size_t i = (size_t)(32 * (E - E_MIN) + j);
+                st = pack_fx_biased(&tab[10 * (1 + i)], std::ldexp(1.0, E - 5), &fx[side * fper + i]);
+                if (st != QM_OK) {
+                    const std::string why = qm_last_error();      // fail() rewrites that buffer
+                    return fail(QM_ERR_UNSUPPORTED, "qm_hyp_create: %s side, binade %d, segment %d: %s",
+                                side ? "left" : "right", E, j, why.c_str());
+                }
+            }
+    }
     if (cudaGetDevice(&h.device) != cudaSuccess) return fail(QM_ERR_CUDA, "qm_hyp_create: no device");
     if (cudaMalloc(&h.mem, sizeof(ttbl::SegT) * packed.size()) != cudaSuccess)
         return fail(QM_ERR_NOMEM, "qm_hyp_create: table allocation failed");
-    if (cudaMemcpy(h.mem, packed.data(), sizeof(ttbl::SegT) * packed.size(), cudaMemcpyHostToDevice) !=
-        cudaSuccess) {
+    if (cudaMalloc(&h.fxmem, sizeof(ttbl::SegTX) * fx.size()) != cudaSuccess) {
         cudaFree(h.mem);
+        return fail(QM_ERR_NOMEM, "qm_hyp_create: table allocation failed");
+    }
+    if (cudaMemcpy(h.mem, packed.data(), sizeof(ttbl::SegT) * packed.size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(h.fxmem, fx.data(), sizeof(ttbl::SegTX) * fx.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(h.mem);
+        cudaFree(h.fxmem);
         return fail(QM_ERR_CUDA, "qm_hyp_create: table upload failed");
     }
-    h.right = HypSide{h.mem, e_max[0]};
-    h.left = HypSide{h.mem + per, e_max[1]};
+    h.right = HypSide{h.mem, h.fxmem, e_max[0]};
+    h.left = HypSide{h.mem + per, h.fxmem + fper, e_max[1]};
     *out = new qm_hyp(h);
     return QM_OK;
 }
@@ -394,6 +439,7 @@ extern "C" qm_status qm_hyp_destroy(qm_hyp* h)
 {
     if (!h) return QM_OK;
     cudaFree(h->mem);
+    cudaFree(h->fxmem);
     delete h;
     return QM_OK;
 }

@@ -54,4 +54,21 @@ static_assert(sizeof(SegTX) == 64, "one 64-byte row per segment");
 // segment violates one.
 qm_status t_pack_fx(const double* seg10, int nseg, ttbl::SegTX* out);
 
+// Rows for maps whose segment coefficients have mixed signs (the same 64-byte
+// SegTX layout, read by segts_eval): Q(start + sigma) = a0 + sigma P(tau),
+// tau = sigma / (2 w) in [0, 1/2) for a segment of width w, P > 0 but d_1..d_8
+// of either sign.  The unsigned chain then runs on biased accumulators:
+// acc_k + 2^60 for the outer steps (|acc_k| < 2^60; each step subtracts
+// floor(Sig / 16) = floor(2^60 tau), the bias carried through the high
+// product), D_1..D_3 stored as d_k 2^-s0 + 2^60, D_4 as d_4 2^-s0 + 2^51 in
+// the low 52 bits of D4e; the 32-bit inner chain on a_k + 2^29 (|a_k| < 2^29,
+// C_8 + 2^25 below 2^27 beside the shift).  s0 puts P 2^-s0 in [2^59, 2^61)
+// over the whole segment (P varies by less than a factor 2; checked from
+// the coefficient bounds), e0 = 1081 + s0.
+//
+// coef: c_0..c_9 of Q in s = sigma - h about the segment centre (h = w / 2).
+// Checks the ranges and the packed form against the original polynomial at
+// points of the segment (relative 1e-13); QM_ERR_UNSUPPORTED if one fails.
+qm_status pack_fx_biased(const double* coef, double w, ttbl::SegTX* out);
+
 }  // namespace qm

@@ -347,6 +347,91 @@ qm_status t_pack_fx(const double* seg10, int nseg, ttbl::SegTX* out)
     return QM_OK;
 }
 
+qm_status pack_fx_biased(const double* coef, double w, ttbl::SegTX* out)
+{
+    using LD = long double;
+    static const LD binom[10][10] = {
+        {1}, {1, 1}, {1, 2, 1}, {1, 3, 3, 1}, {1, 4, 6, 4, 1}, {1, 5, 10, 10, 5, 1},
+        {1, 6, 15, 20, 15, 6, 1}, {1, 7, 21, 35, 35, 21, 7, 1}, {1, 8, 28, 56, 70, 56, 28, 8, 1},
+        {1, 9, 36, 84, 126, 126, 84, 36, 9, 1}};
+    const LD h = (LD)w / 2;
+    LD cp[10];                                                   // about the start: s = sigma - h
+    for (int m = 0; m < 10; ++m) {
+        LD acc = 0, p = 1;
+        for (int k = m; k < 10; ++k) {
+            acc += (LD)coef[k] * binom[k][m] * p;
+            p *= -h;
+        }
+        cp[m] = acc;
+    }
+    LD d[9];                                                     // P in tau = sigma / (2 w)
+    for (int k = 0; k < 9; ++k) d[k] = cp[k + 1] * std::pow(2 * (LD)w, (LD)k);
+    LD var = 0;                                                  // bound on |P - d_0| over tau < 1/2
+    for (int k = 1; k < 9; ++k) var += std::fabs(d[k]) * std::ldexp((LD)1, -k);
+    const LD pmin = d[0] - var, pmax = d[0] + var;
+    if (!(pmin > 0) || !(pmax < 2 * pmin) || !std::isfinite((double)pmax))
+        return fail(QM_ERR_UNSUPPORTED, "fixed-point row: P not within a factor 2 over the segment");
+    int e2 = 0;
+    std::frexp((double)pmin, &e2);                               // pmin in [2^(e2-1), 2^e2)
+    const int s0 = e2 - 60;                                       // pmin 2^-s0 in [2^59, 2^60)
+    // every partial Horner value of the outer steps below 2^60 in magnitude
+    for (int k = 1; k <= 4; ++k) {
+        LD part = 0;
+        for (int i = k; i < 9; ++i) part += std::fabs(d[i]) * std::ldexp((LD)1, -(i - k));
+        if (!(std::ldexp(part, -s0) < std::ldexp((LD)1, 60) - 64))
+            return fail(QM_ERR_UNSUPPORTED, "fixed-point row: partial sum %d out of range", k);
+    }
+    long long D[5];
+    for (int k = 0; k < 5; ++k) D[k] = std::llround(std::ldexp(d[k], -s0));
+    const int e0 = 1081 + s0;
+    if (e0 <= 0 || e0 >= 2048 || D[4] <= -(1ll << 51) || D[4] >= (1ll << 51))
+        return fail(QM_ERR_UNSUPPORTED, "fixed-point row outside the exponent or D_4 range");
+    // inner chain on 32-bit integers under the scale 2^c: |a_k| < 2^29 for
+    // the partial values of C_5..C_7, |C_8| < 2^25
+    LD f[4], pm = 0;
+    for (int k = 0; k < 4; ++k) f[k] = std::ldexp(d[k + 5], -s0);
+    for (int k = 0; k < 4; ++k) {
+        LD part = 0;
+        for (int i = k; i < 4; ++i) part += std::fabs(f[i]) * std::ldexp((LD)1, -(i - k));
+        pm = std::max(pm, part);
+    }
+    int c = (pm > 0) ? std::max(1, (int)std::ceil(std::log2((double)pm)) - 28) : 1;
+    long long C[4];
+    for (;; ++c) {
+        if (c > 32) return fail(QM_ERR_UNSUPPORTED, "fixed-point row: inner chain out of range");
+        for (int k = 0; k < 4; ++k) C[k] = std::llround(std::ldexp(f[k], -c));
+        LD pmc = 0;
+        for (int k = 0; k < 4; ++k) {
+            LD part = 0;
+            for (int i = k; i < 4; ++i) part += std::fabs((LD)C[i]) * std::ldexp((LD)1, -(i - k));
+            pmc = std::max(pmc, part);
+        }
+        if (pmc < (LD)((1ll << 29) - 16) && C[3] > -(1ll << 25) && C[3] < (1ll << 25)) break;
+    }
+    ttbl::SegTX& r = *out;
+    r.a0 = (double)cp[0];
+    r.D0 = (unsigned long long)D[0];
+    r.D1 = (unsigned long long)(D[1] + (1ll << 60));
+    r.D2 = (unsigned long long)(D[2] + (1ll << 60));
+    r.D3 = (unsigned long long)(D[3] + (1ll << 60));
+    r.D4e = (unsigned long long)(D[4] + (1ll << 51)) | ((unsigned long long)e0 << 52);
+    for (int k = 0; k < 3; ++k) r.c[k] = (unsigned)(C[k] + (1ll << 29));
+    r.c[3] = (unsigned)(C[3] + (1ll << 25)) | ((unsigned)(32 - c) << 27);
+    // the packed form against the original expansion at points of the segment
+    for (int q = 0; q <= 4; ++q) {
+        const LD sig = (LD)w * q / 4 * (q == 4 ? (1 - 1.0L / 4096) : 1);
+        const LD tau = sig / (2 * (LD)w), sc = sig - h;
+        LD P = 0, ref = 0;
+        for (int k = 8; k >= 0; --k)
+            P = P * tau + (k < 5 ? std::ldexp((LD)D[k], s0) : std::ldexp((LD)C[k - 5], s0 + c));
+        for (int k = 9; k >= 0; --k) ref = ref * sc + (LD)coef[k];
+        const LD got = (LD)r.a0 + sig * P;
+        if (ref != 0 && std::fabs(got / ref - 1) > 1e-13L)
+            return fail(QM_ERR_UNSUPPORTED, "fixed-point row off by %g", (double)std::fabs(got / ref - 1));
+    }
+    return QM_OK;
+}
+
 namespace {
 
 struct Entry {
