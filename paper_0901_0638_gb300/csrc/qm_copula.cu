@@ -53,22 +53,45 @@ struct CopulaDev {
     const double* chi_c;                  //   and their centres
     const ttbl::SegT* g;                  // G rows (1 + ne 2^QM_TC_G_K)
     const double* g_c;                    //   and their 1 / m_c (row 0: unused)
+    const ttbl::SegTX* chi_fx;            // the same maps as biased fixed-point rows:
+    const ttbl::SegTX* g_fx;              //   QM_TC_NZ log W rows, 1 + ne 2^QM_TC_G_K G rows
     int ne;
     int pad;
 };
 
-// log W for the normal score z (|z| <= 8.3 on the 53-bit grid)
-__device__ __forceinline__ double tc_log_w(const CopulaDev& c, double z)
+// log W for the normal score z from the FP64 rows (z outside the table, NaN)
+static __device__ __noinline__ double tc_log_w_rare(const CopulaDev& c, double z)
 {
     int j = (int)(__fma_rn(z, (double)QM_TC_HZ_INV, QM_TC_Z_MAX * QM_TC_HZ_INV));
     j = min(max(j, 0), QM_TC_NZ - 1);
     return seg_poly(c.chi[j], z - __ldg(c.chi_c + j));
 }
 
-// G(t) = Phi^{-1}(F_nu(t)), no logarithm: |t| = 2^E m selects the row by E
-// and the top QM_TC_G_K bits of m, r = m / m_c - 1 is one FMA; below
-// 2^QM_TC_G_EMIN row 0 is the series about 0 in |t| itself
-__device__ __forceinline__ double tc_g(const CopulaDev& c, double t)
+// log W for the normal score z (|z| <= 8.3 on the 53-bit grid): in
+// u = z + z_max, segment j = floor(16 u) and the offset sigma = u - j/16
+// (exact) from the bits of u, tau = 8 sigma, one biased fixed-point row
+__device__ __forceinline__ double tc_log_w(const CopulaDev& c, double z)
+{
+    const double u = __dadd_rn(z, QM_TC_Z_MAX);
+    if (!(u >= 0.0 && u < 2.0 * QM_TC_Z_MAX)) return tc_log_w_rare(c, z);
+    const uint64_t ub = (uint64_t)__double_as_longlong(u);
+    const int Eu = (int)(ub >> 52) - 1023;                           // u < 17: Eu <= 4
+    const uint64_t M = (ub & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
+    const int q = 48 - Eu;                                            // bits of M below 1/16
+    const bool first = q >= 53;                                       // u < 1/16: segment 0
+    const uint64_t low = first ? M : (M & ((1ull << q) - 1ull));
+    const int j = first ? 0 : (int)(M >> q);
+    const double start = first ? 0.0 : __longlong_as_double((long long)(ub & ~((1ull << q) - 1ull)));
+    const double sig = __dadd_rn(u, -start);
+    const int sh = Eu + 15;                                           // sigma 2^67 = low 2^(Eu + 15)
+    const uint64_t Sig = sh >= 0 ? (low << sh) : (sh > -64 ? (low >> -sh) : 0ull);
+    return segts_eval(c.chi_fx + j, Sig, sig);
+}
+
+// G(t) from the FP64 rows (|t| past the table, inf, NaN): |t| = 2^E m
+// selects the row by E and the top QM_TC_G_K bits of m, r = m / m_c - 1 is
+// one FMA (the last binade's rows continue beyond it)
+static __device__ __noinline__ double tc_g_rare(const CopulaDev& c, double t)
 {
     const double a = fabs(t);
     const unsigned long long b = (unsigned long long)__double_as_longlong(a);
@@ -80,6 +103,29 @@ __device__ __forceinline__ double tc_g(const CopulaDev& c, double t)
     const double m = __longlong_as_double((long long)((b & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull));
     const double v = small ? a : __fma_rn(m, __ldg(c.g_c + row), -1.0);
     return copysign(seg_poly(c.g[row], v), t);
+}
+
+// G(t) = Phi^{-1}(F_nu(t)) from the biased fixed-point rows, no logarithm:
+// |t| >= 2^QM_TC_G_EMIN takes segment j of binade E (sigma = |t| - start
+// exact, tau = the significand's low 47 bits 2^-48); below, row 0 (the
+// series about 0: sigma = |t|, tau = 16 |t|).  Odd in t.
+__device__ __forceinline__ double tc_g(const CopulaDev& c, double t)
+{
+    const uint64_t tb = (uint64_t)__double_as_longlong(t);
+    const uint64_t b = tb & 0x7fffffffffffffffull;
+    const int E = (int)(b >> 52) - 1023;
+    const int e = E - QM_TC_G_EMIN;
+    if (e >= c.ne) return tc_g_rare(c, t);
+    const double a = __longlong_as_double((long long)b);
+    const bool small = e < 0;
+    const uint64_t low = b & ((1ull << 47) - 1ull);
+    const uint64_t M = (b & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = E + 16;                                            // |t| 2^68 = M 2^(E + 16)
+    const uint64_t Sig0 = sh >= 0 ? ((M << sh) & 0x7fffffffffffffffull) : (sh > -64 ? (M >> -sh) : 0ull);
+    const int row = small ? 0 : 1 + (e << QM_TC_G_K) + (int)((b >> 47) & 31u);
+    const double start = small ? 0.0 : __longlong_as_double((long long)(b - low));
+    const double r = segts_eval(c.g_fx + row, small ? Sig0 : (low << 16), __dadd_rn(a, -start));
+    return with_sign_of(r, tb);
 }
 
 // normal from two Philox words (53-bit integer, exact reflected grid point,
@@ -316,8 +362,11 @@ extern "C" qm_status qm_tcopula_create(int d, double nu, const double* chol, con
     c.host.half_log_nu = 0.5 * std::log(nu);
     const void* chi = nullptr;
     const void* g = nullptr;
-    st = tcop_table_device(nu, &chi, &g, &c.host.ne);
+    const void* fx = nullptr;
+    st = tcop_table_device(nu, &chi, &g, &fx, &c.host.ne);
     if (st != QM_OK) return st;
+    c.host.chi_fx = static_cast<const ttbl::SegTX*>(fx);
+    c.host.g_fx = c.host.chi_fx + QM_TC_NZ;
     c.host.chi = static_cast<const ttbl::SegT*>(chi);
     c.host.chi_c = reinterpret_cast<const double*>(c.host.chi + QM_TC_NZ);
     c.host.g = static_cast<const ttbl::SegT*>(g);

@@ -37,6 +37,6 @@ qm_status t_select(double nu, int* k, const void** seg_dev, const double** tail_
 qm_status tcop_table_build(double nu, double* chi_seg, double* g_seg, int* ne);
 // Device layout: 64-byte rows (coefficients 0..4 double, 5..9 float, the
 // Student-t segment layout) followed by one double per row (centre or 1 / m_c).
-qm_status tcop_table_device(double nu, const void** chi, const void** g, int* ne);
+qm_status tcop_table_device(double nu, const void** chi, const void** g, const void** fx, int* ne);
 
 }  // namespace qm

@@ -381,7 +381,8 @@ extern "C" qm_status qm_hyp_create(double alpha, double beta, double delta, qm_h
         for (int E = E_MIN; E <= e_max[side]; ++E)
             for (int j = 0; j < 32; ++j) {
                 const size_t i = (size_t)(32 * (E - E_MIN) + j);
-                st = pack_fx_biased(&tab[10 * (1 + i)], std::ldexp(1.0, E - 5), &fx[side * fper + i]);
+                st = pack_fx_biased(&tab[10 * (1 + i)], std::ldexp(1.0, E - 5), std::ldexp(1.0, E - 6),
+                                    &fx[side * fper + i]);
                 if (st != QM_OK) {
                     const std::string why = qm_last_error();      // fail() rewrites that buffer
                     return fail(QM_ERR_UNSUPPORTED, "qm_hyp_create: %s side, binade %d, segment %d: %s",

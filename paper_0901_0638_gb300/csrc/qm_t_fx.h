@@ -66,9 +66,10 @@ qm_status t_pack_fx(const double* seg10, int nseg, ttbl::SegTX* out);
 // over the whole segment (P varies by less than a factor 2; checked from
 // the coefficient bounds), e0 = 1081 + s0.
 //
-// coef: c_0..c_9 of Q in s = sigma - h about the segment centre (h = w / 2).
-// Checks the ranges and the packed form against the original polynomial at
-// points of the segment (relative 1e-13); QM_ERR_UNSUPPORTED if one fails.
-qm_status pack_fx_biased(const double* coef, double w, ttbl::SegTX* out);
+// coef: c_0..c_9 of Q in s = sigma - h about the point h from the segment
+// start (h = w / 2 for the centre; h = 0 keeps a0 = c_0 exactly).  Checks the
+// ranges and the packed form against the original polynomial at points of
+// the segment (relative 1e-13); QM_ERR_UNSUPPORTED if one fails.
+qm_status pack_fx_biased(const double* coef, double w, double h, ttbl::SegTX* out);
 
 }  // namespace qm

@@ -39,6 +39,7 @@
 
 #include "qm.h"
 #include "qm_host.h"
+#include "qm_t_fx.h"
 
 namespace qm {
 namespace {
@@ -411,8 +412,41 @@ struct TcEntry {
     double nu;
     void* chi;     // device: QM_TC_NZ packed rows, then QM_TC_NZ centres
     void* g;       // device: 1 + ne 2^QM_TC_G_K packed rows, then as many 1 / m_c
+    void* fx;      // device: QM_TC_NZ fixed-point log W rows, then 1 + ne 2^QM_TC_G_K G rows
     int ne;
 };
+
+// The fixed-point rows (pack_fx_biased): log W on [j/16 - z_max, + 1/16)
+// about its centre; G row 0 the series about t = 0 on [0, 2^G_EMIN); G row
+// 1 + e 2^K + j on |t| in [2^E (1 + j/32), + 2^(E-5)), E = G_EMIN + e, its
+// series in r = m / m_c - 1 turned into one in s = |t| - 2^E m_c
+// (coefficient k divided by (2^E m_c)^k).
+qm_status tcop_pack_fx(const double* hc, const double* hg, int ne, std::vector<ttbl::SegTX>& fx)
+{
+    const int ng = 1 + ne * (1 << QM_TC_G_K);
+    fx.assign(QM_TC_NZ + ng, ttbl::SegTX{});
+    const double wz = 1.0 / QM_TC_HZ_INV;
+    for (int j = 0; j < QM_TC_NZ; ++j) {
+        const double start = j * wz - QM_TC_Z_MAX;
+        const qm_status st = pack_fx_biased(&hc[RW * j], wz, hc[RW * j + DO + 1] - start, &fx[j]);
+        if (st != QM_OK) return st;
+    }
+    qm_status st = pack_fx_biased(&hg[0], std::ldexp(1.0, QM_TC_G_EMIN), 0.0, &fx[QM_TC_NZ]);
+    if (st != QM_OK) return st;
+    for (int i = 1; i < ng; ++i) {
+        const int E = QM_TC_G_EMIN + ((i - 1) >> QM_TC_G_K);
+        const double cabs = std::ldexp(1.0, E) / hg[RW * i + DO + 1];
+        double b[DO + 1];
+        double p = 1.0;
+        for (int k = 0; k <= DO; ++k) {
+            b[k] = hg[RW * i + k] / p;
+            p *= cabs;
+        }
+        st = pack_fx_biased(b, std::ldexp(1.0, E - QM_TC_G_K), std::ldexp(1.0, E - QM_TC_G_K - 1), &fx[QM_TC_NZ + i]);
+        if (st != QM_OK) return st;
+    }
+    return QM_OK;
+}
 
 std::mutex g_tc_mu;
 std::vector<TcEntry> g_tc_cache;
@@ -439,7 +473,7 @@ std::vector<unsigned char> pack_rows(const double* rows, int n)
 // Device tables for nu on the current device, built and uploaded at first use
 // (kept until the process exits): packed rows, then the rows' centres (log W)
 // or 1 / m_c (G).
-qm_status tcop_table_device(double nu, const void** chi, const void** g, int* ne)
+qm_status tcop_table_device(double nu, const void** chi, const void** g, const void** fx, int* ne)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return fail(QM_ERR_CUDA, "t copula: no current device");
@@ -448,6 +482,7 @@ qm_status tcop_table_device(double nu, const void** chi, const void** g, int* ne
         if (e.device == dev && e.nu == nu) {
             *chi = e.chi;
             *g = e.g;
+            *fx = e.fx;
             *ne = e.ne;
             return QM_OK;
         }
@@ -458,20 +493,29 @@ qm_status tcop_table_device(double nu, const void** chi, const void** g, int* ne
     if (st != QM_OK) return st;
     const std::vector<unsigned char> pc = pack_rows(hc.data(), QM_TC_NZ);
     const std::vector<unsigned char> pg = pack_rows(hg.data(), 1 + n * (1 << QM_TC_G_K));
-    TcEntry e{dev, nu, nullptr, nullptr, n};
-    if (cudaMalloc(&e.chi, pc.size()) != cudaSuccess || cudaMalloc(&e.g, pg.size()) != cudaSuccess) {
+    std::vector<ttbl::SegTX> pf;
+    const qm_status pst = tcop_pack_fx(hc.data(), hg.data(), n, pf);
+    if (pst != QM_OK) return pst;
+    const size_t fbytes = sizeof(ttbl::SegTX) * pf.size();
+    TcEntry e{dev, nu, nullptr, nullptr, nullptr, n};
+    if (cudaMalloc(&e.chi, pc.size()) != cudaSuccess || cudaMalloc(&e.g, pg.size()) != cudaSuccess ||
+        cudaMalloc(&e.fx, fbytes) != cudaSuccess) {
         if (e.chi) cudaFree(e.chi);
+        if (e.g) cudaFree(e.g);
         return fail(QM_ERR_NOMEM, "t copula: table allocation failed");
     }
     if (cudaMemcpy(e.chi, pc.data(), pc.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(e.g, pg.data(), pg.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaMemcpy(e.g, pg.data(), pg.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(e.fx, pf.data(), fbytes, cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaFree(e.chi);
         cudaFree(e.g);
+        cudaFree(e.fx);
         return fail(QM_ERR_CUDA, "t copula: table upload failed");
     }
     g_tc_cache.push_back(e);
     *chi = e.chi;
     *g = e.g;
+    *fx = e.fx;
     *ne = e.ne;
     return QM_OK;
 }

@@ -347,14 +347,14 @@ qm_status t_pack_fx(const double* seg10, int nseg, ttbl::SegTX* out)
     return QM_OK;
 }
 
-qm_status pack_fx_biased(const double* coef, double w, ttbl::SegTX* out)
+qm_status pack_fx_biased(const double* coef, double w, double h_in, ttbl::SegTX* out)
 {
     using LD = long double;
     static const LD binom[10][10] = {
         {1}, {1, 1}, {1, 2, 1}, {1, 3, 3, 1}, {1, 4, 6, 4, 1}, {1, 5, 10, 10, 5, 1},
         {1, 6, 15, 20, 15, 6, 1}, {1, 7, 21, 35, 35, 21, 7, 1}, {1, 8, 28, 56, 70, 56, 28, 8, 1},
         {1, 9, 36, 84, 126, 126, 84, 36, 9, 1}};
-    const LD h = (LD)w / 2;
+    const LD h = (LD)h_in;
     LD cp[10];                                                   // about the start: s = sigma - h
     for (int m = 0; m < 10; ++m) {
         LD acc = 0, p = 1;
