@@ -246,6 +246,18 @@ qm_status qm_recycle(int src, int dst, const qm_params* p, const double* in,
 #define QM_T_NU_MAX 100.0
 qm_status qm_t_table_build(double nu, double* seg_coef, double* tail);
 
+/* qm_t_rows_build (host only, no GPU): the same segments as the device holds
+ * them -- QM_T_NSEG rows of 64 bytes (QM_FX_ROW_BYTES), segment j re-expanded
+ * about z_j = j/32 and packed for the unsigned fixed-point chain:
+ *   double a0;  uint64 D0, D1, D2, D3, D4e;  uint32 c[4]
+ * |t| = a0 + sigma P(tau), sigma = |z| - z_j, tau = 16 sigma; P = sum d_k tau^k
+ * with D_k = d_k 2^-s0 (k <= 4; D4e = D_4 | e0 << 52, e0 = 1081 + s0) and
+ * c[0..2] = C_5..C_7, c[3] = C_8 | (32 - c) << 27, C_k = d_k 2^-(s0 + c).
+ * Errors as qm_t_table_build; QM_ERR_UNSUPPORTED if a segment does not fit
+ * the form (signs, ranges, or off by more than 1e-13 after packing).       */
+#define QM_FX_ROW_BYTES 64
+qm_status qm_t_rows_build(double nu, void* rows);
+
 /* ---- exponential -> hyperbolic recycling (Sec. 8.1) --------------------------
  * Target: the hyperbolic density f(x) = exp(-alpha sqrt(delta^2 + x^2) +
  * beta x) / Z (location 0; Z = 2 alpha delta K_1(delta gamma) / gamma,
@@ -281,6 +293,17 @@ qm_status qm_hyp_info(const qm_hyp* h, double* info);
 qm_status qm_hyp_destroy(qm_hyp* h);
 qm_status qm_hyp_table_build(double alpha, double beta, double delta, double* seg_right,
                              double* seg_left, int* e_max, double* info);
+
+/* qm_hyp_rows_build (host only, no GPU): the fixed-point rows the device
+ * evaluates, 32 QM_HYP_MAX_BINADES rows of QM_FX_ROW_BYTES per side (row
+ * 32 (E - QM_HYP_E_MIN) + j for segment j of binade E, width 2^(E-5), up to
+ * e_max[side]; later rows zero).  Layout as qm_t_rows_build, but biased for
+ * coefficients of either sign: |Q| = a0 + sigma P(tau), sigma = |v| - start,
+ * tau = sigma / 2^(E-4); D1..D3 hold d_k 2^-s0 + 2^60, D4e the low 52 bits
+ * d_4 2^-s0 + 2^51 (e0 above), c[0..2] C_k + 2^29, c[3] (C_8 + 2^25) |
+ * (32 - c) << 27.  Errors as qm_hyp_table_build.                           */
+qm_status qm_hyp_rows_build(double alpha, double beta, double delta, void* rows_right, void* rows_left,
+                            int* e_max);
 
 /* ---- Gaussian copula with recycled marginals (Sec. 9) ------------------------
  * Samples x in R^d with a Gaussian copula of correlation L L^T and the given

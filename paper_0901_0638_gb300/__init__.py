@@ -92,6 +92,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "qm_hyp_info": [vp, vp],
         "qm_hyp_destroy": [vp],
         "qm_hyp_table_build": [d, d, d, vp, vp, vp, vp],
+        "qm_hyp_rows_build": [d, d, d, vp, vp, vp],
+        "qm_t_rows_build": [d, vp],
         "qm_copula_create": [i, vp, vp, vp],
         "qm_tcopula_create": [i, d, vp, vp, vp],
         "qm_tcopula_table_build": [d, vp, vp, vp],
@@ -230,6 +232,20 @@ def qm_t_table_build(nu: float):
     return seg, tail
 
 
+QM_FX_ROW_BYTES = 64
+
+
+def qm_t_rows_build(nu: float):
+    """The Student-t segments as the device holds them (no GPU): a
+    (QM_T_NSEG, 8) uint64 array, one 64-byte fixed-point row per segment
+    (a0 bits, D0..D3, D4 | e0 << 52, then the four 32-bit inner-chain words
+    packed two per uint64, low word first)."""
+    import numpy as np
+    rows = np.zeros((QM_T_NSEG, QM_FX_ROW_BYTES // 8), dtype=np.uint64)
+    _check(load().qm_t_rows_build(float(nu), rows.ctypes.data))
+    return rows
+
+
 QM_TC_Z_MAX, QM_TC_HZ_INV, QM_TC_NZ, QM_TC_ROW = 8.5, 16, 272, 11
 QM_TC_G_EMIN, QM_TC_G_K, QM_TC_G_NE_MAX = -5, 5, 128
 
@@ -266,6 +282,20 @@ def qm_hyp_table_build(alpha: float, beta: float, delta: float):
     _check(load().qm_hyp_table_build(float(alpha), float(beta), float(delta), right.ctypes.data,
                                      left.ctypes.data, e_max.ctypes.data, info.ctypes.data))
     return right, left, e_max, info
+
+
+def qm_hyp_rows_build(alpha: float, beta: float, delta: float):
+    """The biased fixed-point rows the device evaluates (no GPU): (right,
+    left, e_max), each side a (32 QM_HYP_MAX_BINADES, 8) uint64 array, row
+    32 (E - QM_HYP_E_MIN) + j for segment j of binade E up to e_max."""
+    import numpy as np
+    per = 32 * QM_HYP_MAX_BINADES
+    right = np.zeros((per, QM_FX_ROW_BYTES // 8), dtype=np.uint64)
+    left = np.zeros((per, QM_FX_ROW_BYTES // 8), dtype=np.uint64)
+    e_max = np.zeros(2, dtype=np.int32)
+    _check(load().qm_hyp_rows_build(float(alpha), float(beta), float(delta), right.ctypes.data,
+                                    left.ctypes.data, e_max.ctypes.data))
+    return right, left, e_max
 
 
 class Hyperbolic:

@@ -35,6 +35,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -348,6 +349,51 @@ struct qm_hyp {
     double info[5];
 };
 
+namespace qm {
+namespace {
+
+// The fixed-point rows of both sides from the FP64 tables (binade E,
+// segment j: width 2^(E-5), expanded about its centre), 32 per binade from
+// E_MIN; rows past e_max stay zero and unused.
+qm_status hyp_pack_rows(const double* sr, const double* sl, const int* e_max, ttbl::SegTX* fr, ttbl::SegTX* fl)
+{
+    for (int side = 0; side < 2; ++side) {
+        const double* tab = side ? sl : sr;
+        ttbl::SegTX* out = side ? fl : fr;
+        for (int E = E_MIN; E <= e_max[side]; ++E)
+            for (int j = 0; j < 32; ++j) {
+                const size_t i = (size_t)(32 * (E - E_MIN) + j);
+                const qm_status st = pack_fx_biased(&tab[10 * (1 + i)], std::ldexp(1.0, E - 5),
+                                                    std::ldexp(1.0, E - 6), &out[i]);
+                if (st != QM_OK) {
+                    const std::string why = qm_last_error();      // fail() rewrites that buffer
+                    return fail(QM_ERR_UNSUPPORTED, "hyperbolic: %s side, binade %d, segment %d: %s",
+                                side ? "left" : "right", E, j, why.c_str());
+                }
+            }
+    }
+    return QM_OK;
+}
+
+}  // namespace
+}  // namespace qm
+
+extern "C" qm_status qm_hyp_rows_build(double alpha, double beta, double delta, void* rows_right, void* rows_left,
+                                       int* e_max)
+{
+    if (!rows_right || !rows_left || !e_max) return fail(QM_ERR_INVALID, "qm_hyp_rows_build: null pointer");
+    const size_t per = (size_t)(1 + 32 * QM_HYP_MAX_BINADES);
+    std::vector<double> sr(10 * per), sl(10 * per);
+    double info[5];
+    qm_status st = hyp_table_build(alpha, beta, delta, sr.data(), sl.data(), e_max, info);
+    if (st != QM_OK) return st;
+    const size_t fper = (size_t)(32 * QM_HYP_MAX_BINADES);
+    std::memset(rows_right, 0, sizeof(ttbl::SegTX) * fper);
+    std::memset(rows_left, 0, sizeof(ttbl::SegTX) * fper);
+    return hyp_pack_rows(sr.data(), sl.data(), e_max, static_cast<ttbl::SegTX*>(rows_right),
+                         static_cast<ttbl::SegTX*>(rows_left));
+}
+
 extern "C" qm_status qm_hyp_table_build(double alpha, double beta, double delta, double* seg_right,
                                         double* seg_left, int* e_max, double* info)
 {
@@ -372,24 +418,10 @@ extern "C" qm_status qm_hyp_create(double alpha, double beta, double delta, qm_h
         for (int k = 0; k < 5; ++k) packed[i].b[k] = (float)c[5 + k];
         packed[i].pad = 0.0f;
     }
-    // fixed-point rows of the segments (binade E, segment j: width 2^(E-5)),
-    // 32 per binade from E_MIN; binades past e_max stay zero and unused
     const size_t fper = (size_t)(32 * QM_HYP_MAX_BINADES);
     std::vector<ttbl::SegTX> fx(2 * fper);
-    for (int side = 0; side < 2; ++side) {
-        const double* tab = side ? sl.data() : sr.data();
-        for (int E = E_MIN; E <= e_max[side]; ++E)
-            for (int j = 0; j < 32; ++j) {
-                const size_t i = (size_t)(32 * (E - E_MIN) + j);
-                st = pack_fx_biased(&tab[10 * (1 + i)], std::ldexp(1.0, E - 5), std::ldexp(1.0, E - 6),
-                                    &fx[side * fper + i]);
-                if (st != QM_OK) {
-                    const std::string why = qm_last_error();      // fail() rewrites that buffer
-                    return fail(QM_ERR_UNSUPPORTED, "qm_hyp_create: %s side, binade %d, segment %d: %s",
-                                side ? "left" : "right", E, j, why.c_str());
-                }
-            }
-    }
+    st = hyp_pack_rows(sr.data(), sl.data(), e_max, fx.data(), fx.data() + fper);
+    if (st != QM_OK) return st;
     if (cudaGetDevice(&h.device) != cudaSuccess) return fail(QM_ERR_CUDA, "qm_hyp_create: no device");
     if (cudaMalloc(&h.mem, sizeof(ttbl::SegT) * packed.size()) != cudaSuccess)
         return fail(QM_ERR_NOMEM, "qm_hyp_create: table allocation failed");

@@ -585,3 +585,12 @@ extern "C" qm_status qm_t_table_build(double nu, double* seg_coef, double* tail)
     if (!seg_coef || !tail) return qm::fail(QM_ERR_INVALID, "qm_t_table_build: null pointer");
     return qm::t_table_build(nu, seg_coef, tail);
 }
+
+extern "C" qm_status qm_t_rows_build(double nu, void* rows)
+{
+    if (!rows) return qm::fail(QM_ERR_INVALID, "qm_t_rows_build: null pointer");
+    std::vector<double> seg(10 * QM_T_NSEG), tail(3 + QM_T_TAIL_TERMS);
+    const qm_status st = qm::t_table_build(nu, seg.data(), tail.data());
+    if (st != QM_OK) return st;
+    return qm::t_pack_fx(seg.data(), QM_T_NSEG, static_cast<qm::ttbl::SegTX*>(rows));
+}

@@ -1,0 +1,336 @@
+"""CPU checks of the fixed-point segment rows that the FP64 kernels evaluate
+(no GPU): the generated tables -- csrc/qm_fx_tables.h for the normal
+quantile (the exponential coordinate of Sec. 6 / Sec. 7.2, expansions from
+the recycling ODE of Sec. 2.3) and csrc/qm_exp_fx_tables.h for the
+exponential -> normal map -- read as text, the device arithmetic emulated
+exactly on Python integers (high products from three 32-bit limb
+products, the 32-bit inner chain, the one-bit normalisation and the bit
+assembly of the polynomial's value, the final FMA rounded once), and the
+results compared with the oracle at the library's bars (4e-15 for the
+normal quantile, 1e-12 for the recycled map).  The inputs cover the top
+binade's segments next to u = 1/2, segment boundaries, the tail-stress
+mixture's binades down to subnormal d, and mirrored u >= 1/2."""
+import os
+import re
+import struct
+from fractions import Fraction as Fr
+
+import numpy as np
+import pytest
+
+import oracle
+
+CSRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_0901_0638_gb300", "csrc")
+M64 = (1 << 64) - 1
+MANT = (1 << 52) - 1
+
+
+def bits(x: float) -> int:
+    return struct.unpack("<Q", struct.pack("<d", x))[0]
+
+
+def dbl(b: int) -> float:
+    return struct.unpack("<d", struct.pack("<Q", b & M64))[0]
+
+
+def mulhi3(a: int, b: int) -> int:
+    """The kernels' high product: a1 b1 + hi32(a0 b1 + a1 b0), a < 2^62, b < 2^63."""
+    assert 0 <= a < 2**62 and 0 <= b < 2**63
+    a0, a1, b0, b1 = a & 0xFFFFFFFF, a >> 32, b & 0xFFFFFFFF, b >> 32
+    m = a0 * b1 + a1 * b0
+    assert m < 2**64
+    r = a1 * b1 + (m >> 32)
+    assert 0 <= ((a * b) >> 64) - r <= 1          # exact or one unit low
+    return r
+
+
+def inner(w, t32: int) -> int:
+    """32-bit inner chain on (C_a, C_b, C_c, C_d | sh << 27), Horner, and its
+    join floor(C t32 / 2^sh)."""
+    x = w[3] & 0x07FFFFFF
+    for ck in (w[2], w[1], w[0]):
+        x = ck + ((x * t32) >> 32)
+        assert x < 2**32
+    return (x * t32) >> (w[3] >> 27)
+
+
+def _int(tok: str) -> int:
+    tok = tok.strip()
+    if tok.startswith("("):                           # (-0x7fffffffffffffffll - 1)
+        return -(2**63)
+    return int(tok.rstrip("ul").rstrip("l"), 0)
+
+
+@pytest.fixture(scope="module")
+def fx_table():
+    """(A rows: a0 bits, B0, B1, B2 | e0;  C rows: four 32-bit words)."""
+    text = open(os.path.join(CSRC, "qm_fx_tables.h")).read()
+    body = text[text.index("SEG_FX = {"):]
+    a_part, c_part = body.split(" },\n {\n", 1)
+    A = []
+    for m in re.finditer(r"\{(0x[0-9a-fp.+-]+|[-0-9.e+]+),([^,{}]+),([^,{}]+),([^{}]+)\}", a_part):
+        A.append((bits(float.fromhex(m.group(1))), _int(m.group(2)) & M64, _int(m.group(3)) & M64,
+                  _int(m.group(4)) & M64))
+    C = [tuple(int(x.rstrip("u"), 16) for x in m.group(1).split(","))
+         for m in re.finditer(r"\{(0x[0-9a-f]+u,0x[0-9a-f]+u,0x[0-9a-f]+u,0x[0-9a-f]+u|0u,0u,0u,0u)\}", c_part)]
+    assert len(A) == len(C) == (1072 + 2) << 6
+    return A, C
+
+
+def probit_fixed(A, C, u: float) -> float:
+    """The FIXED kernel's arithmetic for 0 < u < 1 (the reflection and the
+    normalisation of x = 2d on the bits, segment (binade, top 6 bits),
+    Tp = complement of the low 46 bits, the chains, the FMA)."""
+    ub = bits(u)
+    upper = ub >= 0x3FE0000000000000
+    frac = ub & MANT
+    eb = (ub >> 52) & 0x7FF
+    S = (1 << 52) - frac if upper else ((frac | (1 << 52)) if eb else frac)
+    base = 0 if upper else max(eb, 1) - 1022
+    lz = 64 - (S | 1).bit_length() - 11
+    Mx = S << lz
+    assert 2**52 <= Mx < 2**53
+    e = -1 - (base - lz)
+    ec = min(max(e, -1), 1072) + 1
+    idx = (ec << 6) + ((Mx >> 46) & 63)
+    Tp = ~Mx & ((1 << 46) - 1)
+    a0b, B0, B1, B2s = A[idx]
+    acc = (B2s & MANT) + inner(C[idx], Tp >> 15)
+    acc = B1 + mulhi3(acc, Tp << 17)
+    acc = B0 + mulhi3(acc, Tp << 17)
+    if acc == 0:                                  # the zero rows of u = 1/2
+        hbits = 0
+    else:
+        assert 2**61 <= acc < 2**63
+        top = acc >> 62
+        hbits = ((acc + (256 << top)) >> (9 + top)) + (((B2s >> 52) + top) << 52)
+    tu = Fr(Tp + 1, 2**52)
+    z = float(tu * Fr(dbl(hbits)) + Fr(dbl(a0b)))
+    return z if upper else -z
+
+
+def normal_inputs():
+    rng = np.random.default_rng(2026)
+    k = rng.integers(1, 2**53, 1500, dtype=np.int64)
+    uni = k.astype(np.float64) * 2.0**-53                        # 53-bit grid
+    ee = rng.integers(1, 1075, 800)
+    mm = rng.uniform(0.5, 1.0, 800)
+    tails = np.ldexp(mm, -ee)                                     # tail stress, down to subnormal
+    mirrored = 1.0 - tails[:300][tails[:300] > 2.0**-53]          # u >= 1/2 reflections
+    bounds = []
+    for e in (0, 1, 2, 7, 40, 300, 1000):                         # x = 2d at segment boundaries
+        for j in (0, 1, 31, 62, 63):
+            x = np.ldexp(1.0 + j / 64.0, -e - 1)
+            bounds += [x / 2, np.nextafter(x / 2, 0.0), np.nextafter(x / 2, 1.0)]
+    near_half = 0.5 + np.arange(-40, 41) * 2.0**-53
+    u = np.concatenate([uni, tails, mirrored, np.array(bounds), near_half])
+    return u[(u > 0) & (u < 1)]
+
+
+def test_fixed_table_rows_against_the_oracle(fx_table):
+    A, C = fx_table
+    u = normal_inputs()
+    w = oracle.probit(u)
+    z = np.array([probit_fixed(A, C, float(x)) for x in u])
+    zero = w == 0
+    assert np.all(z[zero] == 0.0)
+    r = np.abs(z[~zero] / w[~zero] - 1)
+    print(f"fixed-point table rows, emulated: {len(u)} inputs, max rel {r.max():.3g}")
+    assert r.max() <= 4e-15, u[~zero][np.argmax(r)]
+    # symmetry is exact: x = 2d is formed identically for u and 1 - u
+    pair = u[(u > 0.5) & (u < 1 - 2.0**-53)][:200]
+    for x in pair:
+        assert probit_fixed(A, C, float(x)) == -probit_fixed(A, C, float(1.0 - x))
+
+
+@pytest.fixture(scope="module")
+def exp_rows():
+    """ROWS_V, ROWS_X: (a0 bits, D0, D1, D2, D3, D4 | e0, (four 32-bit words))."""
+    text = open(os.path.join(CSRC, "qm_exp_fx_tables.h")).read()
+    consts = {k: int(v) for k, v in re.findall(r"constexpr int (\w+) = (-?\d+);", text)}
+
+    def rows(name):
+        body = text[text.index(name + "["):]
+        body = body[:body.index("};")]
+        out = []
+        for m in re.finditer(r"\{([^{},]+),(\d+)ull,(\d+)ull,(\d+)ull,(\d+)ull,(\d+)ull,\{([^}]*)\}\}", body):
+            w = tuple(int(x.strip().rstrip("u"), 16) if x.strip() != "0" else 0 for x in m.group(7).split(","))
+            out.append((bits(float.fromhex(m.group(1))),) + tuple(int(m.group(k)) for k in range(2, 7)) + (w,))
+        return out
+
+    V, X = rows("ROWS_V"), rows("ROWS_X")
+    assert len(V) == consts["NV"] and len(X) == consts["NX"]
+    return V, X, consts
+
+
+def segtx(row, Sig: int, mlt: float) -> float:
+    """One fixed-point row (Horner inner chain): fma(mlt, P(Sig 2^-64), a0)."""
+    a0b, D0, D1, D2, D3, D4e, w = row
+    acc = (D4e & MANT) + inner(w, Sig >> 32)
+    for D in (D3, D2, D1, D0):
+        assert acc < 2**62
+        acc = D + mulhi3(acc, Sig)
+    assert 2**59 <= acc < 2**61
+    top = acc >> 60
+    pm = (acc + (64 << top)) >> (7 + top)
+    P = dbl(pm + (((D4e >> 52) + top) << 52))
+    return float(Fr(mlt) * Fr(P) + Fr(dbl(a0b)))
+
+
+def exp_fixed(V, X, consts, x: float):
+    """The exponential -> normal kernel's branch-free path (None where the
+    kernel takes its out-of-line path: x < 2^-26, v >= 64, edge values)."""
+    xb = bits(x)
+    if xb == 0 or xb >= 0x7FF0000000000000:
+        return None
+    v = (x - 0.69314718055994528623) - 2.3190468138462996154e-17
+    vside = v >= -0.015625
+    if (not (v < 64.0)) if vside else (xb < 0x3E50000000000000):
+        return None
+    if vside:
+        vb = bits(v)
+        Ev = ((vb >> 52) & 0x7FF) - 1023
+        Mv = (vb & MANT) | (1 << 52)
+        fine, row0 = v < 1.0, v < 0.03125
+        shv = min(max(47 - Ev if fine else 49 - Ev, 0), 63)
+        q = (Mv >> shv) & 0xFFFFFFFF
+        rv = 0 if row0 else min(q if fine else consts["V_FINE"] + q - consts["V_COARSE"], consts["NV"] - 1)
+        nq = 1 if row0 else (q + 1) & 0xFFFF
+        ln = (nq | 1).bit_length() - 1
+        veb = ((ln - (5 if fine else 3) + 1023) << 52) | ((nq << (52 - ln)) & MANT)
+        t = dbl(veb) - v
+        tb = bits(t)
+        Mt = (tb & MANT) | (1 << 52)
+        st = ((tb >> 52) & 0x7FF) - 1023 + 12 + (3 if fine else 1)
+        Sig = 0 if tb == 0 else (((Mt << min(st, 63)) & (2**63 - 1)) if st >= 0 else (Mt >> -st if st > -64 else 0))
+        return segtx(V[rv], Sig, v if row0 else -t)
+    Ex = (xb >> 52) - 1023
+    rx = (min(max(-1 - Ex, 0), (consts["NX"] >> consts["X_K"]) - 1) << consts["X_K"]) + ((xb >> 47) & 31)
+    Tp = ~xb & ((1 << 47) - 1)
+    tu = dbl(0x3FF0000000000001 + Tp) - 1.0
+    return -segtx(X[rx], Tp << 16, tu)
+
+
+def test_exp_to_normal_rows_against_the_oracle(exp_rows):
+    V, X, consts = exp_rows
+    rng = np.random.default_rng(2027)
+    ln2 = float(np.log(2.0))
+    xs = list(rng.exponential(1.0, 2000))
+    xs += list(np.exp(rng.uniform(np.log(2.0**-26), np.log(ln2), 600)))      # the X binades
+    xs += list(ln2 + rng.uniform(-1 / 64, 1 / 16, 400))                       # through z = 0
+    xs += list(ln2 + rng.uniform(1.0, 63.9, 300))                             # coarse V rows
+    for vv in (-1 / 64, 0.0, 1 / 32, 1 / 16, 0.5, 1.0, 1.125, 8.0, 63.875):  # region and segment ends
+        xs += [ln2 + vv, np.nextafter(ln2 + vv, 0.0), np.nextafter(ln2 + vv, np.inf)]
+    xs = np.array([x for x in xs if x > 0])
+    got = [exp_fixed(V, X, consts, float(x)) for x in xs]
+    keep = np.array([g is not None for g in got])
+    z = np.array([g for g in got if g is not None])
+    w = oracle.recycle_exp(xs[keep])
+    nz = w != 0
+    r = np.abs(z[nz] / w[nz] - 1)
+    print(f"exp -> normal rows, emulated: {int(keep.sum())} inputs, max rel {r.max():.3g}")
+    assert keep.sum() > 0.98 * len(xs)
+    assert r.max() <= 1e-12, xs[keep][nz][np.argmax(r)]
+
+
+def segtx_row(r, Sig: int, mlt: float, estrin: bool = False) -> float:
+    """One unsigned fixed-point row from a uint64[8] array (Horner or Estrin
+    inner chain), as the device evaluates it."""
+    a0b, D0, D1, D2, D3, D4e, c01, c23 = (int(x) for x in r)
+    w = (c01 & 0xFFFFFFFF, c01 >> 32, c23 & 0xFFFFFFFF, c23 >> 32)
+    t = Sig >> 32
+    if estrin:
+        lo = w[0] + ((w[1] * t) >> 32)
+        hi = w[2] + (((w[3] & 0x07FFFFFF) * t) >> 32)
+        x = lo + ((hi * ((t * t) >> 32)) >> 32)
+        assert x < 2**32
+        G = (x * t) >> (w[3] >> 27)
+    else:
+        G = inner(w, t)
+    return _finish((D4e & MANT) + G, (D3, D2, D1, D0), Sig, D4e >> 52, mlt, a0b, bias=False)
+
+
+def _finish(acc, Ds, Sig, e0, mlt, a0b, bias):
+    T16 = Sig >> 4
+    for D in Ds:
+        acc = (D + mulhi3(acc, Sig) - (T16 if bias else 0)) & M64
+        assert 0 <= acc < 2**62
+    assert 2**59 <= acc < 2**61
+    top = acc >> 60
+    pm = (acc + (64 << top)) >> (7 + top)
+    P = dbl(pm + ((e0 + top) << 52))
+    return float(Fr(mlt) * Fr(P) + Fr(dbl(a0b)))
+
+
+def segts_row(r, Sig: int, mlt: float) -> float:
+    """One biased row (coefficients of either sign), as the device evaluates
+    it: accumulators + 2^60 (outer) and + 2^29 / + 2^25 (inner), each step
+    removing the floor of what the bias contributed."""
+    a0b, D0, D1, D2, D3, D4e, c01, c23 = (int(x) for x in r)
+    t = Sig >> 32
+    x = (((((c23 >> 32) & 0x07FFFFFF) * t) >> 32) + (c23 & 0xFFFFFFFF) - (t >> 7)) & 0xFFFFFFFF
+    x = (((x * t) >> 32) + (c01 >> 32) - (t >> 3)) & 0xFFFFFFFF
+    x = (((x * t) >> 32) + (c01 & 0xFFFFFFFF) - (t >> 3)) & 0xFFFFFFFF
+    G = (x * t - (t << 29)) >> (c23 >> 59)                      # signed, arithmetic shift
+    acc = ((D4e & MANT) + (2**60 - 2**51) + G) & M64
+    return _finish(acc, (D3, D2, D1, D0), Sig, D4e >> 52, mlt, a0b, bias=True)
+
+
+def t_fixed(rows, z: float, estrin: bool) -> float:
+    """The normal -> Student t map for |z| < 8.75: segment j = floor(32 |z|)
+    and Sig = (|z| 2^68) mod 2^63 from the bits, sigma = |z| - j/32 exact."""
+    a = abs(z)
+    ab = bits(a)
+    E = (ab >> 52) - 1023
+    M = (ab & MANT) | (1 << 52)
+    j = 0 if E + 5 < 0 else M >> (52 - (E + 5))
+    lj = (j | 1).bit_length() - 1
+    zsb = 0 if j == 0 else ((lj - 5 + 1023) << 52) | ((j << (52 - lj)) & MANT)
+    sig = a - dbl(zsb)
+    sh = E + 16
+    Sig = ((M << sh) & (2**63 - 1)) if sh >= 0 else (M >> -sh if sh > -64 else 0)
+    t = segtx_row(rows[j], Sig, sig, estrin)
+    return t if z >= 0 else -t
+
+
+@pytest.mark.parametrize("nu", [0.75, 4.0, 30.0])
+def test_student_t_rows_against_the_oracle(nu):
+    import paper_0901_0638_gb300 as qm
+    rows = qm.qm_t_rows_build(nu)
+    rng = np.random.default_rng(int(nu * 100))
+    z = np.concatenate([rng.standard_normal(400) * 2.5, rng.uniform(-8.74, 8.74, 200),
+                        np.arange(1, 280) / 32.0, np.arange(1, 280) / 32.0 - 2.0**-40, [1e-300, 2.0**-20, -3e-9]])
+    z = z[np.abs(z) < 8.75]
+    w = oracle.recycle_t(nu, z)
+    for estrin in (False, True):
+        got = np.array([t_fixed(rows, float(x), estrin) for x in z])
+        r = np.abs(got / w - 1)
+        print(f"Student t nu={nu} rows ({'Estrin' if estrin else 'Horner'}): max rel {r.max():.3g}")
+        assert r.max() <= 1e-12, (estrin, z[np.argmax(r)])
+
+
+@pytest.mark.parametrize("abd", [(1.3, 0.4, 0.7), (2.0, -1.5, 0.05)])
+def test_hyperbolic_biased_rows_against_the_oracle(abd):
+    import paper_0901_0638_gb300 as qm
+    from oracle.hyperbolic import Hyperbolic, recycle_hyperbolic
+    a, b, d = abd
+    R, L, e_max = qm.qm_hyp_rows_build(a, b, d)
+    o = Hyperbolic(a, b, d)
+    rng = np.random.default_rng(7)
+    side = rng.random(160) < o.p_plus
+    v = np.where(side, rng.exponential(1 / (a - b), 160), -rng.exponential(1 / (a + b), 160))
+    v = np.concatenate([v, [2.0**-29, -2.0**-29 * 1.5, 1e-6, -1e-3, 0.75, -0.75]])
+    got = []
+    for x in v:
+        ab = bits(abs(float(x)))
+        E = (ab >> 52) - 1023
+        rows = R if x > 0 else L
+        assert qm.QM_HYP_E_MIN <= E <= e_max[0 if x > 0 else 1]
+        low = ab & ((1 << 47) - 1)
+        sig = abs(float(x)) - dbl(ab - low)
+        m = segts_row(rows[32 * (E - qm.QM_HYP_E_MIN) + ((ab >> 47) & 31)], low << 16, sig)
+        got.append(m if x > 0 else -m)
+    w = recycle_hyperbolic(a, b, d, v)
+    r = np.abs(np.array(got) / w - 1)
+    print(f"hyperbolic {abd} biased rows: max rel {r.max():.3g}")
+    assert r.max() <= 1e-12, v[np.argmax(r)]
