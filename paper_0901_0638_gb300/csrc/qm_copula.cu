@@ -73,8 +73,11 @@ static __device__ __noinline__ double tc_log_w_rare(const CopulaDev& c, double z
 __device__ __forceinline__ double tc_log_w(const CopulaDev& c, double z)
 {
     const double u = __dadd_rn(z, QM_TC_Z_MAX);
-    if (!(u >= 0.0 && u < 2.0 * QM_TC_Z_MAX)) return tc_log_w_rare(c, z);
     const uint64_t ub = (uint64_t)__double_as_longlong(u);
+    // 0 <= u < 2 z_max = 17 on the bits (+0 included; -0, negative values and
+    // NaN fail)
+    static_assert(QM_TC_Z_MAX == 8.5, "the bit pattern below is that of 17.0");
+    if (ub >= 0x4031000000000000ull) return tc_log_w_rare(c, z);
     const int Eu = (int)(ub >> 52) - 1023;                           // u < 17: Eu <= 4
     const uint64_t M = (ub & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
     const int q = 48 - Eu;                                            // bits of M below 1/16
