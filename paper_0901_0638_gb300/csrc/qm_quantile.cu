@@ -289,15 +289,20 @@ static int grid_for(K kernel, int block, size_t work_items, int waves = 1)
     return (int)g;
 }
 
+// MINB: single-precision maps 6 blocks of 256 per SM; double-precision maps 4
+// (a 64-register cap: the Student-t map at its compiler's choice of 89
+// registers held 2 blocks, 137 Gs/s, and 175.6 at 4, measured), over 16
+// waves of resident blocks
 template <typename T, class F>
 static qm_status launch_map(const T* in, T* out, size_t n, F f, cudaStream_t s, const char* what)
 {
     constexpr int U = 2, B = 256;
-    constexpr int MINB = sizeof(T) == 4 ? 6 : 1;
+    constexpr int MINB = sizeof(T) == 4 ? 6 : 4;
+    constexpr int WAVES = sizeof(T) == 4 ? 1 : 16;
     const bool aligned = ((uintptr_t)in % 16 == 0) && ((uintptr_t)out % 16 == 0);
     if (aligned) {
         const size_t nv = n / Vec<T>::W;
-        const int g = grid_for(k_map_vec<T, U, F, MINB>, B, (nv + U - 1) / U > 0 ? (nv + U - 1) / U : 1);
+        const int g = grid_for(k_map_vec<T, U, F, MINB>, B, (nv + U - 1) / U > 0 ? (nv + U - 1) / U : 1, WAVES);
         k_map_vec<T, U, F, MINB><<<g, B, 0, s>>>(in, out, n, f);
     } else {
         const int g = grid_for(k_map_scalar<T, F>, B, n);

@@ -5,7 +5,8 @@
 // Layout: every segment is cut into tiles of block x ept elements; a tile
 // never spans two segments, so the target (and nu) is uniform per block.
 // tile0[s] is the prefix sum of the segments' tile counts; a block finds the
-// segment of its tile by binary search over that array.
+// segment of its first tile by binary search over that array and, as its
+// tiles increase, steps forward from there.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -43,12 +44,19 @@ template <int EPT, bool ESTRIN>
 __global__ void __launch_bounds__(512)
 k_batch(const DevSeg* __restrict__ segs, int nseg, unsigned long long ntiles, const fxt::FxTable* fxT)
 {
-    for (unsigned long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        int lo = 0, hi = nseg - 1;
+    // the block's tiles increase, so after a binary search for its first
+    // tile the segment index only moves forward (segments of zero tiles,
+    // equal tile0, are stepped over)
+    int lo = 0;
+    if (blockIdx.x < ntiles) {
+        int hi = nseg - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (segs[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
+            if (segs[mid].tile0 <= blockIdx.x) lo = mid; else hi = mid - 1;
         }
+    }
+    for (unsigned long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        while (lo + 1 < nseg && segs[lo + 1].tile0 <= tile) ++lo;
         const DevSeg sg = segs[lo];
         const size_t base = (size_t)(tile - sg.tile0) * blockDim.x * EPT;
         double x[EPT];
