@@ -2,27 +2,28 @@
 z = Phi^{-1}(1 - e^{-x}) on given Exp(1) samples x (Sec. 2.3, Sec. 6), in the
 fixed-point row form of csrc/qm_t_fx.h (one FP64 FMA per element).
 
-The local expansions are those of gen_exp_tables.py (the exponential-
-background recycling ODE Q'' + Q' = Q Q'^2 composed with each region's
-coordinate).  Each is re-expanded exactly about a point from which |z| has
-non-negative coefficients (asserted here for every row), so the device runs
-one unsigned fixed-point chain for every lane:
+The local expansions come from the exponential-background recycling ODE
+Q'' + Q' = Q Q'^2 (gen_exp_tables.py), each re-expanded exactly about a
+point from which |z| has non-negative coefficients (asserted for every row),
+so the device runs one unsigned fixed-point chain for every lane:
 
-* V rows, x >= ln 2 + 1/32 (v = x - ln 2): segments of width w = 1/32 on
-  v < 1 and 1/8 on 1 <= v < 64, about the segment END v_e, in t = v_e - v:
-      |z| = a0 - t H(t),   H >= 0,   tau = 2^k t (k = 3, or 1 for w = 1/8).
-* V row 0, -1/64 <= v < 1/32 (the central piece, z through 0 at x = ln 2):
+* ROWS[(E - X_EMIN) 2^X_K + j], 2^-26 <= x < 128: segment j (the top X_K
+  bits of the significand m) of the binade x = 2^E m, in the offset
+  t_u = m_end - m back from the segment end (Tu = Tp + 1 integer,
+  t_u = Tu 2^-52, tau = Tp 2^-48 in [0, 1/2)):
+    below the centre segment  |z| = a0 + t_u H,   z = -|z|
+                              (x_seg: Q(-log(2(1 - e^{-x}))));
+    above it                  z = a0 - t_u H      (Q(v), v = x - ln 2,
+                              Q' completely monotone there, so H >= 0).
+* ROW_C, the centre segment [0.6875, 0.703125) that holds ln 2:
       z = v P(t),  t = 1/32 - v,  P(v) = Q(v)/v from the series about v = 0,
-      re-expanded about v = 1/32, tau = 8 t.
-* X rows, 2^-26 <= x < ln 2 - 1/64: binades 2^E <= x < 2^(E+1), 32 segments
-  each, in the offset t_u = m_end - m of the significand m of x back from the
-  segment end (Tu = Tp + 1 integer, t_u = Tu 2^-52):
-      |z| = a0 + t_u H,   tau = Tp 2^-48 in [0, 1/2),   z = -|z|.
+      re-expanded about v = 1/32, tau = 8 t (v_row(0)).
 H (or P) = sum_k d_k tau^k: d_0..d_4 as integers D_k = d_k 2^-s0 (D_0 in
 [2^59, 2^60]), d_5..d_8 as 32-bit integers under a per-row scale (the inner
 chain), e0 = 1081 + s0 (the layout of qm_t_fx.h).  Every row is checked by
 emulating the device's integer steps exactly against mpmath at points of the
-row, and the worst relative error is printed.  Usage:  python -m paper_0901_0638_gb300.fit.gen_exp_fx_tables
+row, and the worst relative error is printed.  Usage:
+python -m paper_0901_0638_gb300.fit.gen_exp_fx_tables
 """
 from __future__ import annotations
 
@@ -34,8 +35,9 @@ from fractions import Fraction as Fr
 
 import mpmath as mp
 
+from . import rode
 from . import targets as T
-from .gen_exp_tables import V_COARSE, V_FINE, V_MAX, V_SPLIT, X_EMIN, X_K, v_seg, x_seg
+from .gen_exp_tables import DEG_V, V_COARSE, V_FINE, V_MAX, V_SPLIT, X_EMIN, X_K, q_and_slope, v_seg, x_seg
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(os.path.dirname(HERE), "csrc", "qm_exp_fx_tables.h")
@@ -197,6 +199,72 @@ def x_row(i):
     return i, a0, D, f, e0, worst
 
 
+X_EMAX = 6                                      # binades 2^X_EMIN .. [64, 128) of x
+NROWS = (X_EMAX - X_EMIN + 1) << X_K
+C_E, C_J = -1, 12                               # the segment [0.6875, 0.703125) holds ln 2
+
+
+def seg_bounds(E, j):
+    lo = mp.mpf(2) ** E * (1 + mp.mpf(j) / 2**X_K)
+    return lo, lo + mp.mpf(2) ** (E - X_K)
+
+
+def seg_kind(E, j):
+    """'neg' below the centre segment (z < 0), 'centre', or 'pos' above it."""
+    clo, chi = seg_bounds(C_E, C_J)
+    lo, hi = seg_bounds(E, j)
+    if (E, j) == (C_E, C_J):
+        return "centre"
+    return "neg" if hi <= clo else "pos"
+
+
+def xp_row(E, j):
+    """A row above the centre: z = a0 - t_u H(t_u) on x = 2^E m, t_u = m_end - m
+    (the offset back from the segment end in the significand, t_u = (Tp + 1)
+    2^-52), H with non-negative coefficients (Q' completely monotone there;
+    asserted by quantise), from the ODE expansion of Q(v), v = x - ln 2, about
+    the segment centre."""
+    mp.mp.dps = 50
+    mlo = 1 + mp.mpf(j) / 2**X_K
+    mhi = mlo + mp.mpf(1) / 2**X_K
+    mc = (mlo + mhi) / 2
+    vc = mp.mpf(2) ** E * mc - LN2
+    q0, q1 = q_and_slope(vc)
+    b = rode.taylor_exp_background(vc, q0, q1, DEG_V + 1)[:DEG_V + 1]   # z in s = v - vc
+    bs = [b[k] * mp.mpf(2) ** (E * k) for k in range(len(b))]          # in m - mc
+    g = reexpand(bs, mhi - mc, -1)                                      # z(m_end - t_u)
+    a0 = float(g[0])
+    H = [-g[m + 1] for m in range(len(g) - 1)]
+    Ht = reexpand(H, mp.mpf(2) ** -52, 1)                               # t_u = 2^-52 + tau / 16
+    d = [Ht[m] / mp.mpf(16) ** m for m in range(len(Ht))]
+    D, f, s0, e0 = quantise(d, mp.mpf("0.5"), ("XP", E, j))
+    worst = 0.0
+    for Tp in (0, 1, 2**23, 2**46, 2**47 - 1):
+        m = mhi - mp.mpf(Tp + 1) * mp.mpf(2) ** -52
+        x = float(m * mp.mpf(2) ** E)
+        tu = float(mp.mpf(Tp + 1) * mp.mpf(2) ** -52)
+        z = emulate(a0, D, f, s0, Tp << 16, -tu)
+        ref = T.q_exp(mp.mpf(x) - LN2)
+        worst = max(worst, float(abs(mp.mpf(z) / ref - 1)))
+    return a0, D, f, e0, worst
+
+
+def xn_row(E, j):
+    """A row below the centre: |z| = a0 + t_u H (the X rows of x_seg)."""
+    i = (-1 - E) * (1 << X_K) + j
+    _, a0, D, f, e0, worst = x_row(i)
+    return a0, D, f, e0, worst
+
+
+def unified_row(ij):
+    E, j = ij
+    kind = seg_kind(E, j)
+    if kind == "centre":
+        return E, j, kind, 0.0, [2**59, 0, 0, 0, 0], [0, 0, 0, 0], 1, 0.0   # not used: ROW_C serves it
+    a0, D, f, e0, worst = (xp_row if kind == "pos" else xn_row)(E, j)
+    return E, j, kind, a0, D, f, e0, worst
+
+
 def row_literal(a0, D, f, e0):
     d4e = D[4] | (e0 << 52)
     return ("  {" + float(a0).hex() + "," + ",".join(f"{x}ull" for x in D[:4]) + f",{d4e}ull,{{" +
@@ -204,30 +272,38 @@ def row_literal(a0, D, f, e0):
 
 
 def main():
+    cells = [(E, j) for E in range(X_EMIN, X_EMAX + 1) for j in range(1 << X_K)]
     with mproc.Pool(max(1, os.cpu_count() or 2)) as pool:
-        vs = pool.map(v_row, range(NV), chunksize=4)
-        xs = pool.map(x_row, range(NX), chunksize=4)
-    wv = max(r[5] for r in vs)
-    wx = max(r[5] for r in xs)
-    print(f"exp -> normal fixed-point rows: V {NV} (worst {wv:.3g}), X {NX} (worst {wx:.3g})", file=sys.stderr)
+        rows = pool.map(unified_row, cells, chunksize=4)
+        centre = v_row(0)
+    clo, chi = seg_bounds(C_E, C_J)
+    assert clo < LN2 < chi and -mp.mpf(1) / 64 <= clo - LN2 and chi - LN2 <= mp.mpf(1) / 32
+    wn = max(r[7] for r in rows if r[2] == "neg")
+    wp = max(r[7] for r in rows if r[2] == "pos")
+    wc = centre[5]
+    print(f"exp -> normal fixed-point rows: {NROWS} binade rows (worst below ln 2 {wn:.3g}, above {wp:.3g}), "
+          f"centre row (worst {wc:.3g})", file=sys.stderr)
     L = [
         "// Generated by paper_0901_0638_gb300/fit/gen_exp_fx_tables.py -- do not edit.\n",
         "// Exponential -> normal recycling map z = Phi^{-1}(1 - e^{-x}) in the fixed-point\n",
-        "// row form of qm_t_fx.h: V rows (x >= ln 2 - 1/64, in v = x - ln 2) and X rows\n",
-        "// (2^-26 <= x < ln 2 - 1/64, binades of x, 32 segments each); see the generator.\n",
-        f"// Emulated worst relative error: V {wv:.3g}, X {wx:.3g}.\n",
+        "// row form of qm_t_fx.h: ROWS[(E - X_EMIN) 2^X_K + j] for segment j of the binade\n",
+        "// [2^E, 2^(E+1)) of x, in the offset t_u back from the segment end (below the\n",
+        "// centre segment |z| = a0 + t_u H, z < 0; above it z = a0 - t_u H), and ROW_C for\n",
+        "// the centre segment [0.6875, 0.703125), which holds ln 2 (z = v P(tau), v = x - ln 2,\n",
+        "// tau = 8 (1/32 - v)); see the generator.\n",
+        f"// Emulated worst relative error: below ln 2 {wn:.3g}, above {wp:.3g}, centre {wc:.3g}.\n",
         "#pragma once\n#include \"qm_t_fx.h\"\n\nnamespace qm {\nnamespace efx {\n\n",
-        f"constexpr int V_FINE = {V_FINE};\nconstexpr int V_COARSE = {V_COARSE};\n",
-        f"constexpr int V_MAX = {V_MAX};\nconstexpr int NV = {NV};\n",
-        f"constexpr int X_K = {X_K};\nconstexpr int X_EMIN = {X_EMIN};\nconstexpr int NX = {NX};\n\n",
-        "__device__ const ttbl::SegTX ROWS_V[NV] = {\n",
+        f"constexpr int X_K = {X_K};\nconstexpr int X_EMIN = {X_EMIN};\nconstexpr int X_EMAX = {X_EMAX};\n",
+        f"constexpr int NROWS = {NROWS};\n",
+        "constexpr unsigned long long C_LO_BITS = 0x3FE6000000000000ull;   // 0.6875\n",
+        "constexpr unsigned long long C_HI_BITS = 0x3FE6800000000000ull;   // 0.703125\n\n",
+        "__device__ const ttbl::SegTX ROWS[NROWS] = {\n",
     ]
-    for _, a0, D, f, e0, _ in vs:
+    for _, _, _, a0, D, f, e0, _ in rows:
         L.append(row_literal(a0, D, f, e0))
-    L.append("};\n\n__device__ const ttbl::SegTX ROWS_X[NX] = {\n")
-    for _, a0, D, f, e0, _ in xs:
-        L.append(row_literal(a0, D, f, e0))
-    L.append("};\n\n}  // namespace efx\n}  // namespace qm\n")
+    _, a0, D, f, e0, _ = centre
+    L.append("};\n\n__device__ const ttbl::SegTX ROW_C = \n" + row_literal(a0, D, f, e0).rstrip(",\n") + ";\n")
+    L.append("\n}  // namespace efx\n}  // namespace qm\n")
     with open(OUT, "w") as fh:
         fh.write("".join(L))
     print("wrote", OUT, file=sys.stderr)

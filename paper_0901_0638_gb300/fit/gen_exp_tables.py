@@ -9,7 +9,9 @@ region:
 
 * x >= ln 2 (v_seg): z = Q(v), v = x - ln 2.  Segments of width 1/32 on
   v in [0, 1) (segment 0 expanded at v = 0, where Q(0) = 0) and 1/8 on
-  [1, 64); local variable s = v - v_c.
+  [1, 64); local variable s = v - v_c.  The device rows use segment 0 (the
+  centre row); above it they take q_and_slope and the ODE series directly
+  at the centres of binade segments of x (gen_exp_fx_tables.xp_row).
 * 2^-26 <= x <= ln 2 - 1/64 (x_seg): z = -F(r), x = 2^E m, segment j =
   top 5 bits of m, r = m c_j - 1, F(r) = Q(g_x(x)), g_x(x) = -log(2(1 - e^{-x})).
 * y_series: the expansion at x = ln 2 in y = ln 2 - x (no longer used on the

@@ -145,22 +145,21 @@ def test_fixed_table_rows_against_the_oracle(fx_table):
 
 @pytest.fixture(scope="module")
 def exp_rows():
-    """ROWS_V, ROWS_X: (a0 bits, D0, D1, D2, D3, D4 | e0, (four 32-bit words))."""
+    """ROWS (binade rows) and ROW_C (the centre row): (a0 bits, D0, D1, D2, D3,
+    D4 | e0, (four 32-bit words))."""
     text = open(os.path.join(CSRC, "qm_exp_fx_tables.h")).read()
     consts = {k: int(v) for k, v in re.findall(r"constexpr int (\w+) = (-?\d+);", text)}
+    pat = r"\{([^{},]+),(\d+)ull,(\d+)ull,(\d+)ull,(\d+)ull,(\d+)ull,\{([^}]*)\}\}"
 
-    def rows(name):
-        body = text[text.index(name + "["):]
-        body = body[:body.index("};")]
-        out = []
-        for m in re.finditer(r"\{([^{},]+),(\d+)ull,(\d+)ull,(\d+)ull,(\d+)ull,(\d+)ull,\{([^}]*)\}\}", body):
-            w = tuple(int(x.strip().rstrip("u"), 16) if x.strip() != "0" else 0 for x in m.group(7).split(","))
-            out.append((bits(float.fromhex(m.group(1))),) + tuple(int(m.group(k)) for k in range(2, 7)) + (w,))
-        return out
+    def row(m):
+        w = tuple(int(x.strip().rstrip("u"), 16) if x.strip() != "0" else 0 for x in m.group(7).split(","))
+        return (bits(float.fromhex(m.group(1))),) + tuple(int(m.group(k)) for k in range(2, 7)) + (w,)
 
-    V, X = rows("ROWS_V"), rows("ROWS_X")
-    assert len(V) == consts["NV"] and len(X) == consts["NX"]
-    return V, X, consts
+    body = text[text.index("ROWS[NROWS] ="):text.index("ROW_C =")]
+    rows = [row(m) for m in re.finditer(pat, body)]
+    centre = row(re.search(pat, text[text.index("ROW_C ="):]))
+    assert len(rows) == consts["NROWS"] == (consts["X_EMAX"] - consts["X_EMIN"] + 1) << consts["X_K"]
+    return rows, centre, consts
 
 
 def segtx(row, Sig: int, mlt: float) -> float:
@@ -177,52 +176,43 @@ def segtx(row, Sig: int, mlt: float) -> float:
     return float(Fr(mlt) * Fr(P) + Fr(dbl(a0b)))
 
 
-def exp_fixed(V, X, consts, x: float):
-    """The exponential -> normal kernel's branch-free path (None where the
-    kernel takes its out-of-line path: x < 2^-26, v >= 64, edge values)."""
+def exp_fixed(rows, centre, consts, x: float):
+    """The exponential -> normal kernel (None where it goes out of line:
+    x < 2^-26, x >= 128, edge values): segment j of the binade of x, the
+    offset t_u back from its end from the bits; the centre segment
+    [0.6875, 0.703125) in v = x - ln 2."""
     xb = bits(x)
-    if xb == 0 or xb >= 0x7FF0000000000000:
+    if xb == 0 or xb >= 0x7FF0000000000000 or xb < 0x3E50000000000000 or xb >= 0x4060000000000000:
         return None
-    v = (x - 0.69314718055994528623) - 2.3190468138462996154e-17
-    vside = v >= -0.015625
-    if (not (v < 64.0)) if vside else (xb < 0x3E50000000000000):
-        return None
-    if vside:
-        vb = bits(v)
-        Ev = ((vb >> 52) & 0x7FF) - 1023
-        Mv = (vb & MANT) | (1 << 52)
-        fine, row0 = v < 1.0, v < 0.03125
-        shv = min(max(47 - Ev if fine else 49 - Ev, 0), 63)
-        q = (Mv >> shv) & 0xFFFFFFFF
-        rv = 0 if row0 else min(q if fine else consts["V_FINE"] + q - consts["V_COARSE"], consts["NV"] - 1)
-        nq = 1 if row0 else (q + 1) & 0xFFFF
-        ln = (nq | 1).bit_length() - 1
-        veb = ((ln - (5 if fine else 3) + 1023) << 52) | ((nq << (52 - ln)) & MANT)
-        t = dbl(veb) - v
+    if 0.6875 <= x < 0.703125:
+        v = (x - 0.69314718055994528623) - 2.3190468138462996154e-17
+        t = 0.03125 - v
         tb = bits(t)
         Mt = (tb & MANT) | (1 << 52)
-        st = ((tb >> 52) & 0x7FF) - 1023 + 12 + (3 if fine else 1)
-        Sig = 0 if tb == 0 else (((Mt << min(st, 63)) & (2**63 - 1)) if st >= 0 else (Mt >> -st if st > -64 else 0))
-        return segtx(V[rv], Sig, v if row0 else -t)
-    Ex = (xb >> 52) - 1023
-    rx = (min(max(-1 - Ex, 0), (consts["NX"] >> consts["X_K"]) - 1) << consts["X_K"]) + ((xb >> 47) & 31)
+        st = ((tb >> 52) & 0x7FF) - 1023 + 15
+        Sig = ((Mt << min(st, 63)) & (2**63 - 1)) if st >= 0 else (Mt >> -st if st > -64 else 0)
+        return segtx(centre, Sig, v)
+    E = (xb >> 52) - 1023
+    r = ((E - consts["X_EMIN"]) << consts["X_K"]) + ((xb >> 47) & 31)
     Tp = ~xb & ((1 << 47) - 1)
     tu = dbl(0x3FF0000000000001 + Tp) - 1.0
-    return -segtx(X[rx], Tp << 16, tu)
+    above = x >= 0.703125
+    z = segtx(rows[r], Tp << 16, -tu if above else tu)
+    return z if above else -z
 
 
 def test_exp_to_normal_rows_against_the_oracle(exp_rows):
-    V, X, consts = exp_rows
+    rows, centre, consts = exp_rows
     rng = np.random.default_rng(2027)
     ln2 = float(np.log(2.0))
     xs = list(rng.exponential(1.0, 2000))
     xs += list(np.exp(rng.uniform(np.log(2.0**-26), np.log(ln2), 600)))      # the X binades
     xs += list(ln2 + rng.uniform(-1 / 64, 1 / 16, 400))                       # through z = 0
-    xs += list(ln2 + rng.uniform(1.0, 63.9, 300))                             # coarse V rows
-    for vv in (-1 / 64, 0.0, 1 / 32, 1 / 16, 0.5, 1.0, 1.125, 8.0, 63.875):  # region and segment ends
-        xs += [ln2 + vv, np.nextafter(ln2 + vv, 0.0), np.nextafter(ln2 + vv, np.inf)]
+    xs += list(np.exp(rng.uniform(0.0, np.log(127.9), 400)))                 # binades up to [64, 128)
+    for x0 in (0.6875, 0.703125, ln2, 0.71875, 1.0, 2.0, 8.0, 64.0, 100.0):   # the centre and binade ends
+        xs += [x0, np.nextafter(x0, 0.0), np.nextafter(x0, np.inf)]
     xs = np.array([x for x in xs if x > 0])
-    got = [exp_fixed(V, X, consts, float(x)) for x in xs]
+    got = [exp_fixed(rows, centre, consts, float(x)) for x in xs]
     keep = np.array([g is not None for g in got])
     z = np.array([g for g in got if g is not None])
     w = oracle.recycle_exp(xs[keep])
