@@ -9,10 +9,11 @@
 // formed exactly by one FP64 add:
 //   below the centre segment:  z = -(a0 + t_u P(tau)),
 //   above it:                  z = a0 - t_u P(tau),   tau = Tp 2^-48.
-// The centre segment [0.6875, 0.703125), which holds ln 2 where z passes
-// through 0, keeps relative accuracy in v = x - ln 2 (ln 2 split hi/lo):
-// z = v P(tau), tau = 8 (1/32 - v), one row of its own, taken by a branch
-// (0.8 % of Exp(1) samples).  Out of line, rarely taken: x < 2^-26 (u = x -
+// The segment [0.6875, 0.703125) holds ln 2, where z passes through 0: its
+// row reads z = a0 - t_u P across it, and |x - ln 2| < 2^-12 keeps relative
+// accuracy in v = x - ln 2 (ln 2 split hi/lo): z = v P(tau),
+// tau = 8 (1/32 - v), one row of its own, taken by a branch (about 1 in 4000
+// Exp(1) samples).  Out of line, rarely taken: x < 2^-26 (u = x -
 // x^2/2 through the normal table), x >= 128 (the deep-tail rational in v),
 // and the edge values.
 // Include in the translation units that use it (tables are per unit).
@@ -59,16 +60,17 @@ __device__ __forceinline__ double exp_to_normal_fx(double x)
     const uint64_t xb = (uint64_t)__double_as_longlong(x);
     if (xb == 0 || xb >= 0x7ff0000000000000ull) return exp_to_normal_edge(x);
     if (xb < 0x3E50000000000000ull || xb >= 0x4060000000000000ull) return exp_to_normal_rare(x);   // 2^-26, 128
-    // every lane runs the binade path (the centre segment's slot holds a
-    // placeholder row, finite and unused), then the centre lanes take theirs:
-    // the straight-line part keeps the elements of a thread interleaved
+    // every lane runs the binade path, then the lanes with |x - ln 2| < 2^-12
+    // (about 1 in 4000 Exp(1) samples) take the centre row: z = a0 - t_u H
+    // passes through 0 in the segment of ln 2, and away from it the
+    // cancellation costs under 2e-14 relative
     const int row = (((int)(xb >> 52) - 1023 - efx::X_EMIN) << efx::X_K) + (int)((xb >> 47) & 31u);
     const uint64_t Tp = ~xb & ((1ull << 47) - 1ull);
     const double tu = __dadd_rn(__longlong_as_double((long long)(0x3FF0000000000001ull + Tp)), -1.0);
-    const bool above = xb >= efx::C_HI_BITS;
-    double r = segtx_eval<false>(efx::ROWS + row, Tp << 16, above ? -tu : tu);
-    r = above ? r : -r;
-    if (xb - efx::C_LO_BITS < efx::C_HI_BITS - efx::C_LO_BITS) r = exp_to_normal_centre(x);
+    const bool pos = xb >= efx::POS_BITS;
+    double r = segtx_eval<false>(efx::ROWS + row, Tp << 16, pos ? -tu : tu);
+    r = pos ? r : -r;
+    if (xb - efx::NEAR_LO_BITS < efx::NEAR_HI_BITS - efx::NEAR_LO_BITS) r = exp_to_normal_centre(x);
     return r;
 }
 

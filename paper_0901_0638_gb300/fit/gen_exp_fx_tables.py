@@ -30,6 +30,7 @@ from __future__ import annotations
 import math
 import multiprocessing as mproc
 import os
+import struct
 import sys
 from fractions import Fraction as Fr
 
@@ -43,7 +44,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(os.path.dirname(HERE), "csrc", "qm_exp_fx_tables.h")
 NV = V_FINE * V_SPLIT + V_COARSE * (V_MAX - V_SPLIT)
 NX = (-X_EMIN) << X_K
-LN2 = mp.log(2)
+with mp.workdps(60):
+    LN2 = +mp.log(2)                  # kept at 60 digits (module import runs at mpmath's default 15)
 
 
 def reexpand(c, h, sign=1):
@@ -209,12 +211,15 @@ def seg_bounds(E, j):
     return lo, lo + mp.mpf(2) ** (E - X_K)
 
 
+V_NEAR = mp.mpf(2) ** -12                      # |v| < V_NEAR: the centre row (z = v P)
+
+
 def seg_kind(E, j):
-    """'neg' below the centre segment (z < 0), 'centre', or 'pos' above it."""
+    """'neg' below the segment that holds ln 2 (z < 0, |z| = a0 + t_u H), else
+    'pos' (z = a0 - t_u H; through z = 0 in the segment of ln 2, where
+    |v| >= V_NEAR keeps the cancellation below 2e-14 relative)."""
     clo, chi = seg_bounds(C_E, C_J)
     lo, hi = seg_bounds(E, j)
-    if (E, j) == (C_E, C_J):
-        return "centre"
     return "neg" if hi <= clo else "pos"
 
 
@@ -239,12 +244,17 @@ def xp_row(E, j):
     d = [Ht[m] / mp.mpf(16) ** m for m in range(len(Ht))]
     D, f, s0, e0 = quantise(d, mp.mpf("0.5"), ("XP", E, j))
     worst = 0.0
-    for Tp in (0, 1, 2**23, 2**46, 2**47 - 1):
+    pts = [0, 1, 2**23, 2**46, 2**47 - 1]
+    if (E, j) == (C_E, C_J):                    # both sides of |v| = V_NEAR, where this row takes over
+        for vv in (V_NEAR, -V_NEAR, 2 * V_NEAR, -2 * V_NEAR, mp.mpf(2) ** -8, -mp.mpf(2) ** -8):
+            pts.append(int((mhi - (LN2 + vv) / mp.mpf(2) ** E) * mp.mpf(2) ** 52) - 1)
+    for Tp in pts:
         m = mhi - mp.mpf(Tp + 1) * mp.mpf(2) ** -52
         x = float(m * mp.mpf(2) ** E)
         tu = float(mp.mpf(Tp + 1) * mp.mpf(2) ** -52)
         z = emulate(a0, D, f, s0, Tp << 16, -tu)
-        ref = T.q_exp(mp.mpf(x) - LN2)
+        v = mp.mpf(x) - LN2
+        ref = T.q_exp(v) if v >= 0 else -T.q_exp(-mp.log(2 - mp.exp(-v)))
         worst = max(worst, float(abs(mp.mpf(z) / ref - 1)))
     return a0, D, f, e0, worst
 
@@ -259,8 +269,6 @@ def xn_row(E, j):
 def unified_row(ij):
     E, j = ij
     kind = seg_kind(E, j)
-    if kind == "centre":
-        return E, j, kind, 0.0, [2**59, 0, 0, 0, 0], [0, 0, 0, 0], 1, 0.0   # not used: ROW_C serves it
     a0, D, f, e0, worst = (xp_row if kind == "pos" else xn_row)(E, j)
     return E, j, kind, a0, D, f, e0, worst
 
@@ -277,10 +285,12 @@ def main():
         rows = pool.map(unified_row, cells, chunksize=4)
         centre = v_row(0)
     clo, chi = seg_bounds(C_E, C_J)
-    assert clo < LN2 < chi and -mp.mpf(1) / 64 <= clo - LN2 and chi - LN2 <= mp.mpf(1) / 32
+    assert clo < LN2 - V_NEAR and LN2 + V_NEAR < chi            # the centre row inside that segment
+    near_lo, near_hi = float(LN2 - V_NEAR), float(LN2 + V_NEAR)   # ROW_C serves [near_lo, near_hi)
+    bits = lambda x: struct.unpack("<Q", struct.pack("<d", x))[0]
     wn = max(r[7] for r in rows if r[2] == "neg")
     wp = max(r[7] for r in rows if r[2] == "pos")
-    wc = centre[5]
+    wc = centre[5]                          # over v in [-1/64, 1/32), wider than it serves
     print(f"exp -> normal fixed-point rows: {NROWS} binade rows (worst below ln 2 {wn:.3g}, above {wp:.3g}), "
           f"centre row (worst {wc:.3g})", file=sys.stderr)
     L = [
@@ -288,15 +298,16 @@ def main():
         "// Exponential -> normal recycling map z = Phi^{-1}(1 - e^{-x}) in the fixed-point\n",
         "// row form of qm_t_fx.h: ROWS[(E - X_EMIN) 2^X_K + j] for segment j of the binade\n",
         "// [2^E, 2^(E+1)) of x, in the offset t_u back from the segment end (below the\n",
-        "// centre segment |z| = a0 + t_u H, z < 0; above it z = a0 - t_u H), and ROW_C for\n",
-        "// the centre segment [0.6875, 0.703125), which holds ln 2 (z = v P(tau), v = x - ln 2,\n",
+        "// segment [0.6875, 0.703125) that holds ln 2, |z| = a0 + t_u H, z < 0; from it on\n",
+        "// z = a0 - t_u H), and ROW_C for |x - ln 2| < 2^-12 (z = v P(tau), v = x - ln 2,\n",
         "// tau = 8 (1/32 - v)); see the generator.\n",
         f"// Emulated worst relative error: below ln 2 {wn:.3g}, above {wp:.3g}, centre {wc:.3g}.\n",
         "#pragma once\n#include \"qm_t_fx.h\"\n\nnamespace qm {\nnamespace efx {\n\n",
         f"constexpr int X_K = {X_K};\nconstexpr int X_EMIN = {X_EMIN};\nconstexpr int X_EMAX = {X_EMAX};\n",
         f"constexpr int NROWS = {NROWS};\n",
-        "constexpr unsigned long long C_LO_BITS = 0x3FE6000000000000ull;   // 0.6875\n",
-        "constexpr unsigned long long C_HI_BITS = 0x3FE6800000000000ull;   // 0.703125\n\n",
+        "constexpr unsigned long long POS_BITS = 0x3FE6000000000000ull;    // 0.6875: z = a0 - t_u H from here\n",
+        f"constexpr unsigned long long NEAR_LO_BITS = {bits(near_lo):#x}ull;   // ln 2 - 2^-12\n",
+        f"constexpr unsigned long long NEAR_HI_BITS = {bits(near_hi):#x}ull;   // ln 2 + 2^-12\n\n",
         "__device__ const ttbl::SegTX ROWS[NROWS] = {\n",
     ]
     for _, _, _, a0, D, f, e0, _ in rows:

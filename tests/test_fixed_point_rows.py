@@ -149,6 +149,8 @@ def exp_rows():
     D4 | e0, (four 32-bit words))."""
     text = open(os.path.join(CSRC, "qm_exp_fx_tables.h")).read()
     consts = {k: int(v) for k, v in re.findall(r"constexpr int (\w+) = (-?\d+);", text)}
+    for k in ("NEAR_LO", "NEAR_HI"):
+        consts[k] = int(re.search(k + r"_BITS = (0x[0-9a-fA-F]+)ull", text).group(1), 16)
     pat = r"\{([^{},]+),(\d+)ull,(\d+)ull,(\d+)ull,(\d+)ull,(\d+)ull,\{([^}]*)\}\}"
 
     def row(m):
@@ -179,12 +181,12 @@ def segtx(row, Sig: int, mlt: float) -> float:
 def exp_fixed(rows, centre, consts, x: float):
     """The exponential -> normal kernel (None where it goes out of line:
     x < 2^-26, x >= 128, edge values): segment j of the binade of x, the
-    offset t_u back from its end from the bits; the centre segment
-    [0.6875, 0.703125) in v = x - ln 2."""
+    offset t_u back from its end from the bits, z = -(a0 + t_u P) below
+    0.6875 and a0 - t_u P from there; |x - ln 2| < 2^-12 in v = x - ln 2."""
     xb = bits(x)
     if xb == 0 or xb >= 0x7FF0000000000000 or xb < 0x3E50000000000000 or xb >= 0x4060000000000000:
         return None
-    if 0.6875 <= x < 0.703125:
+    if consts["NEAR_LO"] <= xb < consts["NEAR_HI"]:
         v = (x - 0.69314718055994528623) - 2.3190468138462996154e-17
         t = 0.03125 - v
         tb = bits(t)
@@ -196,9 +198,9 @@ def exp_fixed(rows, centre, consts, x: float):
     r = ((E - consts["X_EMIN"]) << consts["X_K"]) + ((xb >> 47) & 31)
     Tp = ~xb & ((1 << 47) - 1)
     tu = dbl(0x3FF0000000000001 + Tp) - 1.0
-    above = x >= 0.703125
-    z = segtx(rows[r], Tp << 16, -tu if above else tu)
-    return z if above else -z
+    pos = x >= 0.6875
+    z = segtx(rows[r], Tp << 16, -tu if pos else tu)
+    return z if pos else -z
 
 
 def test_exp_to_normal_rows_against_the_oracle(exp_rows):
@@ -209,7 +211,8 @@ def test_exp_to_normal_rows_against_the_oracle(exp_rows):
     xs += list(np.exp(rng.uniform(np.log(2.0**-26), np.log(ln2), 600)))      # the X binades
     xs += list(ln2 + rng.uniform(-1 / 64, 1 / 16, 400))                       # through z = 0
     xs += list(np.exp(rng.uniform(0.0, np.log(127.9), 400)))                 # binades up to [64, 128)
-    for x0 in (0.6875, 0.703125, ln2, 0.71875, 1.0, 2.0, 8.0, 64.0, 100.0):   # the centre and binade ends
+    for x0 in (0.6875, 0.703125, ln2, ln2 - 2.0**-12, ln2 + 2.0**-12, ln2 - 2.0**-11, ln2 + 2.0**-11,
+               0.71875, 1.0, 2.0, 8.0, 64.0, 100.0):                          # the centre and binade ends
         xs += [x0, np.nextafter(x0, 0.0), np.nextafter(x0, np.inf)]
     xs = np.array([x for x in xs if x > 0])
     got = [exp_fixed(rows, centre, consts, float(x)) for x in xs]
