@@ -795,6 +795,21 @@ def main():
             torch.cuda.synchronize(dev)
             return ev_a.elapsed_time(ev_b) / k2
 
+        # the host link's own copy rate on the same buffers: copy engines
+        # moving the 2^28 inputs host -> device and 2^28 results device ->
+        # host at the same time (two streams); no library call
+        def link_step():
+            cur = torch.cuda.current_stream(dev)
+            for st in streams[:2]:
+                st.wait_stream(cur)
+            with torch.cuda.stream(streams[0]):
+                u.copy_(hu, non_blocking=True)
+            with torch.cuda.stream(streams[1]):
+                hz.copy_(z, non_blocking=True)
+            for st in streams[:2]:
+                cur.wait_stream(st)
+
+        t_link = time_host(link_step)
         t_pipe = time_host(pipe_step)
         hz.zero_()
         t = time_host(e2e_step)
@@ -809,7 +824,14 @@ def main():
                "gpu_launches_per_step": 1,
                "copy_engine_pipeline": {"ms_per_step": t_pipe, "value": n / (t_pipe * 1e-3) / 1e9,
                                         "note": "2^24-element chunks over four streams: copy in, "
-                                                "kernel, copy out"}}
+                                                "kernel, copy out"},
+               "link_roofline": {"bound": "host link", "unit": "GB/s",
+                                 "achieved": 16 * n / (t * 1e-3) / 1e9,
+                                 "peak": 16 * n / (t_link * 1e-3) / 1e9,
+                                 "frac": t_link / t,
+                                 "peak_source": "measured in this run: copy engines moving the step's "
+                                                "inputs in and results out concurrently on the same "
+                                                "pinned buffers"}}
         del hu, hz
         cpu = cpu_oracle_leg(n)
         if not args.no_legs:
