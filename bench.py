@@ -809,8 +809,8 @@ def main():
             for st in streams[:2]:
                 cur.wait_stream(st)
 
-        t_link = time_host(link_step)
         t_pipe = time_host(pipe_step)
+        t_link = time_host(link_step)
         hz.zero_()
         t = time_host(e2e_step)
         idx = torch.arange(0, n, 4099)
