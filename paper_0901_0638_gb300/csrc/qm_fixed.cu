@@ -79,9 +79,9 @@ qm_status launch_f64_fixed(const double* u, double* z, size_t n, void* stream)
     cudaStream_t s = (cudaStream_t)stream;
     if ((uintptr_t)u % 16 == 0 && (uintptr_t)z % 16 == 0) {
         // one double2 per thread per pass over a grid of up to 64 x the
-        // resident blocks (measured: 1, 4, 16, 64 waves give 155.6, 171.1,
-        // 174.8, 175.8 Gs/s on the tail-stress mixture; late blocks fill
-        // the tail of an issue-bound kernel)
+        // resident blocks (measured on the tail-stress mixture: 1, 4, 16, 64
+        // waves give 188.0, 220.9, 229.7, 230.8 Gs/s; a plain device copy
+        // also gains from more waves, 6494 -> 7061 GB/s)
         const int g = grid_of(k_f64_fixed<1>, n / 2, 64);
         k_f64_fixed<1><<<g, kBlock, 0, s>>>(u, z, n);
     } else {
