@@ -1,21 +1,23 @@
 // qm_exp_map.cuh -- the exponential -> normal recycling map
 // z = Phi^{-1}(1 - e^{-x}) (Sec. 2.3, Sec. 6) on given samples x, in the
-// fixed-point row form of qm_t_fx.h (rows: qm_exp_fx_tables.h, generated by
-// fit/gen_exp_fx_tables.py from the recycling-ODE expansions).
+// fixed-point row layout of the FIXED normal quantile (qm_fx.cuh; rows:
+// qm_exp_fx_tables.h, generated by fit/gen_exp_fx_tables.py from the
+// recycling-ODE expansions).
 //
-// Every 2^-26 <= x < 128 takes segment j (top 5 bits of the significand) of
+// Every 2^-26 <= x < 128 takes segment j (top 6 bits of the significand) of
 // its binade, with the offset t_u back from the segment end read from the
-// bits (t_u = (Tp + 1) 2^-52, Tp = the complement of the low 47 bits) and
-// formed exactly by one FP64 add:
-//   below the centre segment:  z = -(a0 + t_u P(tau)),
-//   above it:                  z = a0 - t_u P(tau),   tau = Tp 2^-48.
-// The segment [0.6875, 0.703125) holds ln 2, where z passes through 0: its
-// row reads z = a0 - t_u P across it, and |x - ln 2| < 2^-12 keeps relative
+// bits (t_u = (Tp + 1) 2^-52, Tp = the complement of the low 46 bits), the
+// same two 64-bit Horner steps and 32-bit inner chain as the FIXED kernel,
+// and one FP64 FMA:
+//   below the segment that holds ln 2:  z = -(a0 + t_u H),
+//   from it on:                         z = a0 - t_u H.
+// The segment [0.6875, 0.6953125) holds ln 2, where z passes through 0: its
+// row reads z = a0 - t_u H across it, and |x - ln 2| < 2^-12 keeps relative
 // accuracy in v = x - ln 2 (ln 2 split hi/lo): z = v P(tau),
-// tau = 8 (1/32 - v), one row of its own, taken by a branch (about 1 in 4000
-// Exp(1) samples).  Out of line, rarely taken: x < 2^-26 (u = x -
-// x^2/2 through the normal table), x >= 128 (the deep-tail rational in v),
-// and the edge values.
+// tau = 8 (1/32 - v), one row of its own (the row form of qm_t_fx.h), taken
+// by a branch (about 1 in 4000 Exp(1) samples).  Out of line, rarely taken:
+// x < 2^-26 (u = x - x^2/2 through the normal table), x >= 128 (the
+// deep-tail rational in v), and the edge values.
 // Include in the translation units that use it (tables are per unit).
 #pragma once
 
@@ -55,21 +57,23 @@ __device__ __forceinline__ double exp_to_normal_centre(double x)
     return segtx_eval<false>(&efx::ROW_C, Sig, v);
 }
 
+template <int MIX = FX_INT_LEAN>
 __device__ __forceinline__ double exp_to_normal_fx(double x)
 {
+    static_assert(efx::X_K == fxt::K, "the rows share the FIXED layout");
+    constexpr int K = efx::X_K;
     const uint64_t xb = (uint64_t)__double_as_longlong(x);
     if (xb == 0 || xb >= 0x7ff0000000000000ull) return exp_to_normal_edge(x);
     if (xb < 0x3E50000000000000ull || xb >= 0x4060000000000000ull) return exp_to_normal_rare(x);   // 2^-26, 128
     // every lane runs the binade path, then the lanes with |x - ln 2| < 2^-12
     // (about 1 in 4000 Exp(1) samples) take the centre row: z = a0 - t_u H
     // passes through 0 in the segment of ln 2, and away from it the
-    // cancellation costs under 2e-14 relative
-    const int row = (((int)(xb >> 52) - 1023 - efx::X_EMIN) << efx::X_K) + (int)((xb >> 47) & 31u);
-    const uint64_t Tp = ~xb & ((1ull << 47) - 1ull);
-    const double tu = __dadd_rn(__longlong_as_double((long long)(0x3FF0000000000001ull + Tp)), -1.0);
+    // cancellation costs under 2e-15 relative
+    const int row = (((int)(xb >> 52) - 1023 - efx::X_EMIN) << K) + (int)((xb >> (52 - K)) & ((1u << K) - 1u));
+    const uint64_t Tp = ~xb & ((1ull << (52 - K)) - 1ull);
     const bool pos = xb >= efx::POS_BITS;
-    double r = segtx_eval<false>(efx::ROWS + row, Tp << 16, pos ? -tu : tu);
-    r = pos ? r : -r;
+    double r = fx_row_fma<MIX>(efx::ROWS + row, efx::ROWS_IN + row, Tp, pos);
+    r = __longlong_as_double(__double_as_longlong(r) ^ (long long)((unsigned long long)!pos << 63));
     if (xb - efx::NEAR_LO_BITS < efx::NEAR_HI_BITS - efx::NEAR_LO_BITS) r = exp_to_normal_centre(x);
     return r;
 }

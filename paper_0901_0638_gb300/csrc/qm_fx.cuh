@@ -122,31 +122,21 @@ __device__ __forceinline__ unsigned long long fx_inner(uint4 c, unsigned th32)
     return ((unsigned long long)a * th32) >> (c.w >> 27);
 }
 
-// |Phi^{-1}| bits for x = 2d = S 2^(base - 52), 0 < S < 2^53 (any position of
-// the leading bit), from the table T (x = 1, i.e. d = 1/2, gives +0).
+// One row of the layout above at the offset Tp = Tu - 1 (the complement of
+// the significand's low 52 - K bits): fma(+-t_u, H, a0), with -t_u when neg
+// (rows that store z = a0 - t_u H, as the exponential -> normal map's).
 template <int MIX = FX_INT_LEAN>
-__device__ __forceinline__ unsigned long long probit_mag_fx_sx(const fxt::FxTable* T, unsigned long long S,
-                                                             int base)
+__device__ __forceinline__ double fx_row_fma(const fxt::SegA* A, const fxt::SegC* C, unsigned long long Tp,
+                                             bool neg = false)
 {
-    constexpr int K = fxt::K, sK = 52 - K;
-    const int lz = __clzll(S | 1ull) - 11;
-    const unsigned long long Mx = S << lz;                      // 2^52 <= Mx < 2^53
-    const int e = -1 - (base - lz);                             // binade: x in [2^-e-1, 2^-e)
-    // e >= -1 for every bit pattern (x = 2d <= 1); the clamp keeps the index
-    // inside the table whatever the input
-    const int ec = min(max(e, -1), fxt::E_LAST) + 1;
-    const unsigned j = (unsigned)(Mx >> sK) & ((1u << K) - 1u);
-    const int idx = (ec << K) + (int)j;
-    // offset back from the segment end, Tu = Tp + 1 in [1, 2^sK]: Tp is the
-    // complement of the significand's low sK bits.  H is stored in the half
-    // offset th = Tp 2^-(sK+1) in [0, 1/2) (re-expanded by one unit of the
-    // offset), so th 2^64 is a plain shift below 2^63.
-    const unsigned long long Tp = ~Mx & ((1ull << sK) - 1ull);
+    constexpr int K = fxt::K;
+    // H is stored in the half offset th = Tp 2^-(sK+1) in [0, 1/2) (re-expanded
+    // by one unit of the offset), so th 2^64 is a plain shift below 2^63.
     const unsigned long long Tau = Tp << (11 + K);
 
     unsigned long long a0b, B0, B1, B2s;
-    ld256(&T->a[idx], a0b, B0, B1, B2s);                           // a0, B0, B1, B2 | e0
-    const uint4 c = ld128u(&T->c[idx]);                             // C3..C6 | sh
+    ld256(A, a0b, B0, B1, B2s);                                     // a0, B0, B1, B2 | e0
+    const uint4 c = ld128u(C);                                      // C3..C6 | sh
     const unsigned long long B2 = B2s & ((1ull << 52) - 1ull);
     const unsigned e0 = (unsigned)(B2s >> 52);                      // 1083 + s0
 
@@ -174,8 +164,30 @@ __device__ __forceinline__ unsigned long long probit_mag_fx_sx(const fxt::FxTabl
         const int lt = __clzll(Tu);
         tu = __longlong_as_double((long long)((Tu << (lt - 11)) + ((unsigned long long)(1033 - lt) << 52)));
     }
-    const double g = __fma_rn(tu, __longlong_as_double((long long)hbits), __longlong_as_double((long long)a0b));
-    return (unsigned long long)__double_as_longlong(g);
+    // the sign of t_u on its bits (no FP64 instruction)
+    tu = __longlong_as_double(__double_as_longlong(tu) ^ (long long)((unsigned long long)neg << 63));
+    return __fma_rn(tu, __longlong_as_double((long long)hbits), __longlong_as_double((long long)a0b));
+}
+
+// |Phi^{-1}| bits for x = 2d = S 2^(base - 52), 0 < S < 2^53 (any position of
+// the leading bit), from the table T (x = 1, i.e. d = 1/2, gives +0).
+template <int MIX = FX_INT_LEAN>
+__device__ __forceinline__ unsigned long long probit_mag_fx_sx(const fxt::FxTable* T, unsigned long long S,
+                                                             int base)
+{
+    constexpr int K = fxt::K, sK = 52 - K;
+    const int lz = __clzll(S | 1ull) - 11;
+    const unsigned long long Mx = S << lz;                      // 2^52 <= Mx < 2^53
+    const int e = -1 - (base - lz);                             // binade: x in [2^-e-1, 2^-e)
+    // e >= -1 for every bit pattern (x = 2d <= 1); the clamp keeps the index
+    // inside the table whatever the input
+    const int ec = min(max(e, -1), fxt::E_LAST) + 1;
+    const unsigned j = (unsigned)(Mx >> sK) & ((1u << K) - 1u);
+    const int idx = (ec << K) + (int)j;
+    // offset back from the segment end, Tu = Tp + 1 in [1, 2^sK]: Tp is the
+    // complement of the significand's low sK bits
+    const unsigned long long Tp = ~Mx & ((1ull << sK) - 1ull);
+    return (unsigned long long)__double_as_longlong(fx_row_fma<MIX>(&T->a[idx], &T->c[idx], Tp));
 }
 
 

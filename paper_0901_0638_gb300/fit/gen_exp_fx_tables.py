@@ -1,28 +1,28 @@
 """Generate csrc/qm_exp_fx_tables.h: the exponential -> normal recycling map
-z = Phi^{-1}(1 - e^{-x}) on given Exp(1) samples x (Sec. 2.3, Sec. 6), in the
-fixed-point row form of csrc/qm_t_fx.h (one FP64 FMA per element).
+z = Phi^{-1}(1 - e^{-x}) on given Exp(1) samples x (Sec. 2.3, Sec. 6), with
+one FP64 FMA per element.
 
 The local expansions come from the exponential-background recycling ODE
-Q'' + Q' = Q Q'^2 (gen_exp_tables.py), each re-expanded exactly about a
-point from which |z| has non-negative coefficients (asserted for every row),
-so the device runs one unsigned fixed-point chain for every lane:
+Q'' + Q' = Q Q'^2 (rode.taylor_exp_background):
 
-* ROWS[(E - X_EMIN) 2^X_K + j], 2^-26 <= x < 128: segment j (the top X_K
-  bits of the significand m) of the binade x = 2^E m, in the offset
-  t_u = m_end - m back from the segment end (Tu = Tp + 1 integer,
-  t_u = Tu 2^-52, tau = Tp 2^-48 in [0, 1/2)):
-    below the centre segment  |z| = a0 + t_u H,   z = -|z|
-                              (x_seg: Q(-log(2(1 - e^{-x}))));
-    above it                  z = a0 - t_u H      (Q(v), v = x - ln 2,
-                              Q' completely monotone there, so H >= 0).
-* ROW_C, the centre segment [0.6875, 0.703125) that holds ln 2:
-      z = v P(t),  t = 1/32 - v,  P(v) = Q(v)/v from the series about v = 0,
-      re-expanded about v = 1/32, tau = 8 t (v_row(0)).
-H (or P) = sum_k d_k tau^k: d_0..d_4 as integers D_k = d_k 2^-s0 (D_0 in
-[2^59, 2^60]), d_5..d_8 as 32-bit integers under a per-row scale (the inner
-chain), e0 = 1081 + s0 (the layout of qm_t_fx.h).  Every row is checked by
-emulating the device's integer steps exactly against mpmath at points of the
-row, and the worst relative error is printed.  Usage:
+* ROWS / ROWS_IN[(E - X_EMIN) 2^K + j], 2^-26 <= x < 128, K = 6: segment j
+  (the top 6 bits of the significand m) of the binade x = 2^E m, in the
+  FIXED row layout (gen_fx_tables.quantise: H in the half offset, three
+  64-bit Horner steps and a 32-bit inner chain, H > 0 asserted):
+    below the segment [0.6875, 0.6953125) that holds ln 2:
+        |z| = a0 + t_u H,  z = -|z|,  |z| = Q(y), y = -log(2(1 - e^{-x}))
+        (the ODE series of Q at y_c composed with the series of y);
+    from it on:
+        z = a0 - t_u H,  z = Q(v), v = x - ln 2 (the ODE series at v_c).
+  t_u = m_end - m is the offset back from the segment end, read from the
+  significand bits as in the FIXED quantile kernel.  Each expansion is the
+  centre series truncated to degree 7 and re-expanded exactly about the end.
+* ROW_C, |x - ln 2| < 2^-12: z = v P(t), t = 1/32 - v, P(v) = Q(v)/v from the
+  series about v = 0, re-expanded about v = 1/32, tau = 8 t, in the row form
+  of qm_t_fx.h (v_row(0)); relative accuracy through z = 0.
+
+Every row is checked by emulating the device's integer steps exactly against
+mpmath at points of the row, and the worst relative error is printed.  Usage:
 python -m paper_0901_0638_gb300.fit.gen_exp_fx_tables
 """
 from __future__ import annotations
@@ -37,13 +37,13 @@ from fractions import Fraction as Fr
 import mpmath as mp
 
 from . import rode
+from . import gen_fx_tables as FX
 from . import targets as T
-from .gen_exp_tables import DEG_V, V_COARSE, V_FINE, V_MAX, V_SPLIT, X_EMIN, X_K, q_and_slope, v_seg, x_seg
+from .gen_exp_tables import DEG_V, V_COARSE, V_FINE, V_MAX, V_SPLIT, X_EMIN, q_and_slope, v_seg
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(os.path.dirname(HERE), "csrc", "qm_exp_fx_tables.h")
 NV = V_FINE * V_SPLIT + V_COARSE * (V_MAX - V_SPLIT)
-NX = (-X_EMIN) << X_K
 with mp.workdps(60):
     LN2 = +mp.log(2)                  # kept at 60 digits (module import runs at mpmath's default 15)
 
@@ -170,148 +170,166 @@ def v_row(j):
     return j, a0, D, f, e0, worst
 
 
-def x_row(i):
-    mp.mp.dps = 50
-    E, j = -1 - i // (1 << X_K), i % (1 << X_K)
-    _, _, c, a, _ = x_seg((E, j))
-    mend = 1 + mp.mpf(j + 1) / 2**X_K
-    if mp.mpf(2) ** E * (1 + mp.mpf(j) / 2**X_K) >= LN2 - mp.mpf(1) / 64:
-        return i, 0.0, [2**59, 0, 0, 0, 0], [0, 0, 0, 0], 1, 0.0       # not used by the kernel
-    # |z| = F(r), r = m c - 1 = (m_end c - 1) - c t_u
-    cm = mp.mpf(c)
-    g = reexpand(a, mend * cm - 1, -1)
-    g = [g[m] * cm ** m for m in range(len(g))]           # coefficients in t_u
-    a0 = float(g[0])
-    Hu = [g[m + 1] for m in range(len(g) - 1)]             # H(t_u) = sum Hu_i t_u^i
-    # t_u = tau / 16 + 2^-52 (tau = Tp 2^-48): H as a polynomial in tau
-    h0 = mp.mpf(2) ** -52
-    Ht = reexpand(Hu, h0, 1)                               # H(h0 + s), s = tau / 16
-    d = [Ht[m] / mp.mpf(16) ** m for m in range(len(Ht))]
-    D, f, s0, e0 = quantise(d, mp.mpf("0.5"), ("X", E, j))
-    worst = 0.0
-    for Tp in (0, 1, 2**23, 2**46, 2**47 - 1):
-        m = mend - mp.mpf(Tp + 1) * mp.mpf(2) ** -52
-        x = float(m * mp.mpf(2) ** E)
-        if x >= float(LN2 - mp.mpf(1) / 64) or x < 2.0**-26:
-            continue
-        tu = float(mp.mpf(Tp + 1) * mp.mpf(2) ** -52)
-        z = emulate(a0, D, f, s0, Tp << 16, tu)
-        ref = T.q_exp(-mp.log(2 * (-mp.expm1(-mp.mpf(x)))))
-        worst = max(worst, float(abs(mp.mpf(z) / ref - 1)))
-    return i, a0, D, f, e0, worst
-
-
-X_EMAX = 6                                      # binades 2^X_EMIN .. [64, 128) of x
-NROWS = (X_EMAX - X_EMIN + 1) << X_K
-C_E, C_J = -1, 12                               # the segment [0.6875, 0.703125) holds ln 2
+K = 6                                  # 64 segments in every binade of x (the FIXED layout)
+X_EMAX = 6                             # binades 2^X_EMIN .. [64, 128) of x
+NROWS = (X_EMAX - X_EMIN + 1) << K
+POS_X = mp.mpf("0.6875")               # the segment [0.6875, 0.6953125) holds ln 2: z = a0 - t_u H from it on
+V_NEAR = mp.mpf(2) ** -12              # |v| < V_NEAR: the centre row (z = v P)
 
 
 def seg_bounds(E, j):
-    lo = mp.mpf(2) ** E * (1 + mp.mpf(j) / 2**X_K)
-    return lo, lo + mp.mpf(2) ** (E - X_K)
+    lo = mp.mpf(2) ** E * (1 + mp.mpf(j) / 2**K)
+    return lo, lo + mp.mpf(2) ** (E - K)
 
 
-V_NEAR = mp.mpf(2) ** -12                      # |v| < V_NEAR: the centre row (z = v P)
-
-
-def seg_kind(E, j):
-    """'neg' below the segment that holds ln 2 (z < 0, |z| = a0 + t_u H), else
-    'pos' (z = a0 - t_u H; through z = 0 in the segment of ln 2, where
-    |v| >= V_NEAR keeps the cancellation below 2e-14 relative)."""
-    clo, chi = seg_bounds(C_E, C_J)
-    lo, hi = seg_bounds(E, j)
-    return "neg" if hi <= clo else "pos"
-
-
-def xp_row(E, j):
-    """A row above the centre: z = a0 - t_u H(t_u) on x = 2^E m, t_u = m_end - m
-    (the offset back from the segment end in the significand, t_u = (Tp + 1)
-    2^-52), H with non-negative coefficients (Q' completely monotone there;
-    asserted by quantise), from the ODE expansion of Q(v), v = x - ln 2, about
-    the segment centre."""
+def centre_series(E, j):
+    """z (signed) about the centre of segment j of the binade [2^E, 2^(E+1)),
+    as a series in t = m - m_c (x = 2^E m), degree FX.DEG + 1, and the side:
+    'pos' from the segment that holds ln 2 on (z = Q(v), v = x - ln 2, from
+    the exponential-background ODE series at v_c), 'neg' below it
+    (z = -Q(y), y = -log(2(1 - e^{-x})): the ODE series of Q at y_c composed
+    with the series of y(x_c + s) - y_c)."""
     mp.mp.dps = 50
-    mlo = 1 + mp.mpf(j) / 2**X_K
-    mhi = mlo + mp.mpf(1) / 2**X_K
-    mc = (mlo + mhi) / 2
-    vc = mp.mpf(2) ** E * mc - LN2
-    q0, q1 = q_and_slope(vc)
-    b = rode.taylor_exp_background(vc, q0, q1, DEG_V + 1)[:DEG_V + 1]   # z in s = v - vc
-    bs = [b[k] * mp.mpf(2) ** (E * k) for k in range(len(b))]          # in m - mc
-    g = reexpand(bs, mhi - mc, -1)                                      # z(m_end - t_u)
-    a0 = float(g[0])
-    H = [-g[m + 1] for m in range(len(g) - 1)]
-    Ht = reexpand(H, mp.mpf(2) ** -52, 1)                               # t_u = 2^-52 + tau / 16
-    d = [Ht[m] / mp.mpf(16) ** m for m in range(len(Ht))]
-    D, f, s0, e0 = quantise(d, mp.mpf("0.5"), ("XP", E, j))
-    worst = 0.0
-    pts = [0, 1, 2**23, 2**46, 2**47 - 1]
-    if (E, j) == (C_E, C_J):                    # both sides of |v| = V_NEAR, where this row takes over
-        for vv in (V_NEAR, -V_NEAR, 2 * V_NEAR, -2 * V_NEAR, mp.mpf(2) ** -8, -mp.mpf(2) ** -8):
-            pts.append(int((mhi - (LN2 + vv) / mp.mpf(2) ** E) * mp.mpf(2) ** 52) - 1)
-    for Tp in pts:
-        m = mhi - mp.mpf(Tp + 1) * mp.mpf(2) ** -52
-        x = float(m * mp.mpf(2) ** E)
-        tu = float(mp.mpf(Tp + 1) * mp.mpf(2) ** -52)
-        z = emulate(a0, D, f, s0, Tp << 16, -tu)
-        v = mp.mpf(x) - LN2
-        ref = T.q_exp(v) if v >= 0 else -T.q_exp(-mp.log(2 - mp.exp(-v)))
-        worst = max(worst, float(abs(mp.mpf(z) / ref - 1)))
-    return a0, D, f, e0, worst
+    n = FX.DEG + 2
+    mlo = 1 + mp.mpf(j) / 2**K
+    mc = mlo + mp.mpf(1) / 2**(K + 1)
+    xc = mp.mpf(2) ** E * mc
+    scale = [mp.mpf(2) ** (E * k) for k in range(n + 1)]           # s = x - x_c = 2^E t
+    if mp.mpf(2) ** E * mlo >= POS_X:
+        vc = xc - LN2
+        q0, q1 = q_and_slope(vc)
+        b = rode.taylor_exp_background(vc, q0, q1, n)
+        return "pos", [b[k] * scale[k] for k in range(n + 1)]
+    ec = mp.exp(-xc)
+    A0 = -mp.expm1(-xc)                                            # 1 - e^{-x_c}
+    w = [mp.mpf(0)] + [-ec * mp.mpf(-1) ** k / mp.factorial(k) / A0 for k in range(1, n + 1)]
+    L = [mp.mpf(0)] + [mp.mpf(-1) ** (k + 1) / k for k in range(1, n + 1)]      # log(1 + w)
+    dy = [-c for c in rode.compose(L, w, n)]                       # y(x_c + s) - y_c
+    yc = -mp.log(2 * A0)
+    q0, q1 = q_and_slope(yc)
+    b = rode.taylor_exp_background(yc, q0, q1, n)
+    a = rode.compose(b, dy, n)
+    return "neg", [-a[k] * scale[k] for k in range(n + 1)]
 
 
-def xn_row(E, j):
-    """A row below the centre: |z| = a0 + t_u H (the X rows of x_seg)."""
-    i = (-1 - E) * (1 << X_K) + j
-    _, a0, D, f, e0, worst = x_row(i)
-    return a0, D, f, e0, worst
+def fx_h(q, Tu):
+    """H of a FIXED-layout row at the integer offset Tu, as the kernel forms
+    it (gen_fx_tables: the chains, the rounding shift, the bit assembly)."""
+    Tp = Tu - 1
+    Tau = Tp << (11 + K)
+    acc = q["B"][FX.NI - 1] + FX.inner(q, Tp >> 15)
+    assert acc < 2**62
+    acc = q["B"][1] + FX.mulhi_limbs(acc, Tau)
+    assert acc < 2**62
+    acc = q["B"][0] + FX.mulhi_limbs(acc, Tau)
+    assert 2**61 <= acc < 2**63
+    top = acc >> 62
+    mant = (acc + (256 << top)) >> (9 + top)
+    return Fr(mant) * Fr(2) ** (9 + top + q["s0"])
 
 
-def unified_row(ij):
+def truth(x):
+    x = mp.mpf(x)
+    v = x - LN2
+    if v >= 0:
+        return T.q_exp(v)
+    return -T.q_exp(-mp.log(2 * (-mp.expm1(-x))))
+
+
+def binade_row(ij):
+    """One device row: |z| = a0 + t_u H (neg side, z = -|z|) or z = a0 - t_u H
+    (pos side) in the offset t_u = m_end - m back from the segment end, H with
+    positive coefficients (asserted by gen_fx_tables.quantise), checked by
+    emulating the kernel's arithmetic against mpmath."""
     E, j = ij
-    kind = seg_kind(E, j)
-    a0, D, f, e0, worst = (xp_row if kind == "pos" else xn_row)(E, j)
-    return E, j, kind, a0, D, f, e0, worst
+    mp.mp.dps = 50
+    side, a = centre_series(E, j)
+    # the centre expansion truncated to degree FX.DEG, then re-expanded exactly
+    # about the segment end (the same polynomial, so the same truncation error)
+    g = reexpand(a[:FX.DEG + 1], mp.mpf(1) / 2**(K + 1), -1)       # z(m_end - t_u)
+    if side == "neg":
+        g = [-c for c in g]                                        # |z| = a0 + t_u H
+    else:
+        g = [g[0]] + [-c for c in g[1:]]                           # z = a0 - t_u H
+    q = FX.quantise(E, j, K, g)
+    full = 2**(52 - K)
+    lo, hi = seg_bounds(E, j)
+    pts = [1, 2, 3, full // 3, full // 2, full - 1, full]
+    if lo <= LN2 < hi:                        # both sides of |v| = V_NEAR, where this row takes over
+        for vv in (V_NEAR, -V_NEAR, 2 * V_NEAR, -2 * V_NEAR, mp.mpf(2) ** -8, -mp.mpf(2) ** -8):
+            pts.append(int((hi - (LN2 + vv)) / mp.mpf(2) ** (E - 52)))
+    worst = 0.0
+    for Tu in pts:
+        x = float((hi - mp.mpf(Tu) * mp.mpf(2) ** (E - 52)))
+        if x < 2.0**-26:
+            continue
+        if lo <= LN2 < hi and abs(mp.mpf(x) - LN2) < V_NEAR:
+            continue
+        tu = Fr(Tu, 2**52)
+        if side == "neg":
+            z = -float(tu * fx_h(q, Tu) + Fr(q["a0"]))
+        else:
+            z = float(Fr(q["a0"]) - tu * fx_h(q, Tu))
+        ref = truth(x)
+        worst = max(worst, float(abs(mp.mpf(z) / ref - 1)))
+    return E, j, side, q, worst
 
 
 def row_literal(a0, D, f, e0):
+    """The centre row as a ttbl::SegTX initialiser."""
     d4e = D[4] | (e0 << 52)
     return ("  {" + float(a0).hex() + "," + ",".join(f"{x}ull" for x in D[:4]) + f",{d4e}ull,{{" +
             ",".join(f"{x:#x}u" for x in f) + "}},\n")
 
 
+def i64(v):
+    """A uint64 field as a C long long literal."""
+    if v >= 2**63:
+        v -= 2**64
+    return f"{v}ll" if v != -2**63 else "(-0x7fffffffffffffffll - 1)"
+
+
 def main():
-    cells = [(E, j) for E in range(X_EMIN, X_EMAX + 1) for j in range(1 << X_K)]
+    cells = [(E, j) for E in range(X_EMIN, X_EMAX + 1) for j in range(1 << K)]
     with mproc.Pool(max(1, os.cpu_count() or 2)) as pool:
-        rows = pool.map(unified_row, cells, chunksize=4)
+        rows = pool.map(binade_row, cells, chunksize=8)
         centre = v_row(0)
-    clo, chi = seg_bounds(C_E, C_J)
-    assert clo < LN2 - V_NEAR and LN2 + V_NEAR < chi            # the centre row inside that segment
+    assert len(rows) == NROWS
     near_lo, near_hi = float(LN2 - V_NEAR), float(LN2 + V_NEAR)   # ROW_C serves [near_lo, near_hi)
+    clo, chi = seg_bounds(-1, int((LN2 * 2 - 1) * 2**K))
+    assert clo == POS_X and clo < near_lo and near_hi < chi       # the centre row inside the ln 2 segment
     bits = lambda x: struct.unpack("<Q", struct.pack("<d", x))[0]
-    wn = max(r[7] for r in rows if r[2] == "neg")
-    wp = max(r[7] for r in rows if r[2] == "pos")
+    wn = max(r[4] for r in rows if r[2] == "neg")
+    wp = max(r[4] for r in rows if r[2] == "pos")
     wc = centre[5]                          # over v in [-1/64, 1/32), wider than it serves
     print(f"exp -> normal fixed-point rows: {NROWS} binade rows (worst below ln 2 {wn:.3g}, above {wp:.3g}), "
           f"centre row (worst {wc:.3g})", file=sys.stderr)
     L = [
         "// Generated by paper_0901_0638_gb300/fit/gen_exp_fx_tables.py -- do not edit.\n",
-        "// Exponential -> normal recycling map z = Phi^{-1}(1 - e^{-x}) in the fixed-point\n",
-        "// row form of qm_t_fx.h: ROWS[(E - X_EMIN) 2^X_K + j] for segment j of the binade\n",
-        "// [2^E, 2^(E+1)) of x, in the offset t_u back from the segment end (below the\n",
-        "// segment [0.6875, 0.703125) that holds ln 2, |z| = a0 + t_u H, z < 0; from it on\n",
-        "// z = a0 - t_u H), and ROW_C for |x - ln 2| < 2^-12 (z = v P(tau), v = x - ln 2,\n",
-        "// tau = 8 (1/32 - v)); see the generator.\n",
+        "// Exponential -> normal recycling map z = Phi^{-1}(1 - e^{-x}): segment j (top 6 bits\n",
+        "// of the significand) of the binade [2^E, 2^(E+1)) of x at row (E - X_EMIN) 2^X_K + j,\n",
+        "// in the FIXED row layout of qm_fx.cuh (ROWS: a0, B0, B1, B2 | e0 << 52; ROWS_IN: the\n",
+        "// 32-bit inner chain C3..C6 | (32 - c) << 27), H > 0 in the offset t_u back from the\n",
+        "// segment end: below the segment [0.6875, 0.6953125) that holds ln 2, |z| = a0 + t_u H,\n",
+        "// z < 0; from it on z = a0 - t_u H.  ROW_C (the row form of qm_t_fx.h) serves\n",
+        "// |x - ln 2| < 2^-12: z = v P(tau), v = x - ln 2, tau = 8 (1/32 - v).\n",
         f"// Emulated worst relative error: below ln 2 {wn:.3g}, above {wp:.3g}, centre {wc:.3g}.\n",
-        "#pragma once\n#include \"qm_t_fx.h\"\n\nnamespace qm {\nnamespace efx {\n\n",
-        f"constexpr int X_K = {X_K};\nconstexpr int X_EMIN = {X_EMIN};\nconstexpr int X_EMAX = {X_EMAX};\n",
+        "#pragma once\n#include \"qm_fx.cuh\"\n#include \"qm_t_fx.h\"\n\nnamespace qm {\nnamespace efx {\n\n",
+        f"constexpr int X_K = {K};\nconstexpr int X_EMIN = {X_EMIN};\nconstexpr int X_EMAX = {X_EMAX};\n",
         f"constexpr int NROWS = {NROWS};\n",
-        "constexpr unsigned long long POS_BITS = 0x3FE6000000000000ull;    // 0.6875: z = a0 - t_u H from here\n",
+        f"constexpr unsigned long long POS_BITS = {bits(float(POS_X)):#x}ull;    // 0.6875: z = a0 - t_u H from here\n",
         f"constexpr unsigned long long NEAR_LO_BITS = {bits(near_lo):#x}ull;   // ln 2 - 2^-12\n",
         f"constexpr unsigned long long NEAR_HI_BITS = {bits(near_hi):#x}ull;   // ln 2 + 2^-12\n\n",
-        "__device__ const ttbl::SegTX ROWS[NROWS] = {\n",
+        "__device__ const fxt::SegA ROWS[NROWS] = {\n",
     ]
-    for _, _, _, a0, D, f, e0, _ in rows:
-        L.append(row_literal(a0, D, f, e0))
+    for _, _, _, q, _ in rows:
+        B = q["B"]
+        L.append("  {" + float(q["a0"]).hex() + "," + ",".join(i64(b) for b in B[:2]) + "," +
+                 i64((q["e0"] << 52) | B[2]) + "},\n")
+    L.append("};\n\n__device__ const fxt::SegC ROWS_IN[NROWS] = {\n")
+    for _, _, _, q, _ in rows:
+        C = q["C"]
+        L.append("  {" + ",".join(f"{x:#x}u" for x in C[:3] + [C[3] | (q["sh"] << 27)]) + "},\n")
     _, a0, D, f, e0, _ = centre
     L.append("};\n\n__device__ const ttbl::SegTX ROW_C = \n" + row_literal(a0, D, f, e0).rstrip(",\n") + ";\n")
     L.append("\n}  // namespace efx\n}  // namespace qm\n")

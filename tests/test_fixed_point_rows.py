@@ -94,8 +94,15 @@ def probit_fixed(A, C, u: float) -> float:
     ec = min(max(e, -1), 1072) + 1
     idx = (ec << 6) + ((Mx >> 46) & 63)
     Tp = ~Mx & ((1 << 46) - 1)
-    a0b, B0, B1, B2s = A[idx]
-    acc = (B2s & MANT) + inner(C[idx], Tp >> 15)
+    z = fx_row(A[idx], C[idx], Tp)
+    return z if upper else -z
+
+
+def fx_row(a_row, c_row, Tp: int, neg: bool = False) -> float:
+    """One row of the FIXED layout at the offset Tp = Tu - 1: the chains, the
+    rounding shift and bit assembly of H, and fma(+-t_u, H, a0) rounded once."""
+    a0b, B0, B1, B2s = a_row
+    acc = (B2s & MANT) + inner(c_row, Tp >> 15)
     acc = B1 + mulhi3(acc, Tp << 17)
     acc = B0 + mulhi3(acc, Tp << 17)
     if acc == 0:                                  # the zero rows of u = 1/2
@@ -105,8 +112,7 @@ def probit_fixed(A, C, u: float) -> float:
         top = acc >> 62
         hbits = ((acc + (256 << top)) >> (9 + top)) + (((B2s >> 52) + top) << 52)
     tu = Fr(Tp + 1, 2**52)
-    z = float(tu * Fr(dbl(hbits)) + Fr(dbl(a0b)))
-    return z if upper else -z
+    return float((-tu if neg else tu) * Fr(dbl(hbits)) + Fr(dbl(a0b)))
 
 
 def normal_inputs():
@@ -145,23 +151,26 @@ def test_fixed_table_rows_against_the_oracle(fx_table):
 
 @pytest.fixture(scope="module")
 def exp_rows():
-    """ROWS (binade rows) and ROW_C (the centre row): (a0 bits, D0, D1, D2, D3,
+    """ROWS (a0 bits, B0, B1, B2 | e0) and ROWS_IN (four 32-bit words), the
+    binade rows in the FIXED layout; ROW_C, the centre row (a0 bits, D0..D3,
     D4 | e0, (four 32-bit words))."""
     text = open(os.path.join(CSRC, "qm_exp_fx_tables.h")).read()
     consts = {k: int(v) for k, v in re.findall(r"constexpr int (\w+) = (-?\d+);", text)}
-    for k in ("NEAR_LO", "NEAR_HI"):
+    for k in ("NEAR_LO", "NEAR_HI", "POS"):
         consts[k] = int(re.search(k + r"_BITS = (0x[0-9a-fA-F]+)ull", text).group(1), 16)
+    a_part = text[text.index("ROWS[NROWS] ="):text.index("ROWS_IN[NROWS] =")]
+    c_part = text[text.index("ROWS_IN[NROWS] ="):text.index("ROW_C =")]
+    A = [(bits(float.fromhex(m.group(1))), _int(m.group(2)) & M64, _int(m.group(3)) & M64, _int(m.group(4)) & M64)
+         for m in re.finditer(r"\{(0x[0-9a-fp.+-]+|[-0-9.e+]+),([^,{}]+),([^,{}]+),([^{}]+)\}", a_part)]
+    C = [tuple(int(x.rstrip("u"), 16) for x in m.group(1).split(","))
+         for m in re.finditer(r"\{(0x[0-9a-f]+u,0x[0-9a-f]+u,0x[0-9a-f]+u,0x[0-9a-f]+u)\}", c_part)]
     pat = r"\{([^{},]+),(\d+)ull,(\d+)ull,(\d+)ull,(\d+)ull,(\d+)ull,\{([^}]*)\}\}"
-
-    def row(m):
-        w = tuple(int(x.strip().rstrip("u"), 16) if x.strip() != "0" else 0 for x in m.group(7).split(","))
-        return (bits(float.fromhex(m.group(1))),) + tuple(int(m.group(k)) for k in range(2, 7)) + (w,)
-
-    body = text[text.index("ROWS[NROWS] ="):text.index("ROW_C =")]
-    rows = [row(m) for m in re.finditer(pat, body)]
-    centre = row(re.search(pat, text[text.index("ROW_C ="):]))
-    assert len(rows) == consts["NROWS"] == (consts["X_EMAX"] - consts["X_EMIN"] + 1) << consts["X_K"]
-    return rows, centre, consts
+    m = re.search(pat, text[text.index("ROW_C ="):])
+    w = tuple(int(x.strip().rstrip("u"), 16) if x.strip() != "0" else 0 for x in m.group(7).split(","))
+    centre = (bits(float.fromhex(m.group(1))),) + tuple(int(m.group(k)) for k in range(2, 7)) + (w,)
+    n = (consts["X_EMAX"] - consts["X_EMIN"] + 1) << consts["X_K"]
+    assert len(A) == len(C) == consts["NROWS"] == n and consts["X_K"] == 6
+    return (A, C), centre, consts
 
 
 def segtx(row, Sig: int, mlt: float) -> float:
@@ -180,9 +189,10 @@ def segtx(row, Sig: int, mlt: float) -> float:
 
 def exp_fixed(rows, centre, consts, x: float):
     """The exponential -> normal kernel (None where it goes out of line:
-    x < 2^-26, x >= 128, edge values): segment j of the binade of x, the
-    offset t_u back from its end from the bits, z = -(a0 + t_u P) below
-    0.6875 and a0 - t_u P from there; |x - ln 2| < 2^-12 in v = x - ln 2."""
+    x < 2^-26, x >= 128, edge values): segment j (top 6 bits) of the binade
+    of x, the offset t_u back from its end from the bits, the FIXED row
+    arithmetic, z = -(a0 + t_u H) below 0.6875 and a0 - t_u H from there;
+    |x - ln 2| < 2^-12 by the centre row in v = x - ln 2."""
     xb = bits(x)
     if xb == 0 or xb >= 0x7FF0000000000000 or xb < 0x3E50000000000000 or xb >= 0x4060000000000000:
         return None
@@ -195,11 +205,11 @@ def exp_fixed(rows, centre, consts, x: float):
         Sig = ((Mt << min(st, 63)) & (2**63 - 1)) if st >= 0 else (Mt >> -st if st > -64 else 0)
         return segtx(centre, Sig, v)
     E = (xb >> 52) - 1023
-    r = ((E - consts["X_EMIN"]) << consts["X_K"]) + ((xb >> 47) & 31)
-    Tp = ~xb & ((1 << 47) - 1)
-    tu = dbl(0x3FF0000000000001 + Tp) - 1.0
-    pos = x >= 0.6875
-    z = segtx(rows[r], Tp << 16, -tu if pos else tu)
+    r = ((E - consts["X_EMIN"]) << 6) + ((xb >> 46) & 63)
+    Tp = ~xb & ((1 << 46) - 1)
+    pos = xb >= consts["POS"]
+    A, C = rows
+    z = fx_row(A[r], C[r], Tp, neg=pos)
     return z if pos else -z
 
 
@@ -211,7 +221,7 @@ def test_exp_to_normal_rows_against_the_oracle(exp_rows):
     xs += list(np.exp(rng.uniform(np.log(2.0**-26), np.log(ln2), 600)))      # the X binades
     xs += list(ln2 + rng.uniform(-1 / 64, 1 / 16, 400))                       # through z = 0
     xs += list(np.exp(rng.uniform(0.0, np.log(127.9), 400)))                 # binades up to [64, 128)
-    for x0 in (0.6875, 0.703125, ln2, ln2 - 2.0**-12, ln2 + 2.0**-12, ln2 - 2.0**-11, ln2 + 2.0**-11,
+    for x0 in (0.6875, 0.6953125, 0.703125, ln2, ln2 - 2.0**-12, ln2 + 2.0**-12, ln2 - 2.0**-11, ln2 + 2.0**-11,
                0.71875, 1.0, 2.0, 8.0, 64.0, 100.0):                          # the centre and binade ends
         xs += [x0, np.nextafter(x0, 0.0), np.nextafter(x0, np.inf)]
     xs = np.array([x for x in xs if x > 0])
