@@ -109,6 +109,12 @@ def test_recycle_exp_to_normal():
                   for to in (0.0, 1.0)]),
         [2.0**-26, np.nextafter(2.0**-26, 0.0), np.nextafter(2.0**-26, 1.0), math.log(2) + 64.0,
          np.nextafter(math.log(2) + 64.0, 0.0)],
+        # the device rows: 64 segments in every binade of x from 2^-26 to 128,
+        # the segment [0.6875, 0.6953125) that holds ln 2 and its neighbours
+        np.array([np.nextafter(2.0**E * (1 + j / 64), to) for E in range(-26, 7) for j in (0, 1, 23, 24, 25, 63)
+                  for to in (0.0, 2.0**E * (1 + j / 64), 1e9)]),
+        # where the centre row hands over: |x - ln 2| = 2^-12
+        np.array([math.log(2) + sg * 2.0**-12 * f for sg in (-1.0, 1.0) for f in (1 - 1e-12, 1.0, 1 + 1e-12)]),
     ])
     w = oracle.recycle_exp(x)
     t = torch.from_numpy(x).to(DEV)
