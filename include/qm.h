@@ -214,12 +214,13 @@ qm_status qm_sample_moments_noalloc(uint64_t key, uint64_t ctr0, size_t n,
  * on the host at the first call with that nu on a device -- the recurrence of
  * Sec. 3.2 integrated from the tail coordinate of Sec. 3.3, see
  * qm_t_table_build -- then uploaded (a synchronous cudaMalloc + copy of
- * ~18 KB, kept until exit; at most 256 distinct nu per process, then
+ * QM_T_ROWS_BYTES, kept until exit; at most 256 distinct nu per process, then
  * QM_ERR_NOMEM); nu outside both: QM_ERR_UNSUPPORTED).  On upload every
- * segment is re-expanded about its start and stored for evaluation in 64-bit
- * fixed point with one FP64 FMA (the offline tables too, at the first use
- * on a device); a table whose coefficients fail the conversion's sign or
- * range checks is refused with QM_ERR_UNSUPPORTED;
+ * segment is split into four rows of width 1/128, each re-expanded about its
+ * start and stored for evaluation in 64-bit fixed point with one FP64 FMA
+ * (the offline tables too, at the first use on a device; see
+ * qm_t_rows_build); a table whose coefficients fail the conversion's sign,
+ * range or accuracy checks is refused with QM_ERR_UNSUPPORTED;
  * (EXPONENTIAL, NORMAL): out = Phi^{-1}(1 - e^{-in}) (Sec. 2.3, Sec. 6);
  * (UNIFORM, NORMAL): out = Phi^{-1}(in) (FP64 default variant).
  * Anything else: QM_ERR_UNSUPPORTED.  in, out: double[n] (device).        */
@@ -246,15 +247,22 @@ qm_status qm_recycle(int src, int dst, const qm_params* p, const double* in,
 #define QM_T_NU_MAX 100.0
 qm_status qm_t_table_build(double nu, double* seg_coef, double* tail);
 
-/* qm_t_rows_build (host only, no GPU): the same segments as the device holds
- * them -- QM_T_NSEG rows of 64 bytes (QM_FX_ROW_BYTES), segment j re-expanded
- * about z_j = j/32 and packed for the unsigned fixed-point chain:
- *   double a0;  uint64 D0, D1, D2, D3, D4e;  uint32 c[4]
- * |t| = a0 + sigma P(tau), sigma = |z| - z_j, tau = 16 sigma; P = sum d_k tau^k
- * with D_k = d_k 2^-s0 (k <= 4; D4e = D_4 | e0 << 52, e0 = 1081 + s0) and
- * c[0..2] = C_5..C_7, c[3] = C_8 | (32 - c) << 27, C_k = d_k 2^-(s0 + c).
- * Errors as qm_t_table_build; QM_ERR_UNSUPPORTED if a segment does not fit
- * the form (signs, ranges, or off by more than 1e-13 after packing).       */
+/* qm_t_rows_build (host only, no GPU): the rows the device evaluates for nu,
+ * QM_T_NROW rows of width 1/128 on 0 <= |z| < 8.75 (row r starts at
+ * z_r = r/128; segment j of qm_t_table_build re-expanded about each of its
+ * four row starts and truncated to degree 7), in QM_T_ROWS_BYTES of host
+ * memory: first QM_T_NROW 32-byte rows {double a0; int64 B0, B1, B2e}, then
+ * QM_T_NROW 16-byte rows {uint32 C3, C4, C5, C6s}.
+ * |t| = a0 + sigma H(th), sigma = |z| - z_r, th = 64 sigma in [0, 1/2);
+ * H = sum b'_k th^k with B_k = b'_k 2^-s0 (k <= 2; B2e = B_2 | e0 << 52,
+ * e0 = 1080 + s0, H(0) 2^-s0 in [2^58, 2^59)) and C_k = b'_k 2^-(s0 + c)
+ * (k = 3..6; C6s = C_6 | (32 - c) << 27), every b'_k >= 0.
+ * Errors as qm_t_table_build; QM_ERR_UNSUPPORTED if a row does not fit the
+ * form (signs, ranges, or off by more than 1e-12 from the segment's
+ * degree-9 expansion after packing).  QM_FX_ROW_BYTES is the size of the
+ * 64-byte rows of qm_hyp_rows_build.                                       */
+#define QM_T_NROW 1120
+#define QM_T_ROWS_BYTES (QM_T_NROW * 48)
 #define QM_FX_ROW_BYTES 64
 qm_status qm_t_rows_build(double nu, void* rows);
 

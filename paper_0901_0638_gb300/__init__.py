@@ -233,17 +233,20 @@ def qm_t_table_build(nu: float):
 
 
 QM_FX_ROW_BYTES = 64
+QM_T_NROW = 1120
 
 
 def qm_t_rows_build(nu: float):
-    """The Student-t segments as the device holds them (no GPU): a
-    (QM_T_NSEG, 8) uint64 array, one 64-byte fixed-point row per segment
-    (a0 bits, D0..D3, D4 | e0 << 52, then the four 32-bit inner-chain words
-    packed two per uint64, low word first)."""
+    """The Student-t rows as the device holds them (no GPU): (A, C), A a
+    (QM_T_NROW, 4) uint64 array (a0 bits, B0, B1, B2 | e0 << 52) and C a
+    (QM_T_NROW, 4) uint32 array (C3, C4, C5, C6 | (32 - c) << 27); row r
+    covers r/128 <= |z| < (r + 1)/128."""
     import numpy as np
-    rows = np.zeros((QM_T_NSEG, QM_FX_ROW_BYTES // 8), dtype=np.uint64)
-    _check(load().qm_t_rows_build(float(nu), rows.ctypes.data))
-    return rows
+    buf = np.zeros(QM_T_NROW * 48, dtype=np.uint8)
+    _check(load().qm_t_rows_build(float(nu), buf.ctypes.data))
+    a = buf[: QM_T_NROW * 32].view(np.uint64).reshape(QM_T_NROW, 4).copy()
+    c = buf[QM_T_NROW * 32:].view(np.uint32).reshape(QM_T_NROW, 4).copy()
+    return a, c
 
 
 QM_TC_Z_MAX, QM_TC_HZ_INV, QM_TC_NZ, QM_TC_ROW = 8.5, 16, 272, 11

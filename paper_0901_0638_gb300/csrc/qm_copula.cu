@@ -317,7 +317,7 @@ qm_status fill_copula(int d, const double* chol, const qm_margin* margins, doubl
             const double* tail = nullptr;
             const qm_status st = t_select(m.nu, &c.host.t[j].k, &seg, &tail);
             if (st != QM_OK) return st;
-            c.host.t[j].seg = (const ttbl::SegTX*)seg;
+            c.host.t[j].seg = (const ttbl::TRows*)seg;
             c.host.t[j].tail = tail;
         } else if (m.kind == QM_DIST_NORMAL) {
             c.host.kind[j] = MARGIN_NORMAL;

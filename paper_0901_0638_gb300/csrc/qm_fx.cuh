@@ -122,9 +122,43 @@ __device__ __forceinline__ unsigned long long fx_inner(uint4 c, unsigned th32)
     return ((unsigned long long)a * th32) >> (c.w >> 27);
 }
 
-// One row of the layout above at the offset Tp = Tu - 1 (the complement of
-// the significand's low 52 - K bits): fma(+-t_u, H, a0), with -t_u when neg
-// (rows that store z = a0 - t_u H, as the exponential -> normal map's).
+// One row of the layout above at th = Tau 2^-64 in [0, 1/2) (Tau < 2^63):
+// fma(tu, H(th), a0), tu the row's multiplier (the offset t_u, exact).  The
+// inner chain takes th32 = Tau >> 32 (Horner, or Estrin with ESTRIN: the two
+// truncate differently).  HB is the position of the leading bit of
+// H(0) 2^-s0 (61 for the quantile's rows, e0 = 1083 + s0; rows whose
+// polynomial grows faster keep B2 inside its 52-bit field with a lower one,
+// e0 = 1022 + HB + s0).
+template <bool ESTRIN = false, int HB = 61>
+__device__ __forceinline__ double fx_row_core(const fxt::SegA* A, const fxt::SegC* C, unsigned long long Tau,
+                                              double tu)
+{
+    static_assert(HB >= 54 && HB <= 61, "H(0) 2^-s0 between 2^54 and 2^62");
+    unsigned long long a0b, B0, B1, B2s;
+    ld256(A, a0b, B0, B1, B2s);                                     // a0, B0, B1, B2 | e0
+    const uint4 c = ld128u(C);                                      // C3..C6 | sh
+    const unsigned long long B2 = B2s & ((1ull << 52) - 1ull);
+    const unsigned e0 = (unsigned)(B2s >> 52);                      // 1022 + HB + s0
+
+    unsigned long long acc = B2 + fx_inner<ESTRIN>(c, (unsigned)(Tau >> 32));
+    acc = B1 + mulhi_q(acc, Tau);
+    acc = B0 + mulhi_q(acc, Tau);                                   // H 2^-s0 (0 on the zero rows)
+
+    // H as a double: acc is in [2^HB, 2^(HB+2)) (H varies by under a factor 2
+    // across a segment, and s0 puts H(0) 2^-s0 in [2^HB, 2^(HB+1))), so its
+    // leading bit is bit HB or HB + 1: round to 53 bits by one shift, then
+    // add the exponent field; the significand's leading bit carries into the
+    // exponent (a round-up to 2^53 carries one further, to the next power of
+    // two, exactly)
+    const unsigned top = (unsigned)(acc >> (HB + 1));
+    const unsigned long long hm = (acc + ((1ull << (HB - 53)) << top)) >> (HB - 52 + top);
+    const unsigned long long hbits = hm + ((unsigned long long)(e0 + top) << 52);
+    return __fma_rn(tu, __longlong_as_double((long long)hbits), __longlong_as_double((long long)a0b));
+}
+
+// A row at the offset Tp = Tu - 1 back from the segment end (the complement
+// of the significand's low 52 - K bits): fma(+-t_u, H, a0), with -t_u when
+// neg (rows that store z = a0 - t_u H, as the exponential -> normal map's).
 template <int MIX = FX_INT_LEAN>
 __device__ __forceinline__ double fx_row_fma(const fxt::SegA* A, const fxt::SegC* C, unsigned long long Tp,
                                              bool neg = false)
@@ -133,26 +167,6 @@ __device__ __forceinline__ double fx_row_fma(const fxt::SegA* A, const fxt::SegC
     // H is stored in the half offset th = Tp 2^-(sK+1) in [0, 1/2) (re-expanded
     // by one unit of the offset), so th 2^64 is a plain shift below 2^63.
     const unsigned long long Tau = Tp << (11 + K);
-
-    unsigned long long a0b, B0, B1, B2s;
-    ld256(A, a0b, B0, B1, B2s);                                     // a0, B0, B1, B2 | e0
-    const uint4 c = ld128u(C);                                      // C3..C6 | sh
-    const unsigned long long B2 = B2s & ((1ull << 52) - 1ull);
-    const unsigned e0 = (unsigned)(B2s >> 52);                      // 1083 + s0
-
-    // th = Tp 2^-47: th32 = Tp >> 15 for the inner chain, Tau = th 2^64
-    unsigned long long acc = B2 + fx_inner(c, (unsigned)(Tp >> 15));
-    acc = B1 + mulhi_q(acc, Tau);
-    acc = B0 + mulhi_q(acc, Tau);                                   // H 2^-s0 (0 on the zero rows)
-
-    // H as a double: acc is in [2^61, 2^63) (H varies by under 1.6 % across a
-    // segment, and s0 puts H(0) 2^-s0 in [2^61, 2^62)), so its leading bit is
-    // bit 61 or 62: round to 53 bits by one shift, then add the exponent field;
-    // the significand's leading bit carries into the exponent (a round-up to
-    // 2^53 carries one further, to the next power of two, exactly)
-    const unsigned top = (unsigned)(acc >> 62);
-    const unsigned long long hm = (acc + (256ull << top)) >> (9 + top);
-    const unsigned long long hbits = hm + ((unsigned long long)(e0 + top) << 52);
     // t_u as a double (exact, 1 <= Tu <= 2^sK): 1 + t_u has the bits
     // 0x3FF0... + Tu and taking 1 away again is exact (Sterbenz); or by
     // normalising Tu and inserting the exponent
@@ -166,7 +180,7 @@ __device__ __forceinline__ double fx_row_fma(const fxt::SegA* A, const fxt::SegC
     }
     // the sign of t_u on its bits (no FP64 instruction)
     tu = __longlong_as_double(__double_as_longlong(tu) ^ (long long)((unsigned long long)neg << 63));
-    return __fma_rn(tu, __longlong_as_double((long long)hbits), __longlong_as_double((long long)a0b));
+    return fx_row_core(A, C, Tau, tu);
 }
 
 // |Phi^{-1}| bits for x = 2d = S 2^(base - 52), 0 < S < 2^53 (any position of

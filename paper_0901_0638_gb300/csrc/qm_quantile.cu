@@ -213,7 +213,7 @@ struct ExpToNormal {
 };
 
 struct TDynMap {
-    const ttbl::SegTX* seg;
+    const ttbl::TRows* seg;
     const double* tail;
     __device__ double operator()(double z) const { return recycle_t_dyn(seg, tail, z); }
 };
@@ -954,7 +954,7 @@ extern "C" qm_status qm_sample_fused(int target, const qm_params* p, uint64_t ke
             const double* ttail = nullptr;
             const qm_status st = t_select(p->nu, &tk.k, &tseg, &ttail);
             if (st != QM_OK) return st;
-            tk.seg = (const ttbl::SegTX*)tseg;
+            tk.seg = (const ttbl::TRows*)tseg;
             tk.tail = ttail;
         }
         double* o = (double*)out;
@@ -1023,7 +1023,7 @@ extern "C" qm_status qm_recycle(int src, int dst, const qm_params* p, const doub
         int kk = -1;
         const qm_status st = t_select(p->nu, &kk, &seg, &tail);
         if (st != QM_OK) return st;
-        return launch_map(in, out, n, TDynMap{(const ttbl::SegTX*)seg, tail}, (cudaStream_t)stream,
+        return launch_map(in, out, n, TDynMap{(const ttbl::TRows*)seg, tail}, (cudaStream_t)stream,
                           "recycle normal->t");
     }
     return fail(QM_ERR_UNSUPPORTED, "qm_recycle: pair (%d -> %d) not supported", src, dst);

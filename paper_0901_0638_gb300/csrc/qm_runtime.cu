@@ -250,7 +250,7 @@ extern "C" qm_status qm_batch_create(const qm_segment* segs, int nseg, const qm_
             const double* ttail = nullptr;
             const qm_status st = t_select(s.nu, &d.t.k, &tseg, &ttail);
             if (st != QM_OK) return st;
-            d.t.seg = (const ttbl::SegTX*)tseg;
+            d.t.seg = (const ttbl::TRows*)tseg;
             d.t.tail = ttail;
             d.kind = KIND_T;
         } else if (s.src == QM_DIST_EXPONENTIAL && s.dst == QM_DIST_NORMAL) {

@@ -318,7 +318,7 @@ static void worker_loop(qm_server* s)
                     const void* tseg = nullptr;
                     const double* ttail = nullptr;
                     t_select(c.nu, &d.t.k, &tseg, &ttail);   // validated (and built) at submit
-                    d.t.seg = (const ttbl::SegTX*)tseg;
+                    d.t.seg = (const ttbl::TRows*)tseg;
                     d.t.tail = ttail;
                 }
                 d.tile0 = t0;

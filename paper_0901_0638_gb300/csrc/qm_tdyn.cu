@@ -251,97 +251,118 @@ qm_status t_table_build(double nu_d, double* seg, double* tail)
 // re-expansion is done in double: its k = m term dominates every sum, so the
 // rounding stays at a few ulp, far inside the map's 1e-12 bound (and long
 // double is a software quad type on some hosts, slow at first use).
-qm_status t_pack_fx(const double* seg10, int nseg, ttbl::SegTX* out)
+static_assert(ttbl::T_NROW == QM_T_NROW && sizeof(ttbl::TRows) == QM_T_ROWS_BYTES,
+              "the row layout qm.h documents");
+
+qm_status t_pack_rows(const double* seg10, int nseg, ttbl::TRows* out)
 {
-    static const double binom[10][10] = {
+    using LD = long double;
+    static const LD binom[10][10] = {
         {1}, {1, 1}, {1, 2, 1}, {1, 3, 3, 1}, {1, 4, 6, 4, 1}, {1, 5, 10, 10, 5, 1},
         {1, 6, 15, 20, 15, 6, 1}, {1, 7, 21, 35, 35, 21, 7, 1}, {1, 8, 28, 56, 70, 56, 28, 8, 1},
         {1, 9, 36, 84, 126, 126, 84, 36, 9, 1}};
+    constexpr int DIV = ttbl::T_ROWS_PER_UNIT / H_INV;             // rows per segment (4)
+    if (nseg * DIV != ttbl::T_NROW) return fail(QM_ERR_INVALID, "Student t: %d segments", nseg);
     for (int j = 0; j < nseg; ++j) {
         const double* c = seg10 + 10 * j;
-        double cp[10];
-        const double dl = (j == 0) ? 0.0 : -1.0 / 64;          // s = sigma + dl
-        for (int m = 0; m < 10; ++m) {
-            double acc = 0.0, p = 1.0;
-            for (int k = m; k < 10; ++k) {
-                acc += (double)c[k] * binom[k][m] * p;
-                p *= dl;
+        for (int q = 0; q < DIV; ++q) {
+            const int r = DIV * j + q;
+            // the row start r/128 in the segment's variable s (about the centre,
+            // or about 0 for j = 0): s = sigma + dl
+            const LD dl = (LD)q / ttbl::T_ROWS_PER_UNIT - (j == 0 ? 0.0L : 1.0L / (2 * H_INV));
+            LD cp[10];
+            for (int m = 0; m < 10; ++m) {
+                LD acc = 0, p = 1;
+                for (int k = m; k < 10; ++k) {
+                    acc += (LD)c[k] * binom[k][m] * p;
+                    p *= dl;
+                }
+                cp[m] = acc;
             }
-            cp[m] = acc;
-        }
-        double d[9];
-        for (int k = 0; k < 9; ++k) d[k] = ldexp(cp[k + 1], -4 * k);
-        if (!(d[0] > 0.0))
-            return fail(QM_ERR_UNSUPPORTED, "Student t: segment %d has a non-positive slope", j);
-        for (int k = 1; k < 9; ++k) {
-            if (d[k] < 0.0) {
-                if (-d[k] > 1e-18 * d[0])
-                    return fail(QM_ERR_UNSUPPORTED, "Student t: segment %d coefficient %d negative", j, k);
-                d[k] = 0.0;                                          // rounding residue
+            // H in th = 64 sigma: b'_k = cp_{k+1} 64^-k, k = 0..6 (degree 7 in sigma)
+            LD bh[7];
+            for (int k = 0; k < 7; ++k) bh[k] = std::ldexp(cp[k + 1], -6 * k);
+            if (!(bh[0] > 0)) return fail(QM_ERR_UNSUPPORTED, "Student t: row %d has a non-positive slope", r);
+            for (int k = 1; k < 7; ++k) {
+                if (bh[k] < 0) {
+                    if (-bh[k] > 1e-18L * bh[0])
+                        return fail(QM_ERR_UNSUPPORTED, "Student t: row %d coefficient %d negative", r, k);
+                    bh[k] = 0;                                           // rounding residue
+                }
             }
-        }
-        double pmax = 0.0;
-        for (int k = 0; k < 9; ++k) pmax += ldexp(d[k], -k);         // P at tau = 1/2
-        if (!(pmax < 2.0 * d[0]))
-            return fail(QM_ERR_UNSUPPORTED, "Student t: segment %d varies too fast", j);
-        int e2 = 0;
-        frexp(d[0], &e2);                                            // d_0 in [2^(e2-1), 2^e2)
-        const int s0 = e2 - 60;                                       // D_0 in [2^59, 2^60]
-        unsigned long long D[5];
-        for (int k = 0; k < 5; ++k) D[k] = (unsigned long long)llround(ldexp(d[k], -s0));
-        const int e0 = 1081 + s0;
-        // inner chain: C_k = d_{k+5} 2^-(s0 + c) on 32-bit integers, c the
-        // smallest scale (at least 1) that keeps every Horner partial value
-        // C_k + C_{k+1}/2 + ... (tau < 1/2) below 2^32
-        double fk[4];
-        for (int k = 0; k < 4; ++k) fk[k] = ldexp(d[k + 5], -s0);
-        auto partial_max = [](const double* v) {
-            double m = 0.0;
-            for (int k = 0; k < 4; ++k) {
-                double acc = 0.0;
-                for (int i = 3; i >= k; --i) acc = acc * 0.5 + v[i];
-                m = std::max(m, acc);
+            LD hmax = 0;
+            for (int k = 0; k < 7; ++k) hmax += std::ldexp(bh[k], -k);   // H at th = 1/2
+            if (!(hmax < 2 * bh[0])) return fail(QM_ERR_UNSUPPORTED, "Student t: row %d varies too fast", r);
+            int e2 = 0;
+            std::frexp((double)bh[0], &e2);                              // b'_0 in [2^(e2-1), 2^e2)
+            const int s0 = e2 - 1 - ttbl::T_HB;                           // H(0) 2^-s0 in [2^HB, 2^(HB+1))
+            long long B[3];
+            for (int k = 0; k < 3; ++k) B[k] = std::llround(std::ldexp(bh[k], -s0));
+            const int e0 = 1022 + ttbl::T_HB + s0;
+            // the outer accumulators stay below 2^62 (the high products' bound):
+            // every partial Horner value at th = 1/2
+            for (int k = 1; k <= 2; ++k) {
+                LD part = 0;
+                for (int i = k; i < 7; ++i) part += std::ldexp(bh[i], -(i - k));
+                if (!(std::ldexp(part, -s0) < std::ldexp((LD)1, 62) - 64))
+                    return fail(QM_ERR_UNSUPPORTED, "Student t: row %d partial sum %d out of range", r, k);
             }
-            return m;
-        };
-        int cs = 1;                                                   // the scale c
-        {
-            const double pm = partial_max(fk);
-            if (pm > 0.0) cs = std::max(1, (int)std::ceil(std::log2(pm)) - 32);
-        }
-        unsigned long long C[4];
-        for (;; ++cs) {
-            double cd[4];
-            for (int k = 0; k < 4; ++k) {
-                C[k] = (unsigned long long)llround(ldexp(fk[k], -cs));
-                cd[k] = (double)C[k];
+            // inner chain: C_k = b'_{k+3} 2^-(s0 + cs) on 32-bit integers, cs the
+            // smallest scale (at least 1) that keeps every Horner partial value
+            // C_k + C_{k+1}/2 + ... (th < 1/2) below 2^32
+            LD fk[4];
+            for (int k = 0; k < 4; ++k) fk[k] = std::ldexp(bh[k + 3], -s0);
+            auto partial_max = [](const LD* v) {
+                LD m = 0;
+                for (int k = 0; k < 4; ++k) {
+                    LD acc = 0;
+                    for (int i = 3; i >= k; --i) acc = acc * 0.5L + v[i];
+                    m = std::max(m, acc);
+                }
+                return m;
+            };
+            int cs = 1;
+            {
+                const LD pm = partial_max(fk);
+                if (pm > 0) cs = std::max(1, (int)std::ceil(std::log2((double)pm)) - 32);
             }
-            if (partial_max(cd) < 4294967288.0 || cs > 32) break;
-        }
-        if (D[4] >= (1ull << 52) || e0 <= 0 || e0 >= 2048 || cs > 32 || C[3] >= (1ull << 27))
-            return fail(QM_ERR_UNSUPPORTED, "Student t: segment %d outside the fixed-point range", j);
-        ttbl::SegTX& r = out[j];
-        r.a0 = (double)cp[0];
-        r.D0 = D[0];
-        r.D1 = D[1];
-        r.D2 = D[2];
-        r.D3 = D[3];
-        r.D4e = D[4] | ((unsigned long long)e0 << 52);
-        for (int k = 0; k < 3; ++k) r.c[k] = (unsigned)C[k];
-        r.c[3] = (unsigned)C[3] | ((unsigned)(32 - cs) << 27);
-        // the stored row against the original expansion at the segment's
-        // start, middle and end (quantisation of a0, D_k and C_k)
-        for (int q = 0; q <= 2; ++q) {
-            const double sig = (q == 0 ? 0.0 : q == 1 ? 1.0 / 64 : 1.0 / 32 - 1.0 / 4096);
-            const double tau = 16.0 * sig, s = sig + dl;
-            double P = 0.0, ref = 0.0;
-            for (int k = 8; k >= 0; --k)
-                P = P * tau + (k < 5 ? ldexp((double)D[k], s0) : ldexp((double)C[k - 5], s0 + cs));
-            for (int k = 9; k >= 0; --k) ref = ref * s + (double)c[k];
-            const double got = (double)r.a0 + sig * P;
-            if (ref != 0.0 && fabs(got / ref - 1.0) > 1e-13)
-                return fail(QM_ERR_UNSUPPORTED, "Student t: segment %d fixed-point form off by %g", j,
-                            fabs(got / ref - 1.0));
+            long long C[4];
+            for (;; ++cs) {
+                LD cd[4];
+                for (int k = 0; k < 4; ++k) {
+                    C[k] = std::llround(std::ldexp(fk[k], -cs));
+                    cd[k] = (LD)C[k];
+                }
+                if (partial_max(cd) < 4294967288.0L || cs > 32) break;
+            }
+            if (B[0] < (1ll << ttbl::T_HB) || B[2] >= (1ll << 52) || e0 <= 0 || e0 >= 2048 || cs > 32 ||
+                C[3] >= (1ll << 27))
+                return fail(QM_ERR_UNSUPPORTED, "Student t: row %d outside the fixed-point range", r);
+            fxt::SegA& A = out->a[r];
+            fxt::SegC& W = out->c[r];
+            A.a0 = (double)cp[0];
+            A.B0 = B[0];
+            A.B1 = B[1];
+            A.B2s = (long long)((unsigned long long)B[2] | ((unsigned long long)e0 << 52));
+            W.c3 = (unsigned)C[0];
+            W.c4 = (unsigned)C[1];
+            W.c5 = (unsigned)C[2];
+            W.c6s = (unsigned)C[3] | ((unsigned)(32 - cs) << 27);
+            // the stored row against the original expansion (degree 9) at
+            // points of the row: quantisation of a0, B_k and C_k, and the
+            // truncation to degree 7
+            for (int qq = 0; qq <= 4; ++qq) {
+                const LD sig = (LD)qq / (4 * ttbl::T_ROWS_PER_UNIT) * (qq == 4 ? 1 - 1.0L / 4096 : 1);
+                const LD th = 64 * sig, s = sig + dl;
+                LD H = 0, ref = 0;
+                for (int k = 6; k >= 0; --k)
+                    H = H * th + (k < 3 ? std::ldexp((LD)B[k], s0) : std::ldexp((LD)C[k - 3], s0 + cs));
+                for (int k = 9; k >= 0; --k) ref = ref * s + (LD)c[k];
+                const LD got = (LD)A.a0 + sig * H;
+                if (ref != 0 && std::fabs(got / ref - 1) > 1e-12L)
+                    return fail(QM_ERR_UNSUPPORTED, "Student t: row %d fixed-point form off by %g", r,
+                                (double)std::fabs(got / ref - 1));
+            }
         }
     }
     return QM_OK;
@@ -437,7 +458,7 @@ namespace {
 struct Entry {
     int device;
     double nu;
-    ttbl::SegTX* seg;    // device, NSEG fixed-point rows
+    ttbl::TRows* seg;    // device, the fixed-point rows
     double* tail;        // device, 3 + NT doubles
 };
 
@@ -464,16 +485,16 @@ qm_status t_table_device(double nu, const void** seg_dev, const double** tail_de
     std::vector<double> seg(10 * NSEG), tail(3 + NT);
     const qm_status st = t_table_build(nu, seg.data(), tail.data());
     if (st != QM_OK) return st;
-    std::vector<ttbl::SegTX> packed(NSEG);
-    const qm_status pst = t_pack_fx(seg.data(), NSEG, packed.data());
+    std::vector<ttbl::TRows> packed(1);
+    const qm_status pst = t_pack_rows(seg.data(), NSEG, packed.data());
     if (pst != QM_OK) return pst;
     Entry e{dev, nu, nullptr, nullptr};
-    if (cudaMalloc(&e.seg, sizeof(ttbl::SegTX) * NSEG) != cudaSuccess ||
+    if (cudaMalloc(&e.seg, sizeof(ttbl::TRows)) != cudaSuccess ||
         cudaMalloc(&e.tail, sizeof(double) * tail.size()) != cudaSuccess) {
         if (e.seg) cudaFree(e.seg);
         return fail(QM_ERR_NOMEM, "Student t: table allocation failed");
     }
-    if (cudaMemcpy(e.seg, packed.data(), sizeof(ttbl::SegTX) * NSEG, cudaMemcpyHostToDevice) != cudaSuccess ||
+    if (cudaMemcpy(e.seg, packed.data(), sizeof(ttbl::TRows), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(e.tail, tail.data(), sizeof(double) * tail.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaFree(e.seg);
         cudaFree(e.tail);
@@ -493,7 +514,7 @@ namespace {
 // small buffer; both built once per device and kept until exit.
 struct StaticT {
     int device;
-    ttbl::SegTX* seg;
+    ttbl::TRows* seg;      // NNU row tables
     double* tail;          // NNU x (3 + TAIL_DEG + 1)
 };
 std::vector<StaticT> g_static;
@@ -511,14 +532,14 @@ qm_status static_tables(int dev, const StaticT** out)
     if (cudaMemcpyFromSymbol(offline.data(), ttbl::SEG_T, sizeof(ttbl::SegT) * offline.size()) != cudaSuccess)
         return fail(QM_ERR_CUDA, "Student t: table read failed");
     std::vector<double> seg10(10 * NSEG);
-    std::vector<ttbl::SegTX> packed(ttbl::NNU * NSEG);
+    std::vector<ttbl::TRows> packed(ttbl::NNU);
     for (int k = 0; k < ttbl::NNU; ++k) {
         for (int j = 0; j < NSEG; ++j) {
             const ttbl::SegT& g = offline[k * NSEG + j];
             for (int c = 0; c < 5; ++c) seg10[10 * j + c] = g.a[c];
             for (int c = 0; c < 5; ++c) seg10[10 * j + 5 + c] = g.b[c];
         }
-        const qm_status pst = t_pack_fx(seg10.data(), NSEG, packed.data() + k * NSEG);
+        const qm_status pst = t_pack_rows(seg10.data(), NSEG, packed.data() + k);
         if (pst != QM_OK) return pst;
     }
     double kappa[ttbl::NNU], rt[ttbl::NNU][ttbl::TAIL_DEG + 1];
@@ -535,12 +556,12 @@ qm_status static_tables(int dev, const StaticT** out)
     }
     if (cudaMalloc(&e.tail, sizeof(double) * tail.size()) != cudaSuccess)
         return fail(QM_ERR_NOMEM, "Student t: table allocation failed");
-    if (cudaMalloc(&e.seg, sizeof(ttbl::SegTX) * packed.size()) != cudaSuccess) {
+    if (cudaMalloc(&e.seg, sizeof(ttbl::TRows) * packed.size()) != cudaSuccess) {
         cudaFree(e.tail);
         return fail(QM_ERR_NOMEM, "Student t: table allocation failed");
     }
     if (cudaMemcpy(e.tail, tail.data(), sizeof(double) * tail.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(e.seg, packed.data(), sizeof(ttbl::SegTX) * packed.size(), cudaMemcpyHostToDevice) !=
+        cudaMemcpy(e.seg, packed.data(), sizeof(ttbl::TRows) * packed.size(), cudaMemcpyHostToDevice) !=
             cudaSuccess) {
         cudaFree(e.tail);
         cudaFree(e.seg);
@@ -566,7 +587,7 @@ qm_status t_select(double nu, int* k, const void** seg_dev, const double** tail_
             const StaticT* st = nullptr;
             const qm_status s = static_tables(dev, &st);
             if (s != QM_OK) return s;
-            *seg_dev = st->seg + i * NSEG;
+            *seg_dev = st->seg + i;
             *tail_dev = st->tail + i * kStaticTail;
             return QM_OK;
         }
@@ -592,5 +613,5 @@ extern "C" qm_status qm_t_rows_build(double nu, void* rows)
     std::vector<double> seg(10 * QM_T_NSEG), tail(3 + QM_T_TAIL_TERMS);
     const qm_status st = qm::t_table_build(nu, seg.data(), tail.data());
     if (st != QM_OK) return st;
-    return qm::t_pack_fx(seg.data(), QM_T_NSEG, static_cast<qm::ttbl::SegTX*>(rows));
+    return qm::t_pack_rows(seg.data(), QM_T_NSEG, static_cast<qm::ttbl::TRows*>(rows));
 }

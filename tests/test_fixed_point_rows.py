@@ -236,23 +236,6 @@ def test_exp_to_normal_rows_against_the_oracle(exp_rows):
     assert r.max() <= 1e-12, xs[keep][nz][np.argmax(r)]
 
 
-def segtx_row(r, Sig: int, mlt: float, estrin: bool = False) -> float:
-    """One unsigned fixed-point row from a uint64[8] array (Horner or Estrin
-    inner chain), as the device evaluates it."""
-    a0b, D0, D1, D2, D3, D4e, c01, c23 = (int(x) for x in r)
-    w = (c01 & 0xFFFFFFFF, c01 >> 32, c23 & 0xFFFFFFFF, c23 >> 32)
-    t = Sig >> 32
-    if estrin:
-        lo = w[0] + ((w[1] * t) >> 32)
-        hi = w[2] + (((w[3] & 0x07FFFFFF) * t) >> 32)
-        x = lo + ((hi * ((t * t) >> 32)) >> 32)
-        assert x < 2**32
-        G = (x * t) >> (w[3] >> 27)
-    else:
-        G = inner(w, t)
-    return _finish((D4e & MANT) + G, (D3, D2, D1, D0), Sig, D4e >> 52, mlt, a0b, bias=False)
-
-
 def _finish(acc, Ds, Sig, e0, mlt, a0b, bias):
     T16 = Sig >> 4
     for D in Ds:
@@ -279,20 +262,48 @@ def segts_row(r, Sig: int, mlt: float) -> float:
     return _finish(acc, (D3, D2, D1, D0), Sig, D4e >> 52, mlt, a0b, bias=True)
 
 
+def inner_estrin(w, t32: int) -> int:
+    """The 32-bit inner chain in Estrin form, (C_a + th C_b) + th^2 (C_c + th
+    C_d), th^2 as hi32(th32 th32), and its join."""
+    lo = ((w[1] * t32) >> 32) + w[0]
+    hi = (((w[3] & 0x07FFFFFF) * t32) >> 32) + w[2]
+    x = ((hi * ((t32 * t32) >> 32)) >> 32) + lo
+    assert x < 2**32
+    return (x * t32) >> (w[3] >> 27)
+
+
+def fx_core(a_row, c_row, Tau: int, mlt: float, estrin: bool = False, hb: int = 61) -> float:
+    """One FIXED-layout row at th = Tau 2^-64: fma(mlt, H, a0) rounded once,
+    the leading bit of H(0) 2^-s0 at hb (61 for the quantile's rows, 58 for
+    the Student-t rows)."""
+    a0b, B0, B1, B2s = a_row
+    t32 = Tau >> 32
+    acc = (B2s & MANT) + (inner_estrin(c_row, t32) if estrin else inner(c_row, t32))
+    acc = B1 + mulhi3(acc, Tau)
+    acc = B0 + mulhi3(acc, Tau)
+    assert 2**hb <= acc < 2**(hb + 2)
+    top = acc >> (hb + 1)
+    hbits = ((acc + ((1 << (hb - 53)) << top)) >> (hb - 52 + top)) + (((B2s >> 52) + top) << 52)
+    return float(Fr(mlt) * Fr(dbl(hbits)) + Fr(dbl(a0b)))
+
+
 def t_fixed(rows, z: float, estrin: bool) -> float:
-    """The normal -> Student t map for |z| < 8.75: segment j = floor(32 |z|)
-    and Sig = (|z| 2^68) mod 2^63 from the bits, sigma = |z| - j/32 exact."""
+    """The normal -> Student t map for |z| < 8.75: row r = floor(128 |z|)
+    and Tau = (|z| 2^70) mod 2^63 from the bits, sigma = |z| - r/128 exact."""
+    A, C = rows
     a = abs(z)
     ab = bits(a)
     E = (ab >> 52) - 1023
     M = (ab & MANT) | (1 << 52)
-    j = 0 if E + 5 < 0 else M >> (52 - (E + 5))
-    lj = (j | 1).bit_length() - 1
-    zsb = 0 if j == 0 else ((lj - 5 + 1023) << 52) | ((j << (52 - lj)) & MANT)
+    r = 0 if E + 7 < 0 else M >> (52 - (E + 7))
+    lr = (r | 1).bit_length() - 1
+    zsb = 0 if r == 0 else ((lr - 7 + 1023) << 52) | ((r << (52 - lr)) & MANT)
     sig = a - dbl(zsb)
-    sh = E + 16
-    Sig = ((M << sh) & (2**63 - 1)) if sh >= 0 else (M >> -sh if sh > -64 else 0)
-    t = segtx_row(rows[j], Sig, sig, estrin)
+    sh = E + 18
+    Tau = ((M << sh) & (2**63 - 1)) if sh >= 0 else (M >> -sh if sh > -64 else 0)
+    a_row = tuple(int(x) for x in A[r])
+    c_row = tuple(int(x) for x in C[r])
+    t = fx_core(a_row, c_row, Tau, sig, estrin, hb=58)
     return t if z >= 0 else -t
 
 
@@ -302,7 +313,8 @@ def test_student_t_rows_against_the_oracle(nu):
     rows = qm.qm_t_rows_build(nu)
     rng = np.random.default_rng(int(nu * 100))
     z = np.concatenate([rng.standard_normal(400) * 2.5, rng.uniform(-8.74, 8.74, 200),
-                        np.arange(1, 280) / 32.0, np.arange(1, 280) / 32.0 - 2.0**-40, [1e-300, 2.0**-20, -3e-9]])
+                        np.arange(1, 1120) / 128.0, np.arange(1, 1120) / 128.0 - 2.0**-40,
+                        [1e-300, 2.0**-20, -3e-9, 8.75 - 2.0**-40]])
     z = z[np.abs(z) < 8.75]
     w = oracle.recycle_t(nu, z)
     for estrin in (False, True):
