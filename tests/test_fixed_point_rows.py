@@ -307,7 +307,7 @@ def t_fixed(rows, z: float, estrin: bool) -> float:
     return t if z >= 0 else -t
 
 
-@pytest.mark.parametrize("nu", [0.75, 4.0, 30.0])
+@pytest.mark.parametrize("nu", [0.75, 1.0, 2.7, 4.0, 30.0, 100.0])
 def test_student_t_rows_against_the_oracle(nu):
     import paper_0901_0638_gb300 as qm
     rows = qm.qm_t_rows_build(nu)
