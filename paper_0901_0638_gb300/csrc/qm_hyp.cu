@@ -297,8 +297,14 @@ __device__ __forceinline__ double hyp_side_eval(const HypSide& S, double a)
     const int E = (int)(ab >> 52) - 1023;
     if (E < E_MIN || E > S.e_max) return hyp_side_rare(S.seg, S.e_max, a);
     const uint64_t low = ab & ((1ull << 47) - 1ull);
-    const double sig = __dadd_rn(a, -__longlong_as_double((long long)(ab - low)));
-    return segts_eval(S.fx + 32 * (E - E_MIN) + (int)((ab >> 47) & 31u), low << 16, sig);
+    // sigma = a - (segment start) = low 2^(E - 52) as a double without an FP64
+    // instruction: low < 2^47 normalised (significand (low << lz) >> 11,
+    // exponent E + 11 - lz); the exact subtraction issued FP64 instructions
+    // on a pipe that bound the map
+    const int lz = __clzll(low | 1ull);
+    const uint64_t sb = low == 0 ? 0ull : ((low << lz) >> 11) + ((uint64_t)(E + 1033 - lz) << 52);
+    return segts_eval(S.fx + 32 * (E - E_MIN) + (int)((ab >> 47) & 31u), low << 16,
+                      __longlong_as_double((long long)sb));
 }
 
 __device__ __forceinline__ double hyp_eval(const HypSide& R, const HypSide& L, double v)
@@ -309,9 +315,11 @@ __device__ __forceinline__ double hyp_eval(const HypSide& R, const HypSide& L, d
     // evaluations would run both)
     const bool neg = (vb >> 63) != 0;
     const HypSide S{neg ? L.seg : R.seg, neg ? L.fx : R.fx, neg ? L.e_max : R.e_max};
-    double x = hyp_side_eval(S, a);
-    if ((vb & 0x7fffffffffffffffull) >= 0x7ff0000000000000ull) x = a;   // inf, NaN
-    return with_sign_of(x, vb);
+    // the inf/NaN case and the sign on the bits (no select between doubles)
+    const uint64_t ab = vb & 0x7fffffffffffffffull;
+    const uint64_t xb = ab >= 0x7ff0000000000000ull ? ab                                 // inf, NaN
+                                                    : (uint64_t)__double_as_longlong(hyp_side_eval(S, a));
+    return __longlong_as_double((long long)((xb & 0x7fffffffffffffffull) | (vb & 0x8000000000000000ull)));
 }
 
 // VEC: two elements per thread through 16-byte loads and stores (in and out
