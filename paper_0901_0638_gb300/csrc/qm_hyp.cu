@@ -291,11 +291,12 @@ static __device__ __noinline__ double hyp_side_rare(const ttbl::SegT* seg, int e
 // |Q| on one side for a = |v|: segment j of binade E from the bits, the
 // offset sigma = a - start exact (Sterbenz), tau = sigma / (2 w) =
 // (low 47 bits of the significand) 2^-48, and the biased fixed-point row
-__device__ __forceinline__ double hyp_side_eval(const HypSide& S, double a)
+// (returns the bits of the value: see hyp_eval)
+__device__ __forceinline__ uint64_t hyp_side_eval(const HypSide& S, double a)
 {
     const uint64_t ab = (uint64_t)__double_as_longlong(a);
     const int E = (int)(ab >> 52) - 1023;
-    if (E < E_MIN || E > S.e_max) return hyp_side_rare(S.seg, S.e_max, a);
+    if (E < E_MIN || E > S.e_max) return (uint64_t)__double_as_longlong(hyp_side_rare(S.seg, S.e_max, a));
     const uint64_t low = ab & ((1ull << 47) - 1ull);
     // sigma = a - (segment start) = low 2^(E - 52) as a double without an FP64
     // instruction: low < 2^47 normalised (significand (low << lz) >> 11,
@@ -303,8 +304,8 @@ __device__ __forceinline__ double hyp_side_eval(const HypSide& S, double a)
     // on a pipe that bound the map
     const int lz = __clzll(low | 1ull);
     const uint64_t sb = low == 0 ? 0ull : ((low << lz) >> 11) + ((uint64_t)(E + 1033 - lz) << 52);
-    return segts_eval(S.fx + 32 * (E - E_MIN) + (int)((ab >> 47) & 31u), low << 16,
-                      __longlong_as_double((long long)sb));
+    return (uint64_t)__double_as_longlong(segts_eval(S.fx + 32 * (E - E_MIN) + (int)((ab >> 47) & 31u), low << 16,
+                                                     __longlong_as_double((long long)sb)));
 }
 
 __device__ __forceinline__ double hyp_eval(const HypSide& R, const HypSide& L, double v)
@@ -318,7 +319,7 @@ __device__ __forceinline__ double hyp_eval(const HypSide& R, const HypSide& L, d
     // the inf/NaN case and the sign on the bits (no select between doubles)
     const uint64_t ab = vb & 0x7fffffffffffffffull;
     const uint64_t xb = ab >= 0x7ff0000000000000ull ? ab                                 // inf, NaN
-                                                    : (uint64_t)__double_as_longlong(hyp_side_eval(S, a));
+                                                    : hyp_side_eval(S, a);
     return __longlong_as_double((long long)((xb & 0x7fffffffffffffffull) | (vb & 0x8000000000000000ull)));
 }
 

@@ -59,20 +59,23 @@ k_batch(const DevSeg* __restrict__ segs, int nseg, unsigned long long ntiles, co
         while (lo + 1 < nseg && segs[lo + 1].tile0 <= tile) ++lo;
         const DevSeg sg = segs[lo];
         const size_t base = (size_t)(tile - sg.tile0) * blockDim.x * EPT;
-        double x[EPT];
+        // values move as bits: a select or a join of doubles costs FP64
+        // instructions, and the maps are bound by that pipe
+        unsigned long long xb[EPT];
 #pragma unroll
         for (int k = 0; k < EPT; ++k) {
             const size_t i = base + (size_t)k * blockDim.x + threadIdx.x;
-            x[k] = (i < sg.n) ? __ldcs(sg.in + i) : 0.0;
+            xb[k] = (i < sg.n) ? (unsigned long long)__ldcs(reinterpret_cast<const long long*>(sg.in) + i) : 0ull;
         }
 #pragma unroll
         for (int k = 0; k < EPT; ++k) {
             const size_t i = base + (size_t)k * blockDim.x + threadIdx.x;
-            double y;
-            if (sg.kind == KIND_T) y = recycle_t_sel<ESTRIN>(sg.t, x[k]);
-            else if (sg.kind == KIND_EXP) y = exp_to_normal_fx(x[k]);
-            else y = probit_fx<FX_FP64_LEAN>(fxT, x[k]);
-            if (i < sg.n) __stcs(sg.out + i, y);
+            const double x = __longlong_as_double((long long)xb[k]);
+            long long y;
+            if (sg.kind == KIND_T) y = __double_as_longlong(recycle_t_sel<ESTRIN>(sg.t, x));
+            else if (sg.kind == KIND_EXP) y = __double_as_longlong(exp_to_normal_fx(x));
+            else y = __double_as_longlong(probit_fx<FX_FP64_LEAN>(fxT, x));
+            if (i < sg.n) __stcs(reinterpret_cast<long long*>(sg.out) + i, y);
         }
     }
 }
@@ -84,11 +87,11 @@ k_single(const double* __restrict__ in, double* out, size_t n, int kind, TSel t,
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const double x = __ldcs(in + i);
-        double y;
-        if (kind == KIND_T) y = recycle_t_sel<false>(t, x);
-        else if (kind == KIND_EXP) y = exp_to_normal_fx(x);
-        else y = probit_fx<FX_FP64_LEAN>(fxT, x);
-        __stcs(out + i, y);
+        long long y;                                   // as bits (see k_batch)
+        if (kind == KIND_T) y = __double_as_longlong(recycle_t_sel<false>(t, x));
+        else if (kind == KIND_EXP) y = __double_as_longlong(exp_to_normal_fx(x));
+        else y = __double_as_longlong(probit_fx<FX_FP64_LEAN>(fxT, x));
+        __stcs(reinterpret_cast<long long*>(out) + i, y);
     }
 }
 
