@@ -138,7 +138,8 @@ __device__ __forceinline__ double normal_from_words(const fxt::FxTable* fxT, uin
     const uint64_t k = ((uint64_t)(hi >> 11) << 32) | lo;
     bool upper;
     const double m = probit_grid53_fx<FX_FP64_LEAN>(fxT, k, upper);
-    return upper ? m : -m;
+    // the sign on the bits (a select between m and -m costs FP64 instructions)
+    return __longlong_as_double(__double_as_longlong(m) ^ (long long)((unsigned long long)!upper << 63));
 }
 
 // D: the dimension at compile time, so that y = L eps unrolls to exactly the

@@ -722,15 +722,19 @@ k_fused_f64(PhiloxKeys K, uint64_t blk0, size_t n, double* out, double* partials
             const unsigned long long kk = ((unsigned long long)(hi >> 11) << 32) | lo;
             // |Phi^{-1}((k + 1/2) 2^-53)|; the Student-t map makes KIND 1 FP64 bound
             const double zn = probit_grid53_fx<KIND == 1 ? FX_FP64_LEAN : FX_TU_FADD>(fxT, kk, upper);
-            if (KIND == 0) {
-                z[h] = upper ? zn : -zn;
-            } else if (KIND == 1) {
+            // the sign on the bits: a select between zn and -zn costs FP64
+            // instructions
+            const long long zb = __double_as_longlong(zn);
+            const long long neg = (long long)((unsigned long long)(KIND == 2 ? upper : !upper) << 63);
+            const double zs = __longlong_as_double(zb ^ neg);
+            if (KIND == 1) {
                 // Student t by recycling the normal sample (Sec. 3 map)
-                z[h] = recycle_t_sel(tk, upper ? zn : -zn);
+                z[h] = recycle_t_sel(tk, zs);
             } else {
-                // Exp(1) sample x = -log(u) recycled by the Sec. 6 map:
-                // Q(x) = Phi^{-1}(1 - u), evaluated from the exact u (no log)
-                z[h] = upper ? -zn : zn;
+                // KIND 0: the normal sample; KIND 2: the Exp(1) sample
+                // x = -log(u) recycled by the Sec. 6 map, Q(x) = Phi^{-1}(1 - u),
+                // evaluated from the exact u (no log)
+                z[h] = zs;
             }
         }
         const size_t i0 = b * 2;

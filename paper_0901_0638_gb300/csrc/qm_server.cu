@@ -75,9 +75,10 @@ __device__ __forceinline__ double serve_f64_one(const fxt::FxTable* fxT, int kin
         // normal by Q(x) = Phi^{-1}(1 - e^{-x}) = Phi^{-1}(1 - u) (Sec. 6): the
         // exponential coordinate of u is evaluated by the table from u's bits,
         // so x is never rounded (z > 0 exactly when u < 1/2).
-        return upper ? -m : m;
+        return __longlong_as_double(__double_as_longlong(m) ^ (long long)((unsigned long long)upper << 63));
     }
-    const double z = upper ? m : -m;
+    // the sign on the bits (a select between m and -m costs FP64 instructions)
+    const double z = __longlong_as_double(__double_as_longlong(m) ^ (long long)((unsigned long long)!upper << 63));
     if (kind == 2) return recycle_t_call(t, z);
     return z;
 }

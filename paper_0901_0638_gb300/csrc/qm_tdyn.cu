@@ -256,7 +256,11 @@ static_assert(ttbl::T_NROW == QM_T_NROW && sizeof(ttbl::TRows) == QM_T_ROWS_BYTE
 
 qm_status t_pack_rows(const double* seg10, int nseg, ttbl::TRows* out)
 {
-    using LD = long double;
+    // double precision throughout: the conversion runs at the first use of a
+    // table on a device (for the offline tables inside the first Student-t
+    // call), and long double is software-emulated on some hosts (128-bit on
+    // aarch64), which made that first call take tens of milliseconds
+    using LD = double;
     static const LD binom[10][10] = {
         {1}, {1, 1}, {1, 2, 1}, {1, 3, 3, 1}, {1, 4, 6, 4, 1}, {1, 5, 10, 10, 5, 1},
         {1, 6, 15, 20, 15, 6, 1}, {1, 7, 21, 35, 35, 21, 7, 1}, {1, 8, 28, 56, 70, 56, 28, 8, 1},
@@ -269,7 +273,7 @@ qm_status t_pack_rows(const double* seg10, int nseg, ttbl::TRows* out)
             const int r = DIV * j + q;
             // the row start r/128 in the segment's variable s (about the centre,
             // or about 0 for j = 0): s = sigma + dl
-            const LD dl = (LD)q / ttbl::T_ROWS_PER_UNIT - (j == 0 ? 0.0L : 1.0L / (2 * H_INV));
+            const LD dl = (LD)q / ttbl::T_ROWS_PER_UNIT - (j == 0 ? 0.0 : 1.0 / (2 * H_INV));
             LD cp[10];
             for (int m = 0; m < 10; ++m) {
                 LD acc = 0, p = 1;
@@ -285,7 +289,7 @@ qm_status t_pack_rows(const double* seg10, int nseg, ttbl::TRows* out)
             if (!(bh[0] > 0)) return fail(QM_ERR_UNSUPPORTED, "Student t: row %d has a non-positive slope", r);
             for (int k = 1; k < 7; ++k) {
                 if (bh[k] < 0) {
-                    if (-bh[k] > 1e-18L * bh[0])
+                    if (-bh[k] > 1e-18 * bh[0])
                         return fail(QM_ERR_UNSUPPORTED, "Student t: row %d coefficient %d negative", r, k);
                     bh[k] = 0;                                           // rounding residue
                 }
@@ -316,7 +320,7 @@ qm_status t_pack_rows(const double* seg10, int nseg, ttbl::TRows* out)
                 LD m = 0;
                 for (int k = 0; k < 4; ++k) {
                     LD acc = 0;
-                    for (int i = 3; i >= k; --i) acc = acc * 0.5L + v[i];
+                    for (int i = 3; i >= k; --i) acc = acc * 0.5 + v[i];
                     m = std::max(m, acc);
                 }
                 return m;
@@ -333,7 +337,7 @@ qm_status t_pack_rows(const double* seg10, int nseg, ttbl::TRows* out)
                     C[k] = std::llround(std::ldexp(fk[k], -cs));
                     cd[k] = (LD)C[k];
                 }
-                if (partial_max(cd) < 4294967288.0L || cs > 32) break;
+                if (partial_max(cd) < 4294967288.0 || cs > 32) break;
             }
             if (B[0] < (1ll << ttbl::T_HB) || B[2] >= (1ll << 52) || e0 <= 0 || e0 >= 2048 || cs > 32 ||
                 C[3] >= (1ll << 27))
@@ -352,14 +356,14 @@ qm_status t_pack_rows(const double* seg10, int nseg, ttbl::TRows* out)
             // points of the row: quantisation of a0, B_k and C_k, and the
             // truncation to degree 7
             for (int qq = 0; qq <= 4; ++qq) {
-                const LD sig = (LD)qq / (4 * ttbl::T_ROWS_PER_UNIT) * (qq == 4 ? 1 - 1.0L / 4096 : 1);
+                const LD sig = (LD)qq / (4 * ttbl::T_ROWS_PER_UNIT) * (qq == 4 ? 1 - 1.0 / 4096 : 1);
                 const LD th = 64 * sig, s = sig + dl;
                 LD H = 0, ref = 0;
                 for (int k = 6; k >= 0; --k)
                     H = H * th + (k < 3 ? std::ldexp((LD)B[k], s0) : std::ldexp((LD)C[k - 3], s0 + cs));
                 for (int k = 9; k >= 0; --k) ref = ref * s + (LD)c[k];
                 const LD got = (LD)A.a0 + sig * H;
-                if (ref != 0 && std::fabs(got / ref - 1) > 1e-12L)
+                if (ref != 0 && std::fabs(got / ref - 1) > 1e-12)
                     return fail(QM_ERR_UNSUPPORTED, "Student t: row %d fixed-point form off by %g", r,
                                 (double)std::fabs(got / ref - 1));
             }
