@@ -79,3 +79,27 @@ def test_copula_validation_before_any_device_call(lib):
     L[1, 1] = 0.0
     assert lib.qm_copula_create(3, L.ctypes.data, m, ctypes.byref(h)) == qm.QM_ERR_INVALID
     assert lib.qm_copula_sample(None, 1, 0, None, 8, None) == qm.QM_ERR_INVALID
+
+
+def test_binding_constants_match_the_header():
+    """Every numeric #define and enum value of include/qm.h that the binding
+    also defines has the same value there (layouts and limits the tests and
+    callers size buffers from)."""
+    import os
+    import re
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "qm.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    values = {}
+    for name, expr in re.findall(r"^#define (QM_[A-Z0-9_]+) (.+)$", hdr, flags=re.M):
+        try:
+            values[name] = eval(expr, {}, dict(values))
+        except Exception:
+            pass
+    for name, val in re.findall(r"\b(QM_[A-Z0-9_]+)\s*=\s*(-?\d+)\s*[,}\n]", hdr):
+        values[name] = int(val)
+    checked = 0
+    for name, val in values.items():
+        if hasattr(qm, name):
+            assert getattr(qm, name) == val, (name, getattr(qm, name), val)
+            checked += 1
+    assert checked >= 20, checked
