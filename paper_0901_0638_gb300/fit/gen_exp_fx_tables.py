@@ -19,7 +19,7 @@ Q'' + Q' = Q Q'^2 (rode.taylor_exp_background):
   centre series truncated to degree 7 and re-expanded exactly about the end.
 * ROW_C, |x - ln 2| < 2^-12: z = v P(t), t = 1/32 - v, P(v) = Q(v)/v from the
   series about v = 0, re-expanded about v = 1/32, tau = 8 t, in the row form
-  of qm_t_fx.h (v_row(0)); relative accuracy through z = 0.
+  of qm_t_fx.h (centre_row); relative accuracy through z = 0.
 
 Every row is checked by emulating the device's integer steps exactly against
 mpmath at points of the row, and the worst relative error is printed.  Usage:
@@ -39,13 +39,12 @@ import mpmath as mp
 from . import rode
 from . import gen_fx_tables as FX
 from . import targets as T
-from .gen_exp_tables import DEG_V, V_COARSE, V_FINE, V_MAX, V_SPLIT, X_EMIN, q_and_slope, v_seg
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(os.path.dirname(HERE), "csrc", "qm_exp_fx_tables.h")
-NV = V_FINE * V_SPLIT + V_COARSE * (V_MAX - V_SPLIT)
 with mp.workdps(60):
     LN2 = +mp.log(2)                  # kept at 60 digits (module import runs at mpmath's default 15)
+DEG_C = 9                             # the centre row's ODE series: Q(v) to v^9, P(v) = Q(v)/v to v^8
 
 
 def reexpand(c, h, sign=1):
@@ -127,50 +126,42 @@ def sig_of(t, k):
     return (M << sh) & (2**63 - 1) if sh >= 0 else (M >> -sh if sh > -64 else 0)
 
 
-def v_row(j):
-    mp.mp.dps = 50
-    _, b, _ = v_seg(j)
-    if j < V_FINE * V_SPLIT:
-        w, k = mp.mpf(1) / V_FINE, 3
-        vc = mp.mpf(0) if j == 0 else (mp.mpf(j) + mp.mpf("0.5")) / V_FINE
-        ve = mp.mpf(j + 1) / V_FINE
-    else:
-        q = j - V_FINE * V_SPLIT + V_COARSE * V_SPLIT
-        w, k = mp.mpf(1) / V_COARSE, 1
-        vc = (mp.mpf(q) + mp.mpf("0.5")) / V_COARSE
-        ve = mp.mpf(q + 1) / V_COARSE
-    if j == 0:
-        # z = v P(v), P(v) = sum b_{i+1} v^i about v = 0, re-expanded about
-        # v = 1/32 in t = 1/32 - v
-        p = reexpand(b[1:], ve, -1)
-        d = [p[i] / mp.mpf(2) ** (k * i) for i in range(len(p))]
-        a0 = 0.0
-        taumax = mp.mpf(3) / 8                           # t <= 3/64 (v >= -1/64)
-    else:
-        g = reexpand(b, ve - vc, -1)                      # |z|(v_e - t) = sum g_m t^m
-        a0 = float(g[0])
-        H = [-g[m + 1] for m in range(len(g) - 1)]
-        d = [H[i] / mp.mpf(2) ** (k * i) for i in range(len(H))]
-        taumax = mp.mpf(2) ** k * w
-    D, f, s0, e0 = quantise(d, taumax, ("V", j))
-    # check: the device arithmetic at points of the row against mpmath
+def centre_row():
+    """ROW_C: z = v P(v) about v = 0, P(v) = Q(v)/v from the ODE series with
+    Q(0) = 0, Q'(0) = sqrt(pi/2), re-expanded about v = 1/32 in t = 1/32 - v,
+    tau = 8 t <= 3/8 (v >= -1/64), quantised in the row form of qm_t_fx.h and
+    checked by emulating the device's chain at points of [-1/64, 1/32)."""
+    mp.mp.dps = 40
+    b = rode.taylor_exp_background(mp.mpf(0), mp.mpf(0), mp.sqrt(mp.pi / 2), DEG_C + 1)[: DEG_C + 1]
+    ve = mp.mpf(1) / 32
+    p = reexpand(b[1:], ve, -1)
+    d = [p[i] / mp.mpf(2) ** (3 * i) for i in range(len(p))]
+    D, f, s0, e0 = quantise(d, mp.mpf(3) / 8, "centre row")
     worst = 0.0
-    vlo = mp.mpf(-1) / 64 if j == 0 else ve - w
+    vlo = -ve / 2
     for frac in (0.0, 0.13, 0.5, 0.87, 0.999):
         v = float(vlo + (ve - vlo) * frac)
-        if j == 0 and v == 0.0:
+        if v == 0.0:
             continue
-        t = float(mp.mpf(float(ve)) - mp.mpf(v))        # exact in the device (or rounded for row 0)
-        Sig = sig_of(t, k)
-        mlt = v if j == 0 else -t
-        z = emulate(a0, D, f, s0, Sig, mlt)
+        t = float(mp.mpf(float(ve)) - mp.mpf(v))         # rounded as the device rounds it
+        z = emulate(0.0, D, f, s0, sig_of(t, 3), v)
         vv = mp.mpf(v)
         ref = T.q_exp(vv) if vv >= 0 else -T.q_exp(-mp.log(2 - mp.exp(-vv)))
         worst = max(worst, float(abs(mp.mpf(z) / ref - 1)))
-    return j, a0, D, f, e0, worst
+    return 0.0, D, f, e0, worst
+
+
+def q_and_slope(v):
+    """Q(v) = Phi^{-1}(1 - e^{-v}/2) and Q'(v) = e^{-v} / (2 phi(Q)), the
+    initial values of the exponential-background ODE series at v."""
+    if v == 0:
+        return mp.mpf(0), mp.sqrt(mp.pi / 2)
+    q0 = T.q_exp(v)
+    return q0, mp.exp(-v) / 2 / mp.npdf(q0)
 
 
 K = 6                                  # 64 segments in every binade of x (the FIXED layout)
+X_EMIN = -26                           # below 2^-26, u = x - x^2/2 is 1 - e^{-x} to double precision
 X_EMAX = 6                             # binades 2^X_EMIN .. [64, 128) of x
 NROWS = (X_EMAX - X_EMIN + 1) << K
 POS_X = mp.mpf("0.6875")               # the segment [0.6875, 0.6953125) holds ln 2: z = a0 - t_u H from it on
@@ -293,7 +284,7 @@ def main():
     cells = [(E, j) for E in range(X_EMIN, X_EMAX + 1) for j in range(1 << K)]
     with mproc.Pool(max(1, os.cpu_count() or 2)) as pool:
         rows = pool.map(binade_row, cells, chunksize=8)
-        centre = v_row(0)
+        centre = centre_row()
     assert len(rows) == NROWS
     near_lo, near_hi = float(LN2 - V_NEAR), float(LN2 + V_NEAR)   # ROW_C serves [near_lo, near_hi)
     clo, chi = seg_bounds(-1, int((LN2 * 2 - 1) * 2**K))
@@ -301,7 +292,7 @@ def main():
     bits = lambda x: struct.unpack("<Q", struct.pack("<d", x))[0]
     wn = max(r[4] for r in rows if r[2] == "neg")
     wp = max(r[4] for r in rows if r[2] == "pos")
-    wc = centre[5]                          # over v in [-1/64, 1/32), wider than it serves
+    wc = centre[4]                          # over v in [-1/64, 1/32), wider than it serves
     print(f"exp -> normal fixed-point rows: {NROWS} binade rows (worst below ln 2 {wn:.3g}, above {wp:.3g}), "
           f"centre row (worst {wc:.3g})", file=sys.stderr)
     L = [
@@ -330,7 +321,7 @@ def main():
     for _, _, _, q, _ in rows:
         C = q["C"]
         L.append("  {" + ",".join(f"{x:#x}u" for x in C[:3] + [C[3] | (q["sh"] << 27)]) + "},\n")
-    _, a0, D, f, e0, _ = centre
+    a0, D, f, e0, _ = centre
     L.append("};\n\n__device__ const ttbl::SegTX ROW_C = \n" + row_literal(a0, D, f, e0).rstrip(",\n") + ";\n")
     L.append("\n}  // namespace efx\n}  // namespace qm\n")
     with open(OUT, "w") as fh:

@@ -349,3 +349,53 @@ def test_hyperbolic_biased_rows_against_the_oracle(abd):
     r = np.abs(np.array(got) / w - 1)
     print(f"hyperbolic {abd} biased rows: max rel {r.max():.3g}")
     assert r.max() <= 1e-12, v[np.argmax(r)]
+
+
+def _generated(fn, *args):
+    """Run one row generator at its own mpmath precision, restoring the
+    caller's afterwards."""
+    import mpmath as mp
+    with mp.workprec(mp.mp.prec):
+        return fn(*args)
+
+
+def _row_fields(q):
+    """The device words of one FIXED-layout row from a generator's fields."""
+    a = (bits(float(q["a0"])), q["B"][0] & M64, q["B"][1] & M64, ((q["e0"] << 52) | q["B"][2]) & M64)
+    c = tuple(q["C"][:3]) + (q["C"][3] | (q["sh"] << 27),)
+    return a, c
+
+
+def test_fixed_table_rows_are_what_their_generator_writes(fx_table):
+    """Rows of csrc/qm_fx_tables.h regenerated one by one from
+    fit/gen_fx_tables.py (the u = 1/2 binade, the middle of the main
+    binades, the first deep binade, the last binade) equal the committed
+    words: the table is the generator's output and nothing else."""
+    pytest.importorskip("mpmath")
+    from paper_0901_0638_gb300.fit import gen_fx_tables as G
+    A, C = fx_table
+    for e, j in ((0, 0), (0, 63), (17, 31), (63, 63), (64, 0), (500, 17), (G.E_LAST, 63)):
+        e_, j_, q, worst = _generated(G.job, (e, j))
+        row = G.seg_index(e, j) + (1 << G.K_MAIN)               # after the zero rows of u = 1/2
+        assert (e_, j_) == (e, j) and worst < 4e-16, (e, j, worst)
+        assert (A[row], C[row]) == _row_fields(q), (e, j)
+
+
+def test_exp_to_normal_rows_are_what_their_generator_writes(exp_rows):
+    """Rows of csrc/qm_exp_fx_tables.h regenerated from
+    fit/gen_exp_fx_tables.py -- binade rows on both sides of ln 2 (the
+    segment that holds it included) and the centre row -- equal the
+    committed words."""
+    pytest.importorskip("mpmath")
+    from paper_0901_0638_gb300.fit import gen_exp_fx_tables as G
+    (A, C), centre, consts = exp_rows
+    cells = [(G.X_EMIN, 0), (-8, 40), (-1, 0), (-1, 24), (-1, 25), (0, 7), (G.X_EMAX, 63)]
+    for E, j in cells:
+        E_, j_, side, q, worst = _generated(G.binade_row, (E, j))
+        row = ((E - consts["X_EMIN"]) << consts["X_K"]) + j
+        assert (E_, j_) == (E, j) and side == ("pos" if E >= -1 and (E > -1 or j >= 24) else "neg")
+        assert worst < 2e-15, (E, j, worst)
+        assert (A[row], C[row]) == _row_fields(q), (E, j)
+    a0, D, f, e0, worst = _generated(G.centre_row)
+    assert worst < 1e-13
+    assert centre == (bits(a0), D[0], D[1], D[2], D[3], (e0 << 52) | D[4], tuple(f))

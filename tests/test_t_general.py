@@ -111,3 +111,30 @@ def test_out_of_range_nu_is_rejected():
         with pytest.raises(qm.QMError) as e:
             qm.qm_t_table_build(nu)
         assert e.value.status == qm.QM_ERR_UNSUPPORTED
+
+
+def test_offline_t_tables_are_what_their_generator_writes():
+    """Segments and tail series of csrc/qm_t_tables.h (the tabulated nu)
+    regenerated from fit/gen_t_tables.py equal the committed literals: the
+    first, a middle and the last segment of three nu, and every tail row."""
+    mp = pytest.importorskip("mpmath")
+    import os
+    import re
+    from paper_0901_0638_gb300.fit import gen_t_tables as G
+    text = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                             "paper_0901_0638_gb300", "csrc", "qm_t_tables.h")).read()
+    body = text[text.index("SEG_T[NNU * NSEG] = {"):text.index("T_KAPPA")]
+    rows = re.findall(r"\{\{([^}]*)\},\{([^}]*)\},0\.0f\}", body)
+    assert len(rows) == len(G.NU_SET) * G.NSEG
+    tails = re.findall(r"^  \{([^{}]*)\},$", text[text.index("T_TAIL["):], flags=re.M)
+    assert len(tails) == len(G.NU_SET)
+    with mp.workprec(mp.mp.prec):
+        for i, nu in enumerate(G.NU_SET):
+            if nu in (1, 4, 30):
+                for j in (0, G.NSEG // 2, G.NSEG - 1):
+                    _, _, b, _ = G.seg((nu, j))
+                    d, f = rows[i * G.NSEG + j]
+                    assert d == ",".join(G.hexd(x) for x in b[:5]), (nu, j)
+                    assert f == ",".join(G.hexf(x) for x in b[5:10]), (nu, j)
+            _, R, worst, _ = G.tail_fit(nu)
+            assert tails[i] == ",".join(G.hexd(c) for c in R), nu
