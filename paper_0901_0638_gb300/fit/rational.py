@@ -17,12 +17,6 @@ import numpy as np
 LD = np.longdouble
 
 
-def cheb_nodes(a, b, n):
-    k = np.arange(n, dtype=LD)
-    t = -np.cos((k + LD(0.5)) * np.pi / LD(n))
-    return t
-
-
 def cheb_basis(t, deg):
     T = np.empty((t.size, deg + 1), dtype=LD)
     T[:, 0] = 1

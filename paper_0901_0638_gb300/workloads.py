@@ -143,18 +143,6 @@ def ragged_segments(seed: int = 4, nseg: int = 256, lo: int = 10, hi: int = 24):
     return lens.tolist(), targets.tolist()
 
 
-def ragged_inputs(seed: int, lens, targets, device="cpu") -> torch.Tensor:
-    """Concatenated inputs: normals for Student-t segments, Exp(1) for the
-    exponential->normal segments (segment j uses Philox stream j + 1)."""
-    parts = []
-    for j, (n, tgt) in enumerate(zip(lens, targets)):
-        if tgt == 8:
-            parts.append(exponential(seed, n, 0, j + 1, device))
-        else:
-            parts.append(normal_box_muller(seed, n, 0, j + 1, device))
-    return torch.cat(parts) if parts else torch.empty(0, dtype=torch.float64)
-
-
 # ---------------------------------------------------------------------------
 # Serving trace: Poisson arrivals, log-uniform sizes, mixed targets.
 # ---------------------------------------------------------------------------
