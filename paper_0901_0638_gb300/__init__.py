@@ -13,6 +13,12 @@ import os
 
 from . import _build
 
+
+def _read_text(path):
+    with open(path) as fh:
+        return fh.read()
+
+
 QM_OK, QM_ERR_INVALID, QM_ERR_UNSUPPORTED, QM_ERR_CUDA, QM_ERR_NOMEM, QM_ERR_TIMEOUT = range(6)
 QM_DIST_UNIFORM, QM_DIST_NORMAL, QM_DIST_STUDENT_T, QM_DIST_EXPONENTIAL = range(4)
 (QM_VAR_DEFAULT, QM_VAR_BRANCHFREE, QM_VAR_HYBRID_VOTE, QM_VAR_MIXED_HALLEY,
@@ -137,7 +143,7 @@ def declared_symbols():
     for h in sorted(os.listdir(os.path.join(root, "include"))):
         if not h.endswith(".h"):
             continue
-        txt = open(os.path.join(root, "include", h)).read()
+        txt = _read_text(os.path.join(root, "include", h))
         txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
         names += re.findall(r"\b(qm_[a-z0-9_]+)\s*\(", txt)
     return sorted(set(names))

@@ -9,6 +9,11 @@ import pytest
 import paper_0901_0638_gb300 as qm
 
 
+def _read_text(path):
+    with open(path) as fh:
+        return fh.read()
+
+
 @pytest.fixture(scope="module")
 def lib():
     return qm.load()
@@ -87,7 +92,7 @@ def test_binding_constants_match_the_header():
     callers size buffers from)."""
     import os
     import re
-    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "qm.h")).read()
+    hdr = _read_text(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "qm.h"))
     hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
     values = {}
     for name, expr in re.findall(r"^#define (QM_[A-Z0-9_]+) (.+)$", hdr, flags=re.M):

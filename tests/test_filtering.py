@@ -22,6 +22,12 @@ from scipy import integrate, special
 import oracle
 from paper_0901_0638_gb300 import workloads as W
 
+
+def _read_text(path):
+    with open(path) as fh:
+        return fh.read()
+
+
 HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                    "paper_0901_0638_gb300", "csrc", "qm_filter_coeffs.h")
 
@@ -89,7 +95,7 @@ def c_scalar(text, name):
 
 @pytest.fixture(scope="module")
 def tables():
-    text = re.sub(r"//[^\n]*", "", open(HDR).read())
+    text = re.sub(r"//[^\n]*", "", _read_text(HDR))
     deg64 = int(c_scalar(text, "AN64_DEG"))
     deg32 = int(c_scalar(text, "AN32_DEG"))
     return {

@@ -20,6 +20,12 @@ import pytest
 
 import oracle
 
+
+def _read_text(path):
+    with open(path) as fh:
+        return fh.read()
+
+
 CSRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_0901_0638_gb300", "csrc")
 M64 = (1 << 64) - 1
 MANT = (1 << 52) - 1
@@ -64,7 +70,7 @@ def _int(tok: str) -> int:
 @pytest.fixture(scope="module")
 def fx_table():
     """(A rows: a0 bits, B0, B1, B2 | e0;  C rows: four 32-bit words)."""
-    text = open(os.path.join(CSRC, "qm_fx_tables.h")).read()
+    text = _read_text(os.path.join(CSRC, "qm_fx_tables.h"))
     body = text[text.index("SEG_FX = {"):]
     a_part, c_part = body.split(" },\n {\n", 1)
     A = []
@@ -154,7 +160,7 @@ def exp_rows():
     """ROWS (a0 bits, B0, B1, B2 | e0) and ROWS_IN (four 32-bit words), the
     binade rows in the FIXED layout; ROW_C, the centre row (a0 bits, D0..D3,
     D4 | e0, (four 32-bit words))."""
-    text = open(os.path.join(CSRC, "qm_exp_fx_tables.h")).read()
+    text = _read_text(os.path.join(CSRC, "qm_exp_fx_tables.h"))
     consts = {k: int(v) for k, v in re.findall(r"constexpr int (\w+) = (-?\d+);", text)}
     for k in ("NEAR_LO", "NEAR_HI", "POS"):
         consts[k] = int(re.search(k + r"_BITS = (0x[0-9a-fA-F]+)ull", text).group(1), 16)

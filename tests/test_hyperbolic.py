@@ -202,7 +202,8 @@ def evaluate(tables, v):
         res = np.empty_like(aa)
         central = E < qm.QM_HYP_E_MIN
         Ec = np.minimum(E, em)
-        j = np.where(E > em, 31, np.floor((aa / np.ldexp(1.0, E) - 1) * 32).astype(int))
+        with np.errstate(invalid="ignore", divide="ignore"):        # both branches are evaluated
+            j = np.where(E > em, 31, np.floor((aa / np.ldexp(1.0, E) - 1) * 32).astype(int))
         c = np.ldexp(1 + (2 * j + 1) / 64.0, Ec)
         idx = np.where(central, 0, 1 + 32 * (Ec - qm.QM_HYP_E_MIN) + j)
         s = np.where(central, aa, aa - c)

@@ -15,6 +15,12 @@ import re
 
 import pytest
 
+
+def _read_text(path):
+    with open(path) as fh:
+        return fh.read()
+
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PKG = os.path.join(ROOT, "paper_0901_0638_gb300")
 ORACLE = os.path.join(ROOT, "oracle")
@@ -30,7 +36,7 @@ def _sources(top, exts):
 
 def _code(path):
     """The file's text without comments and docstrings (Python) or comments (C)."""
-    text = open(path).read()
+    text = _read_text(path)
     if path.endswith(".py"):
         tree = ast.parse(text)
         for node in ast.walk(tree):
@@ -57,7 +63,7 @@ def test_oracle_never_reaches_the_package():
 
 
 def test_shared_input_module_imports_neither_side():
-    tree = ast.parse(open(os.path.join(PKG, "workloads.py")).read())
+    tree = ast.parse(_read_text(os.path.join(PKG, "workloads.py")))
     mods = set()
     for node in ast.walk(tree):
         if isinstance(node, ast.Import):
@@ -72,7 +78,7 @@ def test_shared_input_module_imports_neither_side():
     ("__graft_entry__.py", {"build", "smoke"}),
 ])
 def test_oracle_called_only_from_baseline_build_and_smoke(path, allowed):
-    tree = ast.parse(open(os.path.join(ROOT, path)).read())
+    tree = ast.parse(_read_text(os.path.join(ROOT, path)))
     users = set()
 
     def visit(node, fn):

@@ -35,7 +35,7 @@ def _worker(rank, world, port, n, out):
 def test_two_ranks_shard_stream_and_take_max_time():
     n, world = 4096, 2
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_worker, args=(world, port, n, out), nprocs=world, join=True)
         res = dict(out)

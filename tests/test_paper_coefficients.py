@@ -18,12 +18,18 @@ import re
 
 import pytest
 
+
+def _read_text(path):
+    with open(path) as fh:
+        return fh.read()
+
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "paper_0901_0638_gb300", "csrc", "qm_paper_coeffs.h")
 
 
 def stored_tables():
-    src = open(HEADER).read()
+    src = _read_text(HEADER)
     out = {}
     for name in ("A_P", "A_Q", "B_P", "B_Q", "C_P", "C_Q"):
         m = re.search(name + r"\[\w+\]\s*=\s*\{(.*?)\};", src, re.S)
