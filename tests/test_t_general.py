@@ -114,10 +114,11 @@ def test_closed_forms_nu_1_and_2():
 
 
 def test_out_of_range_nu_is_rejected():
-    for nu in (0.5, 0.25, 100.5, 0.0, -1.0, float("nan")):
-        with pytest.raises(qm.QMError) as e:
-            qm.qm_t_table_build(nu)
-        assert e.value.status == qm.QM_ERR_UNSUPPORTED
+    for nu in (0.5, 0.25, 100.5, 0.0, -1.0, float("nan"), float("inf")):
+        for build in (qm.qm_t_table_build, qm.qm_t_rows_build):
+            with pytest.raises(qm.QMError) as e:
+                build(nu)
+            assert e.value.status == qm.QM_ERR_UNSUPPORTED, (build.__name__, nu)
 
 
 def test_offline_t_tables_are_what_their_generator_writes():
